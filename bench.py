@@ -1,0 +1,319 @@
+"""Benchmark of one detection window per step: sd_update over the window's
+pairs (Algorithm 1) and sd_close_window (Algorithm 2 + §4.2), through the C
+ABI.
+
+Prints one JSON line (rank 0).  `value` is whole-job packets per second
+(Gpps) with the pairs already resident in HBM; `e2e` is the same metric with
+the pairs fed from pinned host memory through sd_update (host->device copies
+inside the timed region) and the report read back.  `roofline` covers the
+dominant kernel (the update): algorithmic bytes = 8 per pair, over its CUDA
+event time, against the measured HBM copy bandwidth.
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1803_11449_gb300 import traffic as T  # noqa: E402
+
+WORKLOAD = "core"
+WORKLOAD_DESC = ("core-link window: 2^26 (src,dst) uint32 pairs, 2^24 Zipf(1.05) sources, 2^26 "
+                 "destinations, 500 planted super points (1,024-200,000 peers); DHLA g=512 r=4 "
+                 "k=16 alpha=8 (16 MiB per direction, L2-resident), theta=1024, both directions")
+BYTES_PER_PAIR = 8
+GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
+CPU_SAMPLE_PAIRS = 1 << 23
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region (read-only queries)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return None
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def window_for(rank: int, n: int | None = None):
+    """Each rank processes its own link: an independent window (weak scaling)."""
+    return T.make_window(WORKLOAD, T.window_seed(2, link=rank), n=n)
+
+
+def cpu_oracle_rate(pairs: np.ndarray, sample: int):
+    """The oracle, as it stands, on the first `sample` pairs of the window:
+    update then close, single-threaded.  Returns (pairs/s, seconds)."""
+    import oracle as O
+    O.build()
+    w = T.WORKLOADS[WORKLOAD]
+    op = O.params_from(w.sketch(), seed=T.window_seed(2))
+    grid = O.new_grid(op)
+    sub = np.ascontiguousarray(pairs[:sample])
+    t0 = time.perf_counter()
+    O.update(op, grid, sub)
+    O.close_window(op, grid)
+    dt = time.perf_counter() - t0
+    return sample / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    win = window_for(0)
+    times = []
+    rate = None
+    for i in range(args.warmup + args.steps):
+        r, dt = cpu_oracle_rate(win.pairs, args.ref_sample)
+        if i >= args.warmup:
+            times.append(dt)
+            rate = r
+    total = sum(times)
+    value = args.steps * args.ref_sample / total / 1e9
+    line = {
+        "impl": "reference", "metric": "packets/s (Gpps)", "value": value, "unit": "Gpps",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "pairs_per_step": args.ref_sample},
+        "cpu_baseline": {"value": value, "unit": "Gpps", "cores": 1, "kind": "oracle",
+                         "sample": f"first {args.ref_sample} pairs of the window, update + close"},
+        "e2e": {"value": value, "unit": "Gpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd
+
+    torch.cuda.set_device(local)
+    win = window_for(rank)
+    n = len(win.pairs)
+    pairs_dev = torch.from_numpy(win.pairs.reshape(-1).view(np.int32)).cuda()
+    pairs_host = torch.from_numpy(win.pairs.reshape(-1).view(np.int32)).pin_memory()
+    stream = torch.cuda.current_stream()
+    w = T.WORKLOADS[WORKLOAD]
+    p = sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream.cuda_stream)
+    h = sd.sd_create(p)
+    if args.mode is not None or args.unroll or args.threads:
+        sd.sd_set_tuning(h, mode=args.mode or 0, unroll=args.unroll, block_threads=args.threads)
+
+    def step():
+        sd.sd_update(h, pairs_dev)
+        return sd.sd_close_window(h)
+
+    for _ in range(args.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    close_ms = []
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            sd.sd_update(h, pairs_dev)
+            ev[i][1].record(stream)
+            c0 = time.perf_counter()
+            rep = sd.sd_close_window(h)
+            close_ms.append(1e3 * (time.perf_counter() - c0))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    dist_barrier(world)
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    upd = [a.elapsed_time(b_) / 1e3 for a, b_ in ev]
+    elapsed_max = dist_max(elapsed, world)
+    value = world * args.steps * n / elapsed_max / 1e9
+
+    # end to end: pinned host pairs through sd_update (H2D in the timed
+    # region), report back to the host in sd_close_window
+    for _ in range(2):
+        sd.sd_update(h, pairs_host)
+        sd.sd_close_window(h)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    e0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.e2e_steps):
+        sd.sd_update(h, pairs_host)
+        r2 = sd.sd_close_window(h)
+        d2h += 296 + 8 * r2.n_hits_total
+    torch.cuda.synchronize()
+    e_el = dist_max(time.perf_counter() - e0, world)
+    e2e = world * args.e2e_steps * n / e_el / 1e9
+    tuning = sd.sd_get_tuning(h)
+    sd.sd_destroy(h)
+
+    peak, peak_kind = measured_peaks()
+    t_upd = statistics.mean(upd)
+    achieved = BYTES_PER_PAIR * n / t_upd / 1e9
+    clocks = clk.summary()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, dt = cpu_oracle_rate(win.pairs, args.cpu_sample)
+        cpu = {"value": r / 1e9, "unit": "Gpps", "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} pairs of the window: oracle update + close "
+                         f"({dt:.1f} s, single thread)"}
+    line = {
+        "metric": "packets/s (Gpps)", "value": value, "unit": "Gpps", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "pairs_per_step_per_gpu": n,
+                   "l2": "inputs larger than L2 (512 MiB of pairs per step)",
+                   "parallelism": f"{world} independent link(s), one per GPU",
+                   "tuning": {"mode": tuning.mode, "block_threads": tuning.block_threads,
+                              "blocks_per_sm": tuning.blocks_per_sm, "unroll": tuning.unroll}},
+        "gbps_at_800B": value * 1e9 * GBITS_PER_PACKET,
+        "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
+                             "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
+        "update_ms": 1e3 * t_upd,
+        "bitsets_per_s": p.r * p.dirs * n / t_upd,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_update", "peak_source": f"hbm_gbs, {peak_kind}"},
+        "e2e": {"value": e2e, "unit": "Gpps", "h2d_bytes_per_step": BYTES_PER_PAIR * n,
+                "d2h_bytes_per_step": int(d2h / max(1, args.e2e_steps))},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clocks,
+        "report": {"hits": int(rep.n_hits_total), "n_cand": rep.n_cand,
+                   "n_hot_row0": [int(x) for x in rep.n_hot[:, 0]]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
+    ap.add_argument("--ref-sample", type=int, default=1 << 22)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", type=int, default=None)
+    ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * sd.h -- C ABI of the GB300 library for network super-point detection with
+ * the double-direction hash linear-estimator array (DHLA) of "Economical and
+ * efficient network super points detection based on GPU" (arxiv 1803.11449).
+ *
+ * A handle owns one DHLA per traffic direction on one GPU: r rows ("LA"s) of
+ * 2^k linear estimators of g bits each.  sd_update feeds (src, dst) IPv4
+ * pairs into it (Algorithm 1); sd_close_window finds the hot estimators,
+ * restores candidate super points by inverting the hash group, estimates
+ * their cardinality (Eq. 4) and reports those at or above theta (Algorithm 2
+ * and §4.2), then clears the DHLA for the next window.
+ *
+ * Conventions for every function:
+ *   - Return 0 (SD_OK) on success and a negative SD_ERR_* code otherwise;
+ *     sd_last_error(h) then holds a one-line message.
+ *   - Nothing here takes ownership of caller memory.  Buffers the library
+ *     returns (sd_report.hits) belong to the handle.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by
+ *     the caller.  Different handles are independent.
+ *   - All device work runs on the handle's CUDA stream (sd_params.cuda_stream,
+ *     or a stream the handle creates), in call order.
+ *
+ * Hash group (a reading of §3.1/§3.2, which ask only for "random hash
+ * functions"), fixed so every implementation agrees bit for bit:
+ *   splitmix64 (Steele, Lea, Flood 2014) seeded with
+ *   seed ^ (0x9E3779B97F4A7C15 * (dir + 1)) gives A0 (low 32 bits | 1),
+ *   A1 (| 1) and B1, per direction dir.
+ *   DH_0(x) = (A0 * x mod 2^32) >> (32 - k)                  (multiply-shift)
+ *   DH_i(x) = ((x >> (i-1)*alpha) mod 2^k) xor DH_0(x)       (Eq. 2; shifts
+ *             of 32 bits or more give 0)
+ *   H1(y)   = (A1 * y + B1 mod 2^64) >> (64 - log2 g)        (multiply-add-shift)
+ *   Direction 0 (outbound) keys on src and hashes dst; direction 1 (inbound)
+ *   keys on dst and hashes src.
+ */
+#ifndef SD_H
+#define SD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SD_OK 0
+#define SD_ERR_ARG (-1)             /* invalid argument or parameter set */
+#define SD_ERR_NOMEM (-2)           /* device or pinned host allocation failed */
+#define SD_ERR_CUDA (-3)            /* a CUDA call failed; see sd_last_error */
+#define SD_ERR_SATURATED (-4)       /* some row had ZR(i) = 0: psi = 1, Eq. 4 undefined */
+#define SD_ERR_OVERLOAD (-5)        /* restore work or candidates over their caps */
+#define SD_ERR_REPORT_OVERFLOW (-6) /* more hits than report_cap; count still exact */
+
+/* Per-direction flags, in sd_report.flags at bit offset 8*dir. */
+#define SD_FLAG_SATURATED 1u
+#define SD_FLAG_OVERLOAD_PAIRS 2u  /* |HE(0)| * |HE(1)| > pair_cap: restore skipped */
+#define SD_FLAG_OVERLOAD_CANDS 4u  /* |K| > cand_cap: candidates not kept */
+#define SD_FLAG_REPORT_OVERFLOW 8u /* hits beyond report_cap were dropped */
+
+typedef struct sd_handle sd_handle;
+
+/* Sketch and resource parameters.  A zero in a *_cap / stage field selects
+ * its default. */
+typedef struct {
+    uint32_t g;           /* bits per linear estimator: power of two, 32..4096 */
+    uint32_t r;           /* rows (LAs) per direction: 3..8 */
+    uint32_t k;           /* 2^k estimators per row: 1..24 */
+    uint32_t alpha;       /* bit-block stride of Eq. 2: 1 <= alpha <= k and
+                             (r-2)*alpha + k >= 32 (the two restrictions of §3.3) */
+    double theta;         /* super-point threshold (> 0) */
+    uint64_t seed;        /* seed of the hash constants */
+    uint32_t dirs;        /* 1: outbound (src keyed) only; 2: outbound and inbound */
+    int32_t device;       /* CUDA device ordinal */
+    uint64_t pair_cap;    /* restore is skipped (OVERLOAD) when |HE(0)|*|HE(1)| exceeds
+                             this; default 2^32 */
+    uint64_t cand_cap;    /* capacity for the candidate set K per direction;
+                             default 2^20 */
+    uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
+    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^23 */
+    void *cuda_stream;    /* cudaStream_t for all device work, or NULL for a
+                             handle-owned stream */
+} sd_params;
+
+/* One reported super point. */
+typedef struct {
+    uint32_t ip;       /* the host a0 */
+    uint32_t sz;       /* SZ(a0): zero bits of ULE(a0), the AND of its r estimators */
+    uint32_t dir;      /* 0 outbound (a0 was a src), 1 inbound (a0 was a dst) */
+    uint32_t reserved;
+    double est;        /* C(a0) of Eq. 4, computed in double on the host */
+} sd_hit;
+
+/* Result of one window.  Arrays are indexed [dir][row]; rows >= r and
+ * directions >= dirs are zero. */
+typedef struct {
+    uint64_t n_pairs;       /* pairs fed to the window */
+    uint64_t zr[2][8];      /* ZR(i): zero bits of row i (§3.3) */
+    double psi[2];          /* psi of Lemma 1 with w' averaged over rows; -1 if saturated */
+    uint32_t n_hot[2][8];   /* |HE(i)| */
+    uint64_t n_cand[2];     /* |K| = #{a : DH_i(a) in HE(i) for all i} */
+    uint32_t zhot;          /* largest z_0 that is hot (z_0 < Zmin = g e^(-theta/g)) */
+    uint32_t szmax[2];      /* largest SZ reported: C(SZ) >= theta and SZ <= zhot */
+    uint32_t flags;         /* SD_FLAG_* at bit 8*dir */
+    uint64_t n_hits_total;  /* hits found (exact even when truncated) */
+    uint64_t n_hits;        /* hits returned in `hits` (<= report_cap) */
+    const sd_hit *hits;     /* ordered by (dir, ip); owned by the handle, valid
+                               until the next sd_close_window or sd_destroy */
+} sd_report;
+
+/* Update-kernel launch knobs, chosen by the autotuner.  Zero fields keep the
+ * current value. */
+typedef struct {
+    uint32_t mode;          /* 0: one relaxed atomic OR per row;
+                               1: test the bit first (Algorithm 1's test), skip set bits;
+                               2: 1 + de-duplicate identical (word, bit) targets in a warp */
+    uint32_t block_threads; /* threads per block: 128..1024, multiple of 32 */
+    uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for */
+    uint32_t unroll;        /* 16-byte pair loads in flight per thread: 1, 2 or 4 */
+} sd_tuning;
+
+/* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,
+ * theta=1024, both directions, device 0) and default caps. */
+int sd_default_params(sd_params *p);
+
+/* Validate *p (§3.3 restrictions and layout limits); needs no GPU.
+ * Returns SD_OK or SD_ERR_ARG. */
+int sd_check_params(const sd_params *p);
+
+/* Words of one direction's DHLA: r * 2^k * g/32.  Layout [row][estimator]
+ * [g/32] uint32 words; bit b of an estimator is word b>>5, bit b&31.  0 if
+ * *p is invalid. */
+uint64_t sd_grid_words(const sd_params *p);
+
+/* Device bytes a handle with *p allocates (DHLA, restore scratch, ingest
+ * staging); 0 if *p is invalid. */
+uint64_t sd_device_bytes(const sd_params *p);
+
+/* Create a handle: allocate a zeroed DHLA per direction and the scratch
+ * of the close path on p->device.  *out is set only on success. */
+int sd_create(const sd_params *p, sd_handle **out);
+
+/* Algorithm 1 over n pairs.  `pairs` holds n (src, dst) uint32 pairs,
+ * interleaved (2n words), 4-byte aligned.  A device pointer is read in
+ * place and the call returns once the work is queued: the buffer must stay
+ * valid until the stream has executed it (sd_sync, or any later blocking
+ * call on the handle).  A host pointer (pinned or pageable) is copied in
+ * chunks of stage_pairs through the handle's staging buffers, and the call
+ * returns once the caller's buffer may be reused.  n = 0 is a no-op. */
+int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n);
+
+/* Close the window (Algorithm 2 with the §4.2 estimation step): per
+ * direction compute z_0 and ZR(i), the hot sets HE(i), psi, the candidate
+ * set K, SZ and C for each candidate, and report a0 when C(a0) >= theta.
+ * Blocks until the report is ready, then clears the DHLA (asynchronously, in
+ * stream order).  Returns SD_OK, or SD_ERR_SATURATED / SD_ERR_OVERLOAD /
+ * SD_ERR_REPORT_OVERFLOW with *out still filled (flags say which direction);
+ * the window is closed in every one of these cases. */
+int sd_close_window(sd_handle *h, sd_report *out);
+
+/* Wait for all work queued on the handle's stream. */
+int sd_sync(sd_handle *h);
+
+/* Release every resource of the handle.  NULL is a no-op. */
+int sd_destroy(sd_handle *h);
+
+/* Message of the last error on h (or of the last failed sd_create when h is
+ * NULL).  Owned by the library. */
+const char *sd_last_error(const sd_handle *h);
+
+/* Copy direction dir's DHLA (sd_grid_words words) to / from host memory.
+ * Used for checkpoints and parity checks; both block. */
+int sd_get_grid(sd_handle *h, uint32_t dir, uint32_t *host_dst);
+int sd_set_grid(sd_handle *h, uint32_t dir, const uint32_t *host_src);
+
+/* After a close: row `row`'s hot bitmap of direction dir (2^k bits, packed
+ * LSB-first into ceil(2^k/32) words) as of that close. */
+int sd_get_hot(sd_handle *h, uint32_t dir, uint32_t row, uint32_t *host_bitmap);
+
+/* After a close: copy up to `cap` members of direction dir's candidate set K
+ * (unordered) into host_dst and return |K| (>= 0), or a negative error. */
+int64_t sd_get_candidates(sd_handle *h, uint32_t dir, uint32_t *host_dst, uint64_t cap);
+
+/* OR src's DHLAs into dst's (same g, r, k, alpha, seed, dirs and device).
+ * This is the merge of local DHLAs from several monitors in §4.2, read as a
+ * bitwise OR: the merged DHLA equals the one built from the union of the
+ * streams.  Stream-ordered after the work already queued on both handles. */
+int sd_merge(sd_handle *dst, sd_handle *src);
+
+/* Read or change the update-kernel launch knobs. */
+int sd_get_tuning(const sd_handle *h, sd_tuning *out);
+int sd_set_tuning(sd_handle *h, const sd_tuning *t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SD_H */

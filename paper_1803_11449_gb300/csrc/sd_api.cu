@@ -1,0 +1,601 @@
+// sd_api.cu -- the C ABI declared in include/sd.h: handle lifetime, host
+// ingest, and the orchestration of the close path.
+//
+// The host evaluates the few per-window scalars in double: Zmin and the
+// integer hot threshold zhot (Algorithm 2), psi (Lemma 1 with the w(i)'
+// average of §3.3), the largest SZ that Eq. 4 still reports (szmax), and
+// Eq. 4 itself for each reported host.  These are evaluated exactly as the
+// paper writes them, in IEEE double with step-by-step rounding
+// (-ffp-contract=off), so every implementation that follows the same
+// formulas with the same libm agrees bit for bit.  All per-pair, per-
+// estimator and per-candidate work runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sd.h"
+#include "sd_common.cuh"
+
+using namespace sd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// splitmix64 (Steele, Lea, Flood 2014): the published generator.
+uint64_t splitmix64(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint32_t inverse_odd(uint32_t a) {  // Newton: x <- x(2 - a x) doubles correct bits
+    uint32_t x = a;
+    for (int i = 0; i < 5; i++) x *= 2u - a * x;
+    return x;
+}
+
+uint32_t ilog2(uint32_t v) {
+    uint32_t l = 0;
+    while ((1u << l) < v) l++;
+    return l;
+}
+
+uint64_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Algorithm 2: Zmin = g e^(-theta/g); the largest integer z with z < Zmin.
+int zhot_of(uint32_t g, double theta) {
+    const double Zmin = (double)g * exp(-theta / (double)g);
+    double f = floor(Zmin);
+    if (f >= Zmin) f -= 1.0;
+    if (f > (double)g) f = (double)g;
+    if (f < -1.0) f = -1.0;
+    return (int)f;
+}
+
+// Lemma 1 with w' the mean of w(i)' = -g 2^k ln(ZR(i)/(g 2^k)) (§3.3).
+// -1 when a row is saturated.
+double psi_of(uint32_t g, uint32_t r, uint32_t k, const unsigned long long *zr) {
+    const double G = (double)g * (double)((uint64_t)1 << k);
+    double wsum = 0.0;
+    for (uint32_t i = 0; i < r; i++) {
+        if (zr[i] == 0) return -1.0;
+        const double wi = -G * log((double)zr[i] / G);
+        wsum += wi;
+    }
+    const double w = wsum / (double)r;
+    return 1.0 - exp(-w / G);
+}
+
+// Eq. 4: C(a0) = -g ln(SZ(a0) / (g - g psi^r)).
+double eq4(uint32_t g, uint32_t r, double psi, uint32_t sz) {
+    const double gd = (double)g;
+    return -gd * log((double)sz / (gd - gd * pow(psi, (double)r)));
+}
+
+// Largest SZ in [0, g] that Algorithm 2 reports (C(SZ) >= theta); -1 if none.
+// C decreases in SZ, so the reported values form a prefix [0, szmax].
+int szmax_of(uint32_t g, uint32_t r, double psi, double theta) {
+    auto pass = [&](uint32_t s) { return eq4(g, r, psi, s) >= theta; };
+    if (!pass(0)) return -1;
+    if (pass(g)) return (int)g;
+    uint32_t lo = 0, hi = g;  // pass(lo), !pass(hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (pass(mid)) lo = mid;
+        else hi = mid;
+    }
+    return (int)lo;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct sd_handle {
+    sd_params p{};
+    Geometry G{};
+    Tuning T{};
+    int num_sms = 0;
+    int zhot = -1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;
+
+    uint32_t *grid = nullptr;          // [dirs][r][2^k][g/32]
+    StatBlock *st_d = nullptr;
+    StatBlock *st_h = nullptr;         // pinned
+    uint32_t *hotmap = nullptr;        // [dirs][r][2^k/32]
+    uint32_t *he = nullptr;            // [dirs][2][2^k]
+    uint32_t *cand = nullptr;          // [dirs][cand_cap]
+    unsigned long long *hits = nullptr;   // [dirs][hits_cap]
+    unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
+    uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
+    std::vector<unsigned long long> big_h;
+    std::vector<sd_hit> report;
+    uint64_t last_ncand[2] = {0, 0};
+    bool have_close = false;
+
+    uint64_t stage_pairs = 0;
+    uint32_t *dstage[2] = {nullptr, nullptr};
+    uint32_t *hstage[2] = {nullptr, nullptr};  // pinned
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr};
+    cudaEvent_t ev_kern[2] = {nullptr, nullptr};
+    uint64_t n_pairs = 0;
+    std::string err;
+
+    int fail(int code, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+};
+
+#define SD_CK(h, call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return (h)->fail(e_ == cudaErrorMemoryAllocation ? SD_ERR_NOMEM : SD_ERR_CUDA,     \
+                             "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+extern "C" {
+
+int sd_default_params(sd_params *p) {
+    if (!p) return SD_ERR_ARG;
+    std::memset(p, 0, sizeof *p);
+    p->g = 512;
+    p->r = 4;
+    p->k = 16;
+    p->alpha = 8;
+    p->theta = 1024.0;
+    p->seed = 0x5D5A0002ull;
+    p->dirs = 2;
+    p->device = 0;
+    return SD_OK;
+}
+
+int sd_check_params(const sd_params *p) {
+    if (!p) return SD_ERR_ARG;
+    if (p->g < 32 || p->g > 4096 || (p->g & (p->g - 1))) return SD_ERR_ARG;
+    if (p->r < 3 || p->r > (uint32_t)kMaxRows) return SD_ERR_ARG;
+    if (p->k < 1 || p->k > 24) return SD_ERR_ARG;
+    if (p->alpha < 1 || p->alpha > p->k) return SD_ERR_ARG;       // alpha <= k
+    if ((p->r - 2) * p->alpha + p->k < 32) return SD_ERR_ARG;      // (r-2) alpha + k >= 32
+    if (p->dirs < 1 || p->dirs > 2) return SD_ERR_ARG;
+    if (!(p->theta > 0.0) || !std::isfinite(p->theta)) return SD_ERR_ARG;
+    if (p->device < 0) return SD_ERR_ARG;
+    return SD_OK;
+}
+
+uint64_t sd_grid_words(const sd_params *p) {
+    if (sd_check_params(p) != SD_OK) return 0;
+    return (uint64_t)p->r * ((uint64_t)1 << p->k) * (p->g / 32);
+}
+
+static void resolve_caps(const sd_params *p, uint64_t *pair_cap, uint64_t *cand_cap, uint64_t *hits_cap,
+                         uint64_t *report_cap, uint64_t *stage) {
+    *pair_cap = p->pair_cap ? p->pair_cap : (1ull << 32);
+    *cand_cap = p->cand_cap ? p->cand_cap : (1ull << 20);
+    *hits_cap = next_pow2(*cand_cap);
+    *report_cap = p->report_cap ? p->report_cap : (uint64_t)p->dirs * *cand_cap;
+    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 23);
+}
+
+uint64_t sd_device_bytes(const sd_params *p) {
+    if (sd_check_params(p) != SD_OK) return 0;
+    uint64_t pc, cc, hc, rc, sp;
+    resolve_caps(p, &pc, &cc, &hc, &rc, &sp);
+    const uint64_t cells = (uint64_t)p->r << p->k;
+    return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + hc * 8) +
+           sizeof(StatBlock) + 2 * sp * 8;
+}
+
+static void release(sd_handle *h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    cudaFree(h->grid);
+    cudaFree(h->st_d);
+    cudaFree(h->hotmap);
+    cudaFree(h->he);
+    cudaFree(h->cand);
+    cudaFree(h->hits);
+    cudaFreeHost(h->st_h);
+    cudaFreeHost(h->hits_h);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(h->dstage[b]);
+        cudaFreeHost(h->hstage[b]);
+        if (h->ev_h2d[b]) cudaEventDestroy(h->ev_h2d[b]);
+        if (h->ev_kern[b]) cudaEventDestroy(h->ev_kern[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+static int create_impl(const sd_params *p, sd_handle *h) {
+    h->p = *p;
+    Geometry &G = h->G;
+    G.g = p->g;
+    G.r = p->r;
+    G.k = p->k;
+    G.alpha = p->alpha;
+    G.dirs = p->dirs;
+    G.lg = ilog2(p->g);
+    G.wpc = p->g / 32;
+    G.row_words = ((uint64_t)1 << p->k) * G.wpc;
+    G.dir_words = (uint64_t)p->r * G.row_words;
+    for (uint32_t d = 0; d < 2; d++) {
+        uint64_t st = p->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(d + 1));
+        G.h[d].A0 = (uint32_t)splitmix64(&st) | 1u;
+        G.h[d].A1 = splitmix64(&st) | 1ull;
+        G.h[d].B1 = splitmix64(&st);
+        G.h[d].A0inv = inverse_odd(G.h[d].A0);
+    }
+    h->T = Tuning{0, 512, 0, 2};
+    h->zhot = zhot_of(p->g, p->theta);
+    resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
+
+    SD_CK(h, cudaSetDevice(p->device));
+    SD_CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (p->cuda_stream) {
+        h->stream = (cudaStream_t)p->cuda_stream;
+    } else {
+        SD_CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    SD_CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; b++) {
+        SD_CK(h, cudaEventCreateWithFlags(&h->ev_h2d[b], cudaEventDisableTiming));
+        SD_CK(h, cudaEventCreateWithFlags(&h->ev_kern[b], cudaEventDisableTiming));
+    }
+    const uint64_t words = (uint64_t)p->dirs * G.dir_words;
+    const uint64_t nw = ((uint64_t)1 << p->k) >> 5;
+    SD_CK(h, cudaMalloc(&h->grid, words * 4));
+    SD_CK(h, cudaMalloc(&h->st_d, sizeof(StatBlock)));
+    SD_CK(h, cudaMalloc(&h->hotmap, (uint64_t)p->dirs * p->r * nw * 4));
+    SD_CK(h, cudaMalloc(&h->he, (uint64_t)p->dirs * 2 * ((uint64_t)4 << p->k)));
+    SD_CK(h, cudaMalloc(&h->cand, (uint64_t)p->dirs * h->cand_cap * 4));
+    SD_CK(h, cudaMalloc(&h->hits, (uint64_t)p->dirs * h->hits_cap * 8));
+    SD_CK(h, cudaMallocHost(&h->st_h, sizeof(StatBlock)));
+    SD_CK(h, cudaMallocHost(&h->hits_h, (uint64_t)2 * kSortSmall * 8));
+    SD_CK(h, launch_reset(h->grid, words, h->st_d, h->num_sms, h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    return SD_OK;
+}
+
+int sd_create(const sd_params *p, sd_handle **out) {
+    if (!out) return SD_ERR_ARG;
+    if (sd_check_params(p) != SD_OK) {
+        g_create_error = "sd_create: invalid parameters (see sd_check_params)";
+        return SD_ERR_ARG;
+    }
+    sd_handle *h = new (std::nothrow) sd_handle();
+    if (!h) {
+        g_create_error = "sd_create: out of host memory";
+        return SD_ERR_NOMEM;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    const int rc = create_impl(p, h);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (rc != SD_OK) {
+        g_create_error = h->err;
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SD_OK;
+}
+
+static int ensure_staging(sd_handle *h) {
+    if (h->dstage[0]) return SD_OK;
+    for (int b = 0; b < 2; b++) {
+        SD_CK(h, cudaMalloc(&h->dstage[b], h->stage_pairs * 8));
+        SD_CK(h, cudaMallocHost(&h->hstage[b], h->stage_pairs * 8));
+    }
+    return SD_OK;
+}
+
+int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+    if (!h) return SD_ERR_ARG;
+    if (n == 0) return SD_OK;
+    if (!pairs) return h->fail(SD_ERR_ARG, "sd_update: pairs is NULL");
+    if ((uintptr_t)pairs & 3u) return h->fail(SD_ERR_ARG, "sd_update: pairs is not 4-byte aligned");
+    DeviceGuard dg(h->p.device);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, pairs) != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+        if (attr.type == cudaMemoryTypeDevice && attr.device != h->p.device)
+            return h->fail(SD_ERR_ARG, "sd_update: pairs live on device %d, handle on %d", attr.device,
+                           h->p.device);
+        SD_CK(h, launch_update(pairs, n, h->grid, h->G, h->T, h->num_sms, h->stream));
+        h->n_pairs += n;
+        return SD_OK;
+    }
+    // host memory: chunked, double-buffered H2D overlapped with the kernel
+    const bool pinned = attr.type == cudaMemoryTypeHost;
+    const int rc = ensure_staging(h);
+    if (rc != SD_OK) return rc;
+    uint64_t c = 0;
+    for (uint64_t off = 0; off < n; off += h->stage_pairs, c++) {
+        const uint64_t m = std::min(h->stage_pairs, n - off);
+        const int b = (int)(c & 1);
+        const void *src = pairs + 2 * off;
+        SD_CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_kern[b], 0));
+        if (!pinned) {
+            SD_CK(h, cudaEventSynchronize(h->ev_h2d[b]));
+            std::memcpy(h->hstage[b], src, m * 8);
+            src = h->hstage[b];
+        }
+        SD_CK(h, cudaMemcpyAsync(h->dstage[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream));
+        SD_CK(h, cudaEventRecord(h->ev_h2d[b], h->copy_stream));
+        SD_CK(h, cudaStreamWaitEvent(h->stream, h->ev_h2d[b], 0));
+        SD_CK(h, launch_update(h->dstage[b], m, h->grid, h->G, h->T, h->num_sms, h->stream));
+        SD_CK(h, cudaEventRecord(h->ev_kern[b], h->stream));
+    }
+    // the caller may reuse a pinned buffer only once its copies are done
+    if (pinned) SD_CK(h, cudaEventSynchronize(h->ev_h2d[(c - 1) & 1]));
+    h->n_pairs += n;
+    return SD_OK;
+}
+
+int sd_sync(sd_handle *h) {
+    if (!h) return SD_ERR_ARG;
+    DeviceGuard dg(h->p.device);
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    return SD_OK;
+}
+
+int sd_close_window(sd_handle *h, sd_report *out) {
+    if (!h || !out) return SD_ERR_ARG;
+    DeviceGuard dg(h->p.device);
+    std::memset(out, 0, sizeof *out);
+    const Geometry &G = h->G;
+    const uint32_t dirs = G.dirs;
+    h->report.clear();
+    h->last_ncand[0] = h->last_ncand[1] = 0;
+
+    // hot estimators and row statistics (Algorithm 2, first loop; §4.2)
+    SD_CK(h, launch_row_stats(h->grid, G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
+    SD_CK(h, launch_compact(h->hotmap, G, h->he, h->stream));
+    SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+
+    uint32_t flags = 0;
+    RestoreArgs A;
+    std::memset(&A, 0, sizeof A);
+    double psi[2] = {0.0, 0.0};
+    for (uint32_t d = 0; d < dirs; d++) {
+        for (uint32_t i = 0; i < G.r; i++) {
+            out->zr[d][i] = h->st_h->zr[d][i];
+            out->n_hot[d][i] = h->st_h->nhot[d][i];
+        }
+        psi[d] = psi_of(G.g, G.r, G.k, h->st_h->zr[d]);
+        out->psi[d] = psi[d];
+        if (psi[d] < 0.0) {
+            flags |= SD_FLAG_SATURATED << (8 * d);
+            continue;
+        }
+        const int szmax = szmax_of(G.g, G.r, psi[d], h->p.theta);
+        out->szmax[d] = szmax < 0 ? 0 : (uint32_t)szmax;
+        const uint64_t n0 = h->st_h->nhot[d][0], n1 = h->st_h->nhot[d][1];
+        if (n0 * n1 > h->pair_cap) {
+            flags |= SD_FLAG_OVERLOAD_PAIRS << (8 * d);
+            continue;
+        }
+        A.run[d] = 1;
+        A.n0[d] = (uint32_t)n0;
+        A.n1[d] = (uint32_t)n1;
+        A.szmax[d] = szmax;
+    }
+
+    if (A.run[0] || A.run[1]) {
+        // restore K and estimate each candidate (Algorithm 2 / Algorithms 3-4, §4.2)
+        A.grid = h->grid;
+        A.he = h->he;
+        A.hotmap = h->hotmap;
+        A.cand = h->cand;
+        A.hits = h->hits;
+        A.stats = h->st_d;
+        A.cand_cap = h->cand_cap;
+        A.hits_cap = h->hits_cap;
+        SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
+        SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, dirs, h->stream));
+        SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
+        for (uint32_t d = 0; d < dirs; d++)
+            if (A.run[d])
+                SD_CK(h, cudaMemcpyAsync(h->hits_h + (uint64_t)d * kSortSmall, h->hits + (uint64_t)d * h->hits_cap,
+                                         (uint64_t)kSortSmall * 8, cudaMemcpyDeviceToHost, h->stream));
+        SD_CK(h, cudaStreamSynchronize(h->stream));
+        for (uint32_t d = 0; d < dirs; d++) {
+            if (!A.run[d]) continue;
+            const uint64_t nk = h->st_h->ncand[d];
+            out->n_cand[d] = nk;
+            h->last_ncand[d] = nk;
+            if (nk > h->cand_cap) {
+                flags |= SD_FLAG_OVERLOAD_CANDS << (8 * d);
+                continue;
+            }
+            const uint64_t nh = h->st_h->nhits[d];
+            const unsigned long long *keys = h->hits_h + (uint64_t)d * kSortSmall;
+            if (h->st_h->big_sort[d]) {
+                unsigned long long *dk = h->hits + (uint64_t)d * h->hits_cap;
+                SD_CK(h, launch_sort_big(dk, nh, next_pow2(nh), h->num_sms, h->stream));
+                h->big_h.resize(nh);
+                SD_CK(h, cudaMemcpyAsync(h->big_h.data(), dk, nh * 8, cudaMemcpyDeviceToHost, h->stream));
+                SD_CK(h, cudaStreamSynchronize(h->stream));
+                keys = h->big_h.data();
+            }
+            for (uint64_t q = 0; q < nh; q++) {
+                sd_hit hit;
+                hit.ip = (uint32_t)(keys[q] >> 32);
+                hit.sz = (uint32_t)(keys[q] & 0xFFFFFFFFull);
+                hit.dir = d;
+                hit.reserved = 0;
+                hit.est = eq4(G.g, G.r, psi[d], hit.sz);
+                h->report.push_back(hit);
+            }
+        }
+    }
+    h->have_close = true;
+
+    // clear the DHLA and the counters for the next window (stream-ordered)
+    SD_CK(h, launch_reset(h->grid, (uint64_t)dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
+
+    out->n_hits_total = h->report.size();
+    if (h->report.size() > h->report_cap) {
+        for (uint64_t q = h->report_cap; q < h->report.size(); q++)
+            flags |= SD_FLAG_REPORT_OVERFLOW << (8 * h->report[q].dir);
+        h->report.resize(h->report_cap);
+    }
+    out->n_pairs = h->n_pairs;
+    h->n_pairs = 0;
+    out->zhot = (uint32_t)(h->zhot < 0 ? 0 : h->zhot);
+    out->flags = flags;
+    out->n_hits = h->report.size();
+    out->hits = h->report.empty() ? nullptr : h->report.data();
+
+    const uint32_t any = flags | (flags >> 8);
+    if (any & SD_FLAG_SATURATED) return h->fail(SD_ERR_SATURATED, "sd_close_window: a row is saturated (ZR = 0)");
+    if (any & (SD_FLAG_OVERLOAD_PAIRS | SD_FLAG_OVERLOAD_CANDS))
+        return h->fail(SD_ERR_OVERLOAD, "sd_close_window: restore over its pair or candidate cap");
+    if (any & SD_FLAG_REPORT_OVERFLOW)
+        return h->fail(SD_ERR_REPORT_OVERFLOW, "sd_close_window: more hits than report_cap");
+    return SD_OK;
+}
+
+int sd_destroy(sd_handle *h) {
+    if (!h) return SD_OK;
+    {
+        DeviceGuard dg(h->p.device);
+        release(h);
+    }
+    delete h;
+    return SD_OK;
+}
+
+const char *sd_last_error(const sd_handle *h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int sd_get_grid(sd_handle *h, uint32_t dir, uint32_t *host_dst) {
+    if (!h || !host_dst || dir >= h->G.dirs) return SD_ERR_ARG;
+    DeviceGuard dg(h->p.device);
+    SD_CK(h, cudaMemcpyAsync(host_dst, h->grid + (uint64_t)dir * h->G.dir_words, h->G.dir_words * 4,
+                             cudaMemcpyDeviceToHost, h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    return SD_OK;
+}
+
+int sd_set_grid(sd_handle *h, uint32_t dir, const uint32_t *host_src) {
+    if (!h || !host_src || dir >= h->G.dirs) return SD_ERR_ARG;
+    DeviceGuard dg(h->p.device);
+    SD_CK(h, cudaMemcpyAsync(h->grid + (uint64_t)dir * h->G.dir_words, host_src, h->G.dir_words * 4,
+                             cudaMemcpyHostToDevice, h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    return SD_OK;
+}
+
+int sd_get_hot(sd_handle *h, uint32_t dir, uint32_t row, uint32_t *host_bitmap) {
+    if (!h || !host_bitmap || dir >= h->G.dirs || row >= h->G.r) return SD_ERR_ARG;
+    if (!h->have_close) return h->fail(SD_ERR_ARG, "sd_get_hot: no window has been closed yet");
+    DeviceGuard dg(h->p.device);
+    const uint64_t nw = ((uint64_t)1 << h->G.k) >> 5;
+    SD_CK(h, cudaMemcpyAsync(host_bitmap, h->hotmap + ((uint64_t)dir * h->G.r + row) * nw, nw * 4,
+                             cudaMemcpyDeviceToHost, h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    return SD_OK;
+}
+
+int64_t sd_get_candidates(sd_handle *h, uint32_t dir, uint32_t *host_dst, uint64_t cap) {
+    if (!h || dir >= h->G.dirs || (cap && !host_dst)) return SD_ERR_ARG;
+    if (!h->have_close) return h->fail(SD_ERR_ARG, "sd_get_candidates: no window has been closed yet");
+    DeviceGuard dg(h->p.device);
+    const uint64_t nk = h->last_ncand[dir];
+    const uint64_t m = std::min(std::min(nk, h->cand_cap), cap);
+    if (m) {
+        SD_CK(h, cudaMemcpyAsync(host_dst, h->cand + (uint64_t)dir * h->cand_cap, m * 4, cudaMemcpyDeviceToHost,
+                                 h->stream));
+        SD_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return (int64_t)nk;
+}
+
+int sd_merge(sd_handle *dst, sd_handle *src) {
+    if (!dst || !src || dst == src) return SD_ERR_ARG;
+    const sd_params &a = dst->p, &b = src->p;
+    if (a.g != b.g || a.r != b.r || a.k != b.k || a.alpha != b.alpha || a.seed != b.seed || a.dirs != b.dirs ||
+        a.device != b.device)
+        return dst->fail(SD_ERR_ARG, "sd_merge: handles differ in shape, seed or device");
+    DeviceGuard dg(a.device);
+    cudaEvent_t ev;
+    SD_CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, src->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+    if (e == cudaSuccess)
+        e = launch_merge(dst->grid, src->grid, (uint64_t)a.dirs * dst->G.dir_words, dst->num_sms, dst->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, dst->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);  // src may not change until merged
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return dst->fail(SD_ERR_CUDA, "sd_merge: %s", cudaGetErrorString(e));
+    dst->n_pairs += src->n_pairs;
+    return SD_OK;
+}
+
+int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
+    if (!h || !out) return SD_ERR_ARG;
+    out->mode = h->T.mode;
+    out->block_threads = h->T.block_threads;
+    out->blocks_per_sm = h->T.blocks_per_sm;
+    out->unroll = h->T.unroll;
+    return SD_OK;
+}
+
+int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
+    if (!h || !t) return SD_ERR_ARG;
+    Tuning T = h->T;
+    if (t->mode > 2) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0, 1 or 2");
+    T.mode = t->mode;
+    if (t->block_threads) {
+        if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: block_threads must be a multiple of 32 in [64, 1024]");
+        T.block_threads = t->block_threads;
+    }
+    if (t->blocks_per_sm) T.blocks_per_sm = t->blocks_per_sm;
+    if (t->unroll) {
+        if (t->unroll != 1 && t->unroll != 2 && t->unroll != 4)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: unroll must be 1, 2 or 4");
+        T.unroll = t->unroll;
+    }
+    h->T = T;
+    return SD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,402 @@
+// sd_close.cu -- the window-close path (Algorithm 2 and the estimation step
+// of §4.2) on the GPU.
+//
+//   k_row_stats   z_0 = g - popcount for every estimator, ZR(i) per row, the
+//                 hot bitmap of each row (z_0 <= zhot, i.e. z_0 < Zmin) and
+//                 |HE(i)|.
+//   k_compact     sorted lists HE(0) and HE(1) from their bitmaps.
+//   k_restore     the candidate set K = {a : DH_i(a) in HE(i) for all i} and,
+//                 fused, SZ(a) from ULE(a) = AND of a's r estimators, keeping
+//                 (a, SZ) when SZ <= szmax.
+//   k_sort_small  orders each direction's hits by address (bitonic, smem).
+//   k_bitonic_*   the same for hit lists too large for one block.
+//   k_reset       clears the DHLA and the per-window counters.
+//   k_merge_or    dst |= src over whole DHLAs (multi-monitor merge).
+//
+// Restore.  The paper's GPU restore (Algorithms 3 and 4) joins HE(0) x HE(1)
+// x HE(2) and extends the surviving partial addresses row by row.  Here the
+// join stops after HE(0) x HE(1): with c0 = DH_0(a) and c1 = DH_1(a),
+// L = c0 xor c1 is the low k bits of a (Eq. 3 for i = 1), and because
+// DH_0(a) = (A0 a mod 2^32) >> (32-k) with A0 odd, the remaining 32-k high
+// bits H of a follow from c0 by one multiplication with A0^-1:
+//   write A0*L mod 2^32 = Qh*2^k + Ql; then A0*a mod 2^32 = u*2^k + Ql with
+//   u = (A0*H + Qh) mod 2^(32-k), and DH_0(a) = c0 fixes u:
+//     k >= 16: u = c0 >> (2k-32), provided (Ql >> (32-k)) equals the low
+//              2k-32 bits of c0 (otherwise no a exists);
+//     k <  16: u = (c0 << (32-2k)) | t for each t < 2^(32-2k).
+//   H = A0^-1 (u - Qh) mod 2^(32-k),  a = H*2^k + L.
+// Each a found this way has DH_0(a) = c0 and DH_1(a) = c1 by construction and
+// is kept when DH_i(a) is hot for i = 2..r-1: exactly K.  The work is
+// |HE(0)|*|HE(1)|*2^max(0,32-2k) cheap integer tests instead of a join whose
+// intermediate lists grow with |HE|^3.
+#include "sd_common.cuh"
+
+namespace sd {
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------- row stats
+// One thread per estimator; a warp covers 32 consecutive estimators of one
+// row (2^k >= 32 because (r-1)k >= (r-2)alpha + k >= 32 with r <= 8).
+__global__ void __launch_bounds__(256)
+k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *__restrict__ hotmap,
+            StatBlock *__restrict__ st) {
+    const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ncell; q += stride) {
+        const uint32_t *cell = grid + q * G.wpc;
+        uint32_t pop = 0;
+        if ((G.wpc & 3u) == 0) {
+            const uint4 *c4 = reinterpret_cast<const uint4 *>(cell);
+            for (uint32_t w = 0; w < G.wpc / 4; w++) {
+                const uint4 v = __ldg(c4 + w);
+                pop += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        } else {
+            for (uint32_t w = 0; w < G.wpc; w++) pop += __popc(__ldg(cell + w));
+        }
+        const uint32_t z0 = G.g - pop;
+        const unsigned hot = __ballot_sync(0xFFFFFFFFu, (int)z0 <= zhot);
+        const uint32_t zsum = warp_sum(z0);
+        if (lane == 0) {
+            const uint64_t row = q >> G.k;  // dir * r + i
+            hotmap[q >> 5] = hot;
+            atomicAdd(&st->zr[0][0] + (row / G.r) * kMaxRows + row % G.r, (unsigned long long)zsum);
+            if (hot) atomicAdd(&st->nhot[0][0] + (row / G.r) * kMaxRows + row % G.r, (unsigned)__popc(hot));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- compact
+// One block per (dir, row in {0, 1}): HE(row) in ascending order.
+__global__ void __launch_bounds__(1024)
+k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict__ he) {
+    const uint32_t dir = blockIdx.x >> 1, row = blockIdx.x & 1u;
+    const uint32_t nw = (1u << G.k) >> 5;
+    const uint32_t *bm = hotmap + ((uint64_t)dir * G.r + row) * nw;
+    uint32_t *out = he + ((uint64_t)dir * 2 + row) * (1ull << G.k);
+    const uint32_t per = (nw + blockDim.x - 1) / blockDim.x;
+    const uint32_t w0 = threadIdx.x * per;
+    const uint32_t w1 = min(w0 + per, nw);
+    uint32_t cnt = 0;
+    for (uint32_t w = w0; w < w1; w++) cnt += __popc(bm[w]);
+    // block exclusive scan of cnt
+    __shared__ uint32_t warp_tot[32];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t nwarps = blockDim.x >> 5;
+        uint32_t t = lane < nwarps ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if ((int)lane >= o) t += v;
+        }
+        if (lane < nwarps) warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t pos = incl - cnt + (wid ? warp_tot[wid - 1] : 0);
+    for (uint32_t w = w0; w < w1; w++) {
+        uint32_t b = bm[w];
+        while (b) {
+            const uint32_t bit = __ffs(b) - 1;
+            b &= b - 1u;
+            out[pos++] = (w << 5) | bit;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- restore
+__device__ __forceinline__ bool hot_at(const uint32_t *bm_row, uint32_t c) {
+    return (bm_row[c >> 5] >> (c & 31u)) & 1u;
+}
+
+__global__ void __launch_bounds__(256)
+k_restore(Geometry G, RestoreArgs A) {
+    extern __shared__ uint32_t smem[];
+    // per-direction scalars picked with selects: indexing the parameter
+    // arrays with a run-time index would copy them to local memory
+    const uint32_t dir = blockIdx.y;
+    if (!(dir ? A.run[1] : A.run[0])) return;
+    const uint32_t n0 = dir ? A.n0[1] : A.n0[0];
+    const uint32_t n1 = dir ? A.n1[1] : A.n1[0];
+    const int szmax = dir ? A.szmax[1] : A.szmax[0];
+    if (n0 == 0 || n1 == 0) return;
+    const uint32_t k = G.k, kmask = (1u << k) - 1u;
+    const uint32_t hmask = (k >= 32u) ? 0u : ((1u << (32u - k)) - 1u);  // 32-k high bits
+    const uint32_t nw = (1u << k) >> 5;
+    const uint32_t A0 = dir ? G.h[1].A0 : G.h[0].A0;
+    const uint32_t A0inv = dir ? G.h[1].A0inv : G.h[0].A0inv;
+    const uint32_t *he0 = A.he + (uint64_t)dir * 2 * (1ull << k);
+    const uint32_t *he1 = he0 + (1ull << k);
+    const uint32_t *bm_dir = A.hotmap + (uint64_t)dir * G.r * nw;  // row i at bm_dir + i*nw
+
+    // rows 2..r-1 of the hot bitmap; row i is at hot2 + (i-2)*nw
+    const uint32_t *hot2 = bm_dir + 2 * nw;
+    uint32_t *tile = smem;
+    if (A.smem_hot) {
+        uint32_t *sb = smem + A.tile0;
+        const uint32_t words = (G.r - 2) * nw;
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sb[w] = hot2[w];
+        hot2 = sb;
+    }
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t J = (uint64_t)n1 << A.ulog;
+    const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
+    const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
+    const uint64_t ntiles = (uint64_t)ntile0 * nchunk;
+    const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
+    const uint32_t lowbits = (k >= 16u) ? (2u * k - 32u) : 0u;
+    const uint32_t lowmask = (1u << lowbits) - 1u;
+    const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
+
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t t0 = (uint32_t)(t / nchunk);
+        const uint64_t jc = t % nchunk;
+        const uint32_t c0_base = t0 * A.tile0;
+        const uint32_t nc0 = min(A.tile0, n0 - c0_base);
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nc0; q += blockDim.x) tile[q] = he0[c0_base + q];
+        __syncthreads();
+        for (uint32_t m = 0; m < iters; m++) {
+            const uint64_t j = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
+            const bool jvalid = j < J;
+            const uint32_t i1 = (uint32_t)(j >> A.ulog);
+            const uint32_t tt = (uint32_t)(j & ((1ull << A.ulog) - 1ull));
+            const uint32_t c1 = jvalid ? he1[i1] : 0u;
+            for (uint32_t q = 0; q < nc0; q++) {
+                const uint32_t c0 = tile[q];
+                const uint32_t L = c0 ^ c1;                 // BL(1): the low k bits of a
+                const uint32_t Q = A0 * L;
+                const uint32_t Qh = Q >> k, Ql = Q & kmask;
+                bool found = jvalid;
+                uint32_t u;
+                if (k >= 16u) {
+                    found = found && ((Ql >> (32u - k)) == (c0 & lowmask));
+                    u = c0 >> lowbits;
+                } else {
+                    u = (c0 << (32u - 2u * k)) | tt;
+                }
+                const uint32_t H = (A0inv * ((u - Qh) & hmask)) & hmask;
+                const uint32_t a = (H << k) | L;
+                for (uint32_t i = 2; i < G.r && found; i++)
+                    found = hot_at(hot2 + (uint64_t)(i - 2) * nw, dh_row(G, i, a, c0));
+                const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
+                if (!fb) continue;
+                // append the candidates of this warp to K
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&A.stats->ncand[dir], (unsigned long long)__popc(fb));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (found) {
+                    const unsigned long long slot = base + __popc(fb & ((1u << lane) - 1u));
+                    if (slot < A.cand_cap) A.cand[(uint64_t)dir * A.cand_cap + slot] = a;
+                }
+                // SZ of each candidate, one warp-wide AND + popcount at a time
+                unsigned rest = fb;
+                while (rest) {
+                    const int src = __ffs(rest) - 1;
+                    rest &= rest - 1u;
+                    const uint32_t x = __shfl_sync(0xFFFFFFFFu, a, src);
+                    uint32_t ones = 0;
+                    for (uint32_t w = lane; w < G.wpc; w += 32) {
+                        uint32_t ule = 0xFFFFFFFFu;
+                        for (uint32_t i = 0; i < G.r; i++) {
+                            const uint32_t ci = (i == 0) ? c0 : dh_row(G, i, x, c0);
+                            ule &= __ldg(gdir + (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc + w);
+                        }
+                        ones += __popc(ule);
+                    }
+                    ones = warp_sum(ones);
+                    const uint32_t SZ = G.g - ones;
+                    if (lane == 0 && (int)SZ <= szmax) {
+                        const unsigned long long slot = atomicAdd(&A.stats->nhits[dir], 1ull);
+                        if (slot < A.hits_cap)
+                            A.hits[(uint64_t)dir * A.hits_cap + slot] =
+                                ((unsigned long long)x << 32) | SZ;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------- sort
+__device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long &b, bool up) {
+    if ((a > b) == up) {
+        const unsigned long long t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// One block per direction: bitonic sort of up to kSortSmall hits in shared
+// memory (padding with all-ones keys, which sort last).
+__global__ void __launch_bounds__(1024)
+k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 run) {
+    extern __shared__ unsigned long long s[];  // kSortSmall keys
+    const uint32_t dir = blockIdx.x;
+    if (!(dir ? run.y : run.x)) return;
+    const unsigned long long n = st->nhits[dir];
+    const unsigned long long nn = n < hits_cap ? n : hits_cap;
+    if (nn > (unsigned long long)kSortSmall) {
+        if (threadIdx.x == 0) st->big_sort[dir] = 1;
+        return;
+    }
+    if (nn <= 1) return;
+    unsigned P = 2;
+    while (P < nn) P <<= 1;
+    unsigned long long *hd = hits + (uint64_t)dir * hits_cap;
+    for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < nn ? hd[i] : ~0ull;
+    __syncthreads();
+    for (unsigned kk = 2; kk <= P; kk <<= 1) {
+        for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+            for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
+                const unsigned ix = i ^ j;
+                if (ix > i) cswap(s[i], s[ix], (i & kk) == 0);
+            }
+            __syncthreads();
+        }
+    }
+    for (unsigned i = threadIdx.x; i < nn; i += blockDim.x) hd[i] = s[i];
+}
+
+__global__ void k_pad(unsigned long long *keys, uint64_t from, uint64_t to) {
+    for (uint64_t i = from + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < to;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        keys[i] = ~0ull;
+}
+
+// One compare-exchange stage (kk, j) of a bitonic sort over P keys in global
+// memory.
+__global__ void k_bitonic_step(unsigned long long *keys, uint64_t P, uint64_t kk, uint64_t j) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t ix = i ^ j;
+        if (ix > i) {
+            unsigned long long a = keys[i], b = keys[ix];
+            const bool up = (i & kk) == 0;
+            if ((a > b) == up) {
+                keys[i] = b;
+                keys[ix] = a;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ reset/merge
+__global__ void k_reset(uint4 *grid4, uint64_t n4, StatBlock *st) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+        grid4[i] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x == 0) {
+        uint32_t *w = reinterpret_cast<uint32_t *>(st);
+        for (uint32_t i = threadIdx.x; i < sizeof(StatBlock) / 4; i += blockDim.x) w[i] = 0;
+    }
+}
+
+__global__ void k_merge_or(uint4 *dst, const uint4 *__restrict__ src, uint64_t n4) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 a = dst[i], b = __ldg(src + i);
+        dst[i] = make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static unsigned grid_for(uint64_t items, unsigned threads, int num_sms, unsigned per_sm) {
+    uint64_t b = (items + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)num_sms * per_sm;
+    if (b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, uint32_t *hotmap,
+                             StatBlock *st, int num_sms, cudaStream_t s) {
+    const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
+    k_row_stats<<<grid_for(ncell, 256, num_sms, 8), 256, 0, s>>>(grid, G, zhot, hotmap, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, cudaStream_t s) {
+    k_compact<<<G.dirs * 2, 1024, 0, s>>>(hotmap, G, he);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
+    const unsigned threads = 256;
+    A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
+    A.tile0 = 32;
+    A.jchunk = threads * 8;
+    const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
+    size_t smem = A.tile0 * 4;
+    A.smem_hot = (hot_bytes + smem) <= (size_t)200 * 1024;
+    if (A.smem_hot) smem += hot_bytes;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_restore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    uint64_t most = 0;
+    for (uint32_t d = 0; d < G.dirs; d++) {
+        if (!A.run[d]) continue;
+        const uint64_t t0 = (A.n0[d] + A.tile0 - 1) / A.tile0;
+        const uint64_t nc = (((uint64_t)A.n1[d] << A.ulog) + A.jchunk - 1) / A.jchunk;
+        if (t0 * nc > most) most = t0 * nc;
+    }
+    if (most == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_restore, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)num_sms * per_sm;
+    if (most < blocks) blocks = most;
+    dim3 grid((unsigned)blocks, G.dirs);
+    k_restore<<<grid, threads, smem, s>>>(G, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
+                              const uint32_t run[2], uint32_t dirs, cudaStream_t s) {
+    const int smem = kSortSmall * (int)sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_sort_small<<<dirs, 1024, smem, s>>>(hits, hits_cap, st, make_uint2(run[0], run[1]));
+    return cudaGetLastError();
+}
+
+// Sort keys[0, n) ascending; keys has room for P >= n entries (P a power of
+// two).  Used only when a direction has more than kSortSmall hits.
+cudaError_t launch_sort_big(unsigned long long *keys, uint64_t n, uint64_t P, int num_sms, cudaStream_t s) {
+    const unsigned blocks = grid_for(P, 256, num_sms, 8);
+    k_pad<<<blocks, 256, 0, s>>>(keys, n, P);
+    for (uint64_t kk = 2; kk <= P; kk <<= 1)
+        for (uint64_t j = kk >> 1; j > 0; j >>= 1) k_bitonic_step<<<blocks, 256, 0, s>>>(keys, P, kk, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s) {
+    const uint64_t n4 = words / 4;
+    k_reset<<<grid_for(n4, 256, num_sms, 8), 256, 0, s>>>(reinterpret_cast<uint4 *>(grid), n4, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s) {
+    const uint64_t n4 = words / 4;
+    k_merge_or<<<grid_for(n4, 256, num_sms, 8), 256, 0, s>>>(reinterpret_cast<uint4 *>(dst),
+                                                            reinterpret_cast<const uint4 *>(src), n4);
+    return cudaGetLastError();
+}
+
+}  // namespace sd

@@ -1,0 +1,133 @@
+// sd_common.cuh -- types and device helpers shared by the library's
+// translation units (update, close, C ABI).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sd {
+
+constexpr int kMaxRows = 8;
+
+// Hash constants of one direction (see include/sd.h for the definitions).
+struct HashDir {
+    uint32_t A0;     // odd multiplier of DH_0
+    uint32_t A0inv;  // its inverse mod 2^32 (restore)
+    uint64_t A1;     // odd multiplier of H1
+    uint64_t B1;     // additive constant of H1
+};
+
+// Shape of one handle's DHLA plus its hash constants, passed by value to
+// every kernel.
+struct Geometry {
+    uint32_t g, r, k, alpha, dirs;
+    uint32_t lg;          // log2 g
+    uint32_t wpc;         // 32-bit words per estimator, g / 32
+    uint64_t row_words;   // 2^k * wpc
+    uint64_t dir_words;   // r * row_words
+    HashDir h[2];
+};
+
+struct Tuning {
+    uint32_t mode;           // 0 plain, 1 test-then-set, 2 test + warp de-dup
+    uint32_t block_threads;
+    uint32_t blocks_per_sm;
+    uint32_t unroll;
+};
+
+constexpr int kSortSmall = 8192;  // hits per direction sorted in one block
+
+// Per-window counters, copied to the host in one transfer.
+struct StatBlock {
+    unsigned long long zr[2][kMaxRows];
+    unsigned long long ncand[2];
+    unsigned long long nhits[2];
+    unsigned int nhot[2][kMaxRows];
+    unsigned int big_sort[2];  // 1: hits did not fit the one-block sort
+    unsigned int pad[2];
+};
+
+struct RestoreArgs {
+    const uint32_t *grid;
+    const uint32_t *he;      // [dirs][2][2^k]
+    const uint32_t *hotmap;  // [dirs][r][2^k/32]
+    uint32_t *cand;          // [dirs][cand_cap]
+    unsigned long long *hits;  // [dirs][hits_cap]: (a << 32) | SZ
+    StatBlock *stats;
+    uint64_t cand_cap, hits_cap;
+    uint32_t n0[2], n1[2];
+    int32_t szmax[2];        // largest reported SZ; -1: none
+    uint32_t run[2];
+    uint32_t ulog;           // log2 of the preimage count per (c0, c1): max(0, 32-2k)
+    uint32_t tile0;          // c0 values per block tile
+    uint32_t jchunk;         // (c1, t) items per block tile
+    int smem_hot;            // rows 2..r-1 of the hot bitmap staged in shared memory
+};
+
+// ---------------------------------------------------------------- hashes
+// DH_0(x) = (A0 x mod 2^32) >> (32 - k)
+__device__ __forceinline__ uint32_t dh0(uint32_t A0, uint32_t k, uint32_t x) {
+    return (A0 * x) >> (32u - k);
+}
+
+// (x >> s) for s <= 31, 0 for s >= 32 (funnel shift with clamp).
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t s) {
+    return __funnelshift_rc(x, 0u, s);
+}
+
+// Eq. 2 for i >= 1, given DH_0(x) = c0.  The shift (i-1)*alpha is formed
+// in registers (indexing a kernel-parameter array with a run-time row would
+// copy the whole parameter block to local memory).
+__device__ __forceinline__ uint32_t dh_row(const Geometry &G, uint32_t i, uint32_t x, uint32_t c0) {
+    return (shr_clamp(x, (i - 1u) * G.alpha) & ((1u << G.k) - 1u)) ^ c0;
+}
+
+// H1(y) = (A1 y + B1 mod 2^64) >> (64 - log2 g)
+__device__ __forceinline__ uint32_t h1(const HashDir &h, uint32_t lg, uint32_t y) {
+    return (uint32_t)((h.A1 * (uint64_t)y + h.B1) >> (64u - lg));
+}
+
+// ------------------------------------------------------------ memory ops
+// 16-byte streaming load of the pair stream: read once, do not keep in L1.
+__device__ __forceinline__ uint4 ld_stream_v4(const uint4 *p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t *p) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Relaxed device-scope bitwise OR with no return value (a reduction).  Bits
+// only ever go 0 -> 1 within a window, so no ordering is needed.
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Weak cached load of a DHLA word.  A stale 0 only costs a redundant OR; a
+// stale 1 cannot happen because bits are never cleared inside a window.
+__device__ __forceinline__ uint32_t ld_weak(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_update(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                          const Tuning &T, int num_sms, cudaStream_t s);
+cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, uint32_t *hotmap,
+                             StatBlock *st, int num_sms, cudaStream_t s);
+cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, cudaStream_t s);
+cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
+cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
+                              const uint32_t run[2], uint32_t dirs, cudaStream_t s);
+cudaError_t launch_sort_big(unsigned long long *keys, uint64_t n, uint64_t P, int num_sms, cudaStream_t s);
+cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
+cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
+
+}  // namespace sd

@@ -1,0 +1,351 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer results (DHLA bits, ZR, hot sets, |K|, K, reported addresses, SZ)
+must be identical; psi and the Eq. 4 estimates are evaluated from identical
+integers by the same double formulas on the host and must be bit-identical
+too.  Inputs come from the seeded traffic generator only.
+"""
+import numpy as np
+import pytest
+
+from paper_1803_11449_gb300 import traffic as T
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED5EED
+
+
+@pytest.fixture(scope="module")
+def sd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd as mod
+    mod.lib()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _oracle_run(O, w, pairs, seed, **caps):
+    op = O.params_from(w.sketch(), seed=seed, **caps)
+    og = O.new_grid(op)
+    O.update(op, og, pairs)
+    ref = O.close_window(op, og, want_cands=True)
+    return op, og, ref
+
+
+def _dev(torch_mod, pairs):
+    return torch_mod.from_numpy(np.ascontiguousarray(pairs).reshape(-1).view(np.int32)).cuda()
+
+
+def _grids(sd, h):
+    return np.concatenate([sd.sd_get_grid(h, d) for d in range(h.params.dirs)])
+
+
+def _assert_report_equal(O, rep, ref, p):
+    assert rep.n_cand == ref["n_cand"]
+    assert [rep.dir_flags(d) for d in range(p.dirs)] == ref["flags"]
+    assert np.array_equal(rep.zr, ref["zr"])
+    assert np.array_equal(rep.n_hot, ref["n_hot"])
+    assert rep.psi == ref["psi"]
+    assert rep.n_hits_total == ref["n_hits"]
+    assert np.array_equal(rep.hits["dir"], ref["dir"])
+    assert np.array_equal(rep.hits["ip"], ref["ip"])
+    assert np.array_equal(rep.hits["sz"], ref["sz"])
+    assert np.array_equal(rep.hits["est"], ref["est"])   # bit-exact doubles
+
+
+def _full_check(sd, O, torch_mod, w, win, seed=SEED, tuning=None, **caps):
+    p = sd.params_for(w, seed, cuda_stream=torch_mod.cuda.current_stream().cuda_stream, **caps)
+    h = sd.sd_create(p)
+    try:
+        if tuning:
+            sd.sd_set_tuning(h, **tuning)
+        sd.sd_update(h, _dev(torch_mod, win.pairs))
+        grid = _grids(sd, h)
+        rep = sd.sd_close_window(h)
+        hot = [[sd.sd_get_hot(h, d, i) for i in range(p.r)] for d in range(p.dirs)]
+        cands = [sd.sd_get_candidates(h, d) for d in range(p.dirs)]
+        after = _grids(sd, h)
+    finally:
+        sd.sd_destroy(h)
+    op, og, ref = _oracle_run(O, w, win.pairs, seed, **caps)
+    assert np.array_equal(grid, og), "DHLA bits differ"
+    assert not after.any(), "DHLA not cleared by the close"
+    _assert_report_equal(O, rep, ref, p)
+    for d in range(p.dirs):
+        z0, _ = O.row_stats(op, og, d)
+        he, nhe = O.hot_sets(op, z0)
+        for i in range(p.r):
+            assert np.array_equal(np.flatnonzero(hot[d][i]), he[i, :nhe[i]])
+        if ref["flags"][d] == 0:
+            nk, ks = cands[d]
+            assert nk == ref["n_cand"][d]
+            assert np.array_equal(np.sort(ks), ref["cands"][d])
+    return rep, ref
+
+
+def test_tiny_window_full_parity(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"]
+    rep, ref = _full_check(sd, O, torch_mod, w, T.make_window(w, T.window_seed(1)))
+    assert ref["n_hits"] > 20
+
+
+@pytest.mark.parametrize("mode,unroll,threads", [(0, 1, 256), (0, 4, 1024), (1, 2, 512), (2, 2, 512),
+                                                 (2, 4, 256), (1, 1, 128)])
+def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, threads):
+    w = T.WORKLOADS["tiny"].with_(dirs=2, n=(1 << 19) + 3)
+    win = T.make_window(w, 8)
+    _full_check(sd, O, torch_mod, w, win,
+                tuning=dict(mode=mode, unroll=unroll, block_threads=threads))
+
+
+def test_ragged_and_misaligned_inputs(sd, O, torch_mod):
+    """Odd pair counts and buffers starting 8 or 4 bytes past a 16-byte
+    boundary take the head/tail and unaligned paths."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    win = T.make_window(w, 21)
+    n = len(win.pairs)
+    flat = _dev(torch_mod, win.pairs)
+    op = O.params_from(w.sketch(), seed=SEED)
+    for off_words, count in ((0, n - 7), (2, n - 2), (1, 5), (2, 1), (0, 1), (3, 999)):
+        p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+        h = sd.sd_create(p)
+        try:
+            if off_words % 2 == 0:
+                view = flat[off_words: off_words + 2 * count]
+                sd.sd_update(h, view)
+                sub = win.pairs[off_words // 2: off_words // 2 + count]
+            else:
+                # a buffer whose pairs start on an odd word
+                buf = torch_mod.zeros(2 * count + 1, dtype=torch_mod.int32, device="cuda")
+                buf[1:] = flat[: 2 * count]
+                sd.sd_update(h, buf[1:])
+                sub = win.pairs[:count]
+            grid = _grids(sd, h)
+        finally:
+            sd.sd_destroy(h)
+        og = O.new_grid(op)
+        O.update(op, og, sub)
+        assert np.array_equal(grid, og), (off_words, count)
+
+
+def test_empty_window_and_split_updates(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"]
+    win = T.make_window(w, 5)
+    p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        rep0 = sd.sd_close_window(h)        # nothing fed: no hot estimators, no hits
+        assert rep0.n_hits_total == 0 and rep0.n_cand == [0] and rep0.flags == 0
+        assert rep0.psi == [0.0]
+        sd.sd_update(h, np.zeros(0, dtype=np.uint32))
+        dev = _dev(torch_mod, win.pairs)
+        for part in torch_mod.tensor_split(dev, 9):
+            if part.numel() % 2:
+                continue
+            sd.sd_update(h, part)
+        # tensor_split may cut a pair; feed the whole stream again (idempotent)
+        sd.sd_update(h, dev)
+        grid = sd.sd_get_grid(h, 0)
+        rep = sd.sd_close_window(h)
+    finally:
+        sd.sd_destroy(h)
+    op, og, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert np.array_equal(grid, og)
+    _assert_report_equal(O, rep, ref, p)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_pointer_ingest(sd, O, torch_mod, pinned):
+    """Host buffers (pageable or pinned) go through the chunked staging path;
+    small chunks force many double-buffered copies."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    win = T.make_window(w, 6)
+    p = sd.params_for(w, SEED, stage_pairs=40_000,
+                      cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        if pinned:
+            host = torch_mod.from_numpy(win.pairs.reshape(-1).view(np.int32)).pin_memory()
+            sd.sd_update(h, host)
+        else:
+            sd.sd_update(h, win.pairs.reshape(-1))
+        grid = _grids(sd, h)
+        rep = sd.sd_close_window(h)
+    finally:
+        sd.sd_destroy(h)
+    op, og, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert np.array_equal(grid, og)
+    _assert_report_equal(O, rep, ref, p)
+
+
+def _small_core(**kw):
+    base = dict(n=1 << 22, planted=40, planted_c=("loguniform", 1024, 20000), src_pool=1 << 20,
+                dst_pool=1 << 22)
+    base.update(kw)
+    return base
+
+
+@pytest.mark.parametrize("name", ["core", "paper"])
+def test_core_and_paper_parameters_small_window(sd, O, torch_mod, name):
+    w = T.WORKLOADS[name].with_(**_small_core())
+    _full_check(sd, O, torch_mod, w, T.make_window(w, 99))
+
+
+def test_core_link_window_full_size(sd, O, torch_mod):
+    """The benchmarked workload itself: 2^26 pairs, g=512, r=4, k=16, both
+    directions, default launch configuration."""
+    w = T.WORKLOADS["core"]
+    rep, ref = _full_check(sd, O, torch_mod, w, T.make_window(w, T.window_seed(2)))
+    assert rep.n_hits_total > 500
+
+
+def test_saturated_row(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"]
+    win = T.make_window(w, 3)
+    p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    op = O.params_from(w.sketch(), seed=SEED)
+    og = O.new_grid(op)
+    O.update(op, og, win.pairs)
+    rw = og.size // p.r
+    og[2 * rw: 3 * rw] = 0xFFFFFFFF          # row 2 completely set
+    h = sd.sd_create(p)
+    try:
+        sd.sd_set_grid(h, 0, og)
+        rep = sd.sd_close_window(h)
+    finally:
+        sd.sd_destroy(h)
+    ref = O.close_window(op, og)
+    assert rep.rc == sd.SD_ERR_SATURATED
+    assert rep.dir_flags(0) == sd.SD_FLAG_SATURATED == ref["flags"][0]
+    assert rep.psi[0] == -1.0 and rep.n_hits_total == 0
+    assert np.array_equal(rep.zr, ref["zr"])
+
+
+def test_overload_caps(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"]
+    win = T.make_window(w, T.window_seed(1))
+    _, _, full = _oracle_run(O, w, win.pairs, SEED)
+    nh = full["n_hot"][0]
+    for caps in (dict(pair_cap=int(nh[0] * nh[1]) - 1), dict(cand_cap=full["n_cand"][0] - 1),
+                 dict(cand_cap=full["n_cand"][0])):
+        rep, ref = _full_check(sd, O, torch_mod, w, win, **caps)
+        if ref["flags"][0]:
+            assert rep.rc == sd.SD_ERR_OVERLOAD and rep.n_hits_total == 0
+
+
+def test_report_cap_truncates_in_order(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"]
+    win = T.make_window(w, T.window_seed(1))
+    p = sd.params_for(w, SEED, report_cap=17, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        sd.sd_update(h, _dev(torch_mod, win.pairs))
+        rep = sd.sd_close_window(h)
+    finally:
+        sd.sd_destroy(h)
+    _, _, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert rep.rc == sd.SD_ERR_REPORT_OVERFLOW
+    assert rep.n_hits_total == ref["n_hits"] and len(rep.hits) == 17
+    assert np.array_equal(rep.hits["ip"], ref["ip"][:17])
+    assert np.array_equal(rep.hits["est"], ref["est"][:17])
+
+
+def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod):
+    """A DHLA where ~4.7% of the estimators of each row are full: |K| is about
+    p^4 2^32 (tens of thousands), every candidate has SZ = 0 and is reported,
+    more than one block sorts."""
+    w = T.WORKLOADS["core"].with_(dirs=1, g=256)
+    p_full = 0.0465
+    rng = np.random.default_rng(12)
+    cells = rng.random((w.r, 1 << w.k)) < p_full
+    grid = np.zeros((w.r, 1 << w.k, w.g // 32), dtype=np.uint32)
+    grid[cells] = 0xFFFFFFFF
+    grid[~cells, 0] = 1   # every other estimator keeps g-1 zero bits
+    grid = grid.reshape(-1)
+    p = sd.params_for(w, SEED, cand_cap=1 << 17,
+                      cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        sd.sd_set_grid(h, 0, grid)
+        rep = sd.sd_close_window(h)
+    finally:
+        sd.sd_destroy(h)
+    op = O.params_from(w.sketch(), seed=SEED, cand_cap=1 << 17)
+    ref = O.close_window(op, grid)
+    assert ref["n_hits"] > 8192
+    _assert_report_equal(O, rep, ref, p)
+
+
+def test_checkpoint_resume(sd, O, torch_mod):
+    """Snapshot the DHLA mid-window, restore it in a fresh handle, finish the
+    window there: same report as an uninterrupted run."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    win = T.make_window(w, 31)
+    half = len(win.pairs) // 2
+    stream = torch_mod.cuda.current_stream().cuda_stream
+    p = sd.params_for(w, SEED, cuda_stream=stream)
+    a = sd.sd_create(p)
+    b = sd.sd_create(p)
+    try:
+        sd.sd_update(a, _dev(torch_mod, win.pairs[:half]))
+        snap = [sd.sd_get_grid(a, d) for d in range(2)]
+        for d in range(2):
+            sd.sd_set_grid(b, d, snap[d])
+        sd.sd_update(b, _dev(torch_mod, win.pairs[half:]))
+        rep = sd.sd_close_window(b)
+    finally:
+        sd.sd_destroy(a)
+        sd.sd_destroy(b)
+    _, _, ref = _oracle_run(O, w, win.pairs, SEED)
+    _assert_report_equal(O, rep, ref, p)
+
+
+def test_merge_of_monitors_equals_union(sd, O, torch_mod):
+    """§4.2 merge of local DHLAs (read as bitwise OR): three monitors each see
+    part of the traffic; the merged DHLA reports what one monitor seeing all
+    of it would."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    win = T.make_window(w, 41)
+    parts = np.array_split(win.pairs, 3)
+    stream = torch_mod.cuda.current_stream().cuda_stream
+    p = sd.params_for(w, SEED, cuda_stream=stream)
+    hs = [sd.sd_create(p) for _ in parts]
+    try:
+        for h, part in zip(hs, parts):
+            sd.sd_update(h, _dev(torch_mod, part))
+        sd.sd_merge(hs[0], hs[1])
+        sd.sd_merge(hs[0], hs[2])
+        grid = _grids(sd, hs[0])
+        rep = sd.sd_close_window(hs[0])
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    _, og, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert np.array_equal(grid, og)
+    _assert_report_equal(O, rep, ref, p)
+
+
+def test_consecutive_windows_are_independent(sd, O, torch_mod):
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    wins = [T.make_window(w, s) for s in (51, 52, 53)]
+    p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        reps = []
+        for win in wins:
+            sd.sd_update(h, _dev(torch_mod, win.pairs))
+            reps.append(sd.sd_close_window(h))
+    finally:
+        sd.sd_destroy(h)
+    for win, rep in zip(wins, reps):
+        _, _, ref = _oracle_run(O, w, win.pairs, SEED)
+        _assert_report_equal(O, rep, ref, p)
+        assert rep.n_pairs == len(win.pairs)
