@@ -432,7 +432,8 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         for (uint32_t d = 0; d < dirs; d++)
             if (A.run[d])
                 SD_CK(h, cudaMemcpyAsync(h->hits_h + (uint64_t)d * kSortSmall, h->hits + (uint64_t)d * h->hits_cap,
-                                         (uint64_t)kSortSmall * 8, cudaMemcpyDeviceToHost, h->stream));
+                                         std::min<uint64_t>(kSortSmall, h->hits_cap) * 8, cudaMemcpyDeviceToHost,
+                                         h->stream));
         SD_CK(h, cudaStreamSynchronize(h->stream));
         for (uint32_t d = 0; d < dirs; d++) {
             if (!A.run[d]) continue;
