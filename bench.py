@@ -131,9 +131,21 @@ def dist_barrier(world: int):
         dist.barrier()
 
 
+TRAFFIC = "core"
+
+
 def window_for(rank: int, n: int | None = None):
     """Each rank processes its own link: an independent window (weak scaling)."""
+    if TRAFFIC == "uniform":
+        n = n or T.WORKLOADS[WORKLOAD].n
+        rng = np.random.default_rng(T.window_seed(2, link=rank))
+        pairs = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+        return T.Window(pairs=pairs, planted_ip=np.zeros(0, np.uint32),
+                        planted_dir=np.zeros(0, np.uint8), planted_c=np.zeros(0, np.int64),
+                        workload=T.WORKLOADS[WORKLOAD], seed=0)
     return T.make_window(WORKLOAD, T.window_seed(2, link=rank), n=n)
+
+
 
 
 def cpu_oracle_rate(pairs: np.ndarray, sample: int):
@@ -186,16 +198,22 @@ def run_ours(args, rank, world, local):
     from paper_1803_11449_gb300 import sd
 
     torch.cuda.set_device(local)
-    win = window_for(rank)
+    win = window_for(rank, n=args.pairs)
     n = len(win.pairs)
     pairs_dev = torch.from_numpy(win.pairs.reshape(-1).view(np.int32)).cuda()
     pairs_host = torch.from_numpy(win.pairs.reshape(-1).view(np.int32)).pin_memory()
-    stream = torch.cuda.current_stream()
+    # one explicit stream shared by the library and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     w = T.WORKLOADS[WORKLOAD]
     p = sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream.cuda_stream)
     h = sd.sd_create(p)
+    tuned = None
     if args.mode is not None or args.unroll or args.threads:
         sd.sd_set_tuning(h, mode=args.mode or 0, unroll=args.unroll, block_threads=args.threads)
+    elif args.autotune:
+        from paper_1803_11449_gb300.tune import autotune
+        tuned = autotune(h, pairs_dev, stream, verbose=args.verbose)
 
     def step():
         sd.sd_update(h, pairs_dev)
@@ -268,8 +286,10 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD_DESC, "pairs_per_step_per_gpu": n,
                    "l2": "inputs larger than L2 (512 MiB of pairs per step)",
                    "parallelism": f"{world} independent link(s), one per GPU",
+                   "traffic": args.traffic,
                    "tuning": {"mode": tuning.mode, "block_threads": tuning.block_threads,
-                              "blocks_per_sm": tuning.blocks_per_sm, "unroll": tuning.unroll}},
+                              "blocks_per_sm": tuning.blocks_per_sm, "unroll": tuning.unroll,
+                              "autotuned": tuned is not None}},
         "gbps_at_800B": value * 1e9 * GBITS_PER_PACKET,
         "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
@@ -299,12 +319,21 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--ref-sample", type=int, default=1 << 22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="pairs per window (default: the workload's 2^26); profiling only")
     ap.add_argument("--mode", type=int, default=None)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the update kernel's launch knobs by timing them first")
+    ap.add_argument("--traffic", default="core", choices=["core", "uniform"],
+                    help="uniform: every pair random (no Zipf, no planted hosts)")
+    ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global TRAFFIC
+    TRAFFIC = args.traffic
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)

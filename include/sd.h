@@ -97,7 +97,7 @@ typedef struct {
     uint32_t n_hot[2][8];   /* |HE(i)| */
     uint64_t n_cand[2];     /* |K| = #{a : DH_i(a) in HE(i) for all i} */
     uint32_t zhot;          /* largest z_0 that is hot (z_0 < Zmin = g e^(-theta/g)) */
-    uint32_t szmax[2];      /* largest SZ reported: C(SZ) >= theta and SZ <= zhot */
+    uint32_t szmax[2];      /* largest SZ with C(SZ) >= theta (Eq. 4): hits have SZ <= szmax */
     uint32_t flags;         /* SD_FLAG_* at bit 8*dir */
     uint64_t n_hits_total;  /* hits found (exact even when truncated) */
     uint64_t n_hits;        /* hits returned in `hits` (<= report_cap) */
@@ -110,10 +110,15 @@ typedef struct {
 typedef struct {
     uint32_t mode;          /* 0: one relaxed atomic OR per row;
                                1: test the bit first (Algorithm 1's test), skip set bits;
-                               2: 1 + de-duplicate identical (word, bit) targets in a warp */
-    uint32_t block_threads; /* threads per block: 128..1024, multiple of 32 */
-    uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for */
+                               2: 1 + merge the targets of one word inside a warp;
+                               3: a per-block shared-memory filter of bits known to
+                                  be set, then 1;
+                               4: the filter, then 0 */
+    uint32_t block_threads; /* threads per block: 64..1024, multiple of 32 */
+    uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (0: as
+                               many as fit) */
     uint32_t unroll;        /* 16-byte pair loads in flight per thread: 1, 2 or 4 */
+    uint32_t filter_log2;   /* log2 of the filter's 8-byte entries: 8..14 */
 } sd_tuning;
 
 /* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,

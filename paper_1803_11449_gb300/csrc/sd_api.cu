@@ -128,10 +128,12 @@ struct sd_handle {
     uint32_t *he = nullptr;            // [dirs][2][2^k]
     uint32_t *cand = nullptr;          // [dirs][cand_cap]
     unsigned long long *hits = nullptr;   // [dirs][hits_cap]
+    unsigned long long *hits_tmp = nullptr;  // [hits_cap]: scratch of the large-list sort
     unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
     uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
     std::vector<unsigned long long> big_h;
     std::vector<sd_hit> report;
+    std::vector<double> est_tbl;
     uint64_t last_ncand[2] = {0, 0};
     bool have_close = false;
 
@@ -211,7 +213,7 @@ uint64_t sd_device_bytes(const sd_params *p) {
     resolve_caps(p, &pc, &cc, &hc, &rc, &sp);
     const uint64_t cells = (uint64_t)p->r << p->k;
     return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + hc * 8) +
-           sizeof(StatBlock) + 2 * sp * 8;
+           hc * 8 + sizeof(StatBlock) + 2 * sp * 8;
 }
 
 static void release(sd_handle *h) {
@@ -223,6 +225,7 @@ static void release(sd_handle *h) {
     cudaFree(h->he);
     cudaFree(h->cand);
     cudaFree(h->hits);
+    cudaFree(h->hits_tmp);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     for (int b = 0; b < 2; b++) {
@@ -254,7 +257,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         G.h[d].B1 = splitmix64(&st);
         G.h[d].A0inv = inverse_odd(G.h[d].A0);
     }
-    h->T = Tuning{0, 512, 0, 2};
+    h->T = Tuning{3, 512, 0, 2, 13};
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -279,6 +282,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     SD_CK(h, cudaMalloc(&h->he, (uint64_t)p->dirs * 2 * ((uint64_t)4 << p->k)));
     SD_CK(h, cudaMalloc(&h->cand, (uint64_t)p->dirs * h->cand_cap * 4));
     SD_CK(h, cudaMalloc(&h->hits, (uint64_t)p->dirs * h->hits_cap * 8));
+    SD_CK(h, cudaMalloc(&h->hits_tmp, h->hits_cap * 8));
     SD_CK(h, cudaMallocHost(&h->st_h, sizeof(StatBlock)));
     SD_CK(h, cudaMallocHost(&h->hits_h, (uint64_t)2 * kSortSmall * 8));
     SD_CK(h, launch_reset(h->grid, words, h->st_d, h->num_sms, h->stream));
@@ -447,20 +451,28 @@ int sd_close_window(sd_handle *h, sd_report *out) {
             const uint64_t nh = h->st_h->nhits[d];
             const unsigned long long *keys = h->hits_h + (uint64_t)d * kSortSmall;
             if (h->st_h->big_sort[d]) {
-                unsigned long long *dk = h->hits + (uint64_t)d * h->hits_cap;
-                SD_CK(h, launch_sort_big(dk, nh, next_pow2(nh), h->num_sms, h->stream));
+                unsigned long long *sorted = nullptr;
+                SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp, nh, h->num_sms,
+                                         h->stream, &sorted));
                 h->big_h.resize(nh);
-                SD_CK(h, cudaMemcpyAsync(h->big_h.data(), dk, nh * 8, cudaMemcpyDeviceToHost, h->stream));
+                SD_CK(h, cudaMemcpyAsync(h->big_h.data(), sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
                 SD_CK(h, cudaStreamSynchronize(h->stream));
                 keys = h->big_h.data();
             }
+            // Eq. 4 depends on SZ alone within a window: one evaluation per
+            // distinct SZ value (hits have SZ <= szmax), bit-identical to
+            // evaluating it per hit
+            std::vector<double> &tbl = h->est_tbl;
+            tbl.assign((size_t)(A.szmax[d] >= 0 ? A.szmax[d] + 1 : 0), 0.0);
+            for (size_t z = 0; z < tbl.size(); z++) tbl[z] = eq4(G.g, G.r, psi[d], (uint32_t)z);
+            h->report.reserve(h->report.size() + nh);
             for (uint64_t q = 0; q < nh; q++) {
                 sd_hit hit;
                 hit.ip = (uint32_t)(keys[q] >> 32);
                 hit.sz = (uint32_t)(keys[q] & 0xFFFFFFFFull);
                 hit.dir = d;
                 hit.reserved = 0;
-                hit.est = eq4(G.g, G.r, psi[d], hit.sz);
+                hit.est = hit.sz < tbl.size() ? tbl[hit.sz] : eq4(G.g, G.r, psi[d], hit.sz);
                 h->report.push_back(hit);
             }
         }
@@ -576,13 +588,14 @@ int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     out->block_threads = h->T.block_threads;
     out->blocks_per_sm = h->T.blocks_per_sm;
     out->unroll = h->T.unroll;
+    out->filter_log2 = h->T.filter_log2;
     return SD_OK;
 }
 
 int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
     if (!h || !t) return SD_ERR_ARG;
     Tuning T = h->T;
-    if (t->mode > 2) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0, 1 or 2");
+    if (t->mode > 4) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..4");
     T.mode = t->mode;
     if (t->block_threads) {
         if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
@@ -594,6 +607,11 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
         if (t->unroll != 1 && t->unroll != 2 && t->unroll != 4)
             return h->fail(SD_ERR_ARG, "sd_set_tuning: unroll must be 1, 2 or 4");
         T.unroll = t->unroll;
+    }
+    if (t->filter_log2) {
+        if (t->filter_log2 < 8 || t->filter_log2 > 14)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: filter_log2 must be in [8, 14]");
+        T.filter_log2 = t->filter_log2;
     }
     h->T = T;
     return SD_OK;

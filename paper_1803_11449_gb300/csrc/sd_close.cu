@@ -204,6 +204,9 @@ k_restore(Geometry G, RestoreArgs A) {
                     const unsigned long long slot = base + __popc(fb & ((1u << lane) - 1u));
                     if (slot < A.cand_cap) A.cand[(uint64_t)dir * A.cand_cap + slot] = a;
                 }
+                // past the candidate cap the direction is reported as overloaded
+                // and its hits are dropped: keep counting K, skip SZ
+                if (base + __popc(fb) > A.cand_cap) continue;
                 // SZ of each candidate, one warp-wide AND + popcount at a time
                 unsigned rest = fb;
                 while (rest) {
@@ -273,26 +276,58 @@ k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 r
     for (unsigned i = threadIdx.x; i < nn; i += blockDim.x) hd[i] = s[i];
 }
 
-__global__ void k_pad(unsigned long long *keys, uint64_t from, uint64_t to) {
-    for (uint64_t i = from + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < to;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        keys[i] = ~0ull;
+// Sort every segment keys[j*kSortSmall, (j+1)*kSortSmall) of keys[0, n) in
+// shared memory (one block per segment, bitonic, padded with all-ones keys).
+__global__ void __launch_bounds__(1024)
+k_sort_segments(unsigned long long *keys, uint64_t n) {
+    extern __shared__ unsigned long long s[];
+    const uint64_t base = (uint64_t)blockIdx.x * kSortSmall;
+    if (base >= n) return;
+    const uint64_t left = n - base;
+    const unsigned len = (unsigned)(left < (uint64_t)kSortSmall ? left : (uint64_t)kSortSmall);
+    unsigned P = 1;
+    while (P < len) P <<= 1;
+    unsigned long long *kd = keys + base;
+    for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? kd[i] : ~0ull;
+    __syncthreads();
+    for (unsigned kk = 2; kk <= P; kk <<= 1) {
+        for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+            for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
+                const unsigned ix = i ^ j;
+                if (ix > i) cswap(s[i], s[ix], (i & kk) == 0);
+            }
+            __syncthreads();
+        }
+    }
+    for (unsigned i = threadIdx.x; i < len; i += blockDim.x) kd[i] = s[i];
 }
 
-// One compare-exchange stage (kk, j) of a bitonic sort over P keys in global
-// memory.
-__global__ void k_bitonic_step(unsigned long long *keys, uint64_t P, uint64_t kk, uint64_t j) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t ix = i ^ j;
-        if (ix > i) {
-            unsigned long long a = keys[i], b = keys[ix];
-            const bool up = (i & kk) == 0;
-            if ((a > b) == up) {
-                keys[i] = b;
-                keys[ix] = a;
-            }
+// Merge neighbouring sorted runs of length L (the last may be shorter) from
+// src into dst.  Keys are distinct, so an element's place in the merged run
+// is its index in its own run plus the number of keys below it in the other
+// run (a binary search): every element moves independently.
+__global__ void k_merge_rank(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst,
+                             uint64_t n, uint64_t L) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t run = i / L;
+        const uint64_t pb = (run & ~1ull) * L;
+        const uint64_t a0 = pb, a1 = (pb + L < n) ? pb + L : n;
+        const uint64_t b0 = a1, b1 = (pb + 2 * L < n) ? pb + 2 * L : n;
+        const unsigned long long key = src[i];
+        uint64_t lo, hi, own;
+        if ((run & 1) == 0) {
+            lo = b0; hi = b1; own = i - a0;
+        } else {
+            lo = a0; hi = a1; own = i - b0;
         }
+        const uint64_t other0 = lo;
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo) / 2;
+            if (src[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        dst[pb + own + (lo - other0)] = key;
     }
 }
 
@@ -376,13 +411,23 @@ cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatB
     return cudaGetLastError();
 }
 
-// Sort keys[0, n) ascending; keys has room for P >= n entries (P a power of
-// two).  Used only when a direction has more than kSortSmall hits.
-cudaError_t launch_sort_big(unsigned long long *keys, uint64_t n, uint64_t P, int num_sms, cudaStream_t s) {
-    const unsigned blocks = grid_for(P, 256, num_sms, 8);
-    k_pad<<<blocks, 256, 0, s>>>(keys, n, P);
-    for (uint64_t kk = 2; kk <= P; kk <<= 1)
-        for (uint64_t j = kk >> 1; j > 0; j >>= 1) k_bitonic_step<<<blocks, 256, 0, s>>>(keys, P, kk, j);
+// Sort keys[0, n) ascending (distinct keys) with `tmp` as scratch of the
+// same size; *out points at whichever of the two holds the result.
+cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
+                            cudaStream_t s, unsigned long long **out) {
+    const int smem = kSortSmall * (int)sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t segs = (n + kSortSmall - 1) / kSortSmall;
+    k_sort_segments<<<(unsigned)segs, 1024, smem, s>>>(keys, n);
+    unsigned long long *a = keys, *b = tmp;
+    for (uint64_t L = kSortSmall; L < n; L <<= 1) {
+        k_merge_rank<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(a, b, n, L);
+        unsigned long long *t = a;
+        a = b;
+        b = t;
+    }
+    *out = a;
     return cudaGetLastError();
 }
 

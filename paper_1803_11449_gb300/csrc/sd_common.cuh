@@ -29,10 +29,12 @@ struct Geometry {
 };
 
 struct Tuning {
-    uint32_t mode;           // 0 plain, 1 test-then-set, 2 test + warp de-dup
+    uint32_t mode;           // 0 plain, 1 test-then-set, 2 test + warp de-dup,
+                             // 3 filter + test, 4 filter + plain
     uint32_t block_threads;
     uint32_t blocks_per_sm;
     uint32_t unroll;
+    uint32_t filter_log2;    // log2 of the shared-memory filter entries (modes 3, 4)
 };
 
 constexpr int kSortSmall = 8192;  // hits per direction sorted in one block
@@ -126,7 +128,8 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s);
-cudaError_t launch_sort_big(unsigned long long *keys, uint64_t n, uint64_t P, int num_sms, cudaStream_t s);
+cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
+                            cudaStream_t s, unsigned long long **out);
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
 

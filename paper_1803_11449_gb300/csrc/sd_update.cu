@@ -7,28 +7,75 @@
 // the L2-resident DHLA as relaxed `red.or` reductions.  Mode 1 adds
 // Algorithm 1's own test ("if the bit is 1, continue") as a weak cached load
 // so set bits cost a load instead of an atomic; mode 2 additionally merges
-// bit-sets that hit the same word inside a warp (__match_any_sync).  The
-// grid is persistent: a multiple of the SM count, grid-stride over the pairs
-// with a trip count that is uniform across each warp (mode 2 needs converged
-// warps).
+// bit-sets that hit the same word inside a warp (__match_any_sync).  Modes 3
+// and 4 put a shared-memory filter of words known to be set in front of the
+// test (3) or of the plain reduction (4): with Zipf-distributed hosts most
+// bit-sets repeat bits that heavy hosts set long ago, and those never leave
+// the SM.  The grid is persistent: a multiple of the SM count, grid-stride
+// over the pairs with a trip count that is uniform across each warp (mode 2
+// needs converged warps).
 #include "sd_common.cuh"
 
 namespace sd {
 
+// Per-block filter of DHLA words with bits known to be set: a direct-mapped
+// table in shared memory of 64-bit entries (word index << 32 | known mask).
+// An entry is written with one 64-bit store, so a reader always sees a tag
+// and a mask that belong together; every bit in a stored mask is either
+// already 1 in the DHLA or covered by a reduction this block has issued, and
+// those complete before the kernel ends.  So a filter hit may skip the
+// bit-set; a lost or overwritten entry only costs a redundant operation.
+struct Filter {
+    unsigned long long *tab;
+    uint32_t shift;  // 32 - log2(entries)
+};
+
+__device__ __forceinline__ uint32_t filter_slot(const Filter &f, uint32_t word) {
+    return (word * 0x9E3779B1u) >> f.shift;
+}
+
 // Set bit H1(elem) of the estimators DH_i(key), i < R, of one direction.
+// `word0` is the index of the direction's first DHLA word (filter tags).
 template <int R, int MODE>
 __device__ __forceinline__ void set_bits(uint32_t *__restrict__ dgrid, const Geometry &G,
                                          const HashDir &h, uint32_t key, uint32_t elem,
-                                         bool valid) {
+                                         bool valid, const Filter &f, uint32_t word0) {
     const uint32_t bit = h1(h, G.lg, elem);
     const uint32_t c0 = dh0(h.A0, G.k, key);
     const uint32_t mask = 1u << (bit & 31u);
     uint32_t *const base = dgrid + (bit >> 5);
     uint32_t *addr[R];
+    uint32_t widx[R];
 #pragma unroll
     for (int i = 0; i < R; i++) {
         const uint32_t ci = (i == 0) ? c0 : dh_row(G, i, key, c0);
-        addr[i] = base + (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc;
+        const uint64_t off = (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc;
+        addr[i] = base + off;
+        widx[i] = word0 + (uint32_t)off + (bit >> 5);
+    }
+    if (MODE >= 3) {
+        // filter first; then test (mode 3) or reduce directly (mode 4)
+        unsigned long long e[R];
+#pragma unroll
+        for (int i = 0; i < R; i++) e[i] = valid ? f.tab[filter_slot(f, widx[i])] : 0ull;
+        bool need[R];
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+            const bool tag_ok = (uint32_t)(e[i] >> 32) == widx[i];
+            need[i] = valid && !(tag_ok && ((uint32_t)e[i] & mask));
+        }
+        uint32_t cur[R];
+#pragma unroll
+        for (int i = 0; i < R; i++) cur[i] = (MODE == 3 && need[i]) ? ld_weak(addr[i]) : 0u;
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+            if (!need[i]) continue;
+            if (!(cur[i] & mask)) red_or(addr[i], mask);
+            const bool tag_ok = (uint32_t)(e[i] >> 32) == widx[i];
+            const uint32_t known = (tag_ok ? (uint32_t)e[i] : 0u) | cur[i] | mask;
+            f.tab[filter_slot(f, widx[i])] = ((unsigned long long)widx[i] << 32) | known;
+        }
+        return;
     }
     if (MODE == 0) {
         if (valid) {
@@ -70,9 +117,10 @@ __device__ __forceinline__ void set_bits(uint32_t *__restrict__ dgrid, const Geo
 
 template <int R, int MODE>
 __device__ __forceinline__ void apply_pair(uint32_t *__restrict__ grid, const Geometry &G,
-                                           uint32_t src, uint32_t dst, bool valid) {
-    set_bits<R, MODE>(grid, G, G.h[0], src, dst, valid);
-    if (G.dirs > 1) set_bits<R, MODE>(grid + G.dir_words, G, G.h[1], dst, src, valid);
+                                           uint32_t src, uint32_t dst, bool valid, const Filter &f) {
+    set_bits<R, MODE>(grid, G, G.h[0], src, dst, valid, f, 0u);
+    if (G.dirs > 1)
+        set_bits<R, MODE>(grid + G.dir_words, G, G.h[1], dst, src, valid, f, (uint32_t)G.dir_words);
 }
 
 // pairs: 8-byte aligned (the launcher guarantees it).  The first pair is
@@ -80,7 +128,17 @@ __device__ __forceinline__ void apply_pair(uint32_t *__restrict__ grid, const Ge
 // 16-byte load, then a last odd pair.
 template <int R, int MODE, int UNROLL>
 __global__ void __launch_bounds__(1024)
-k_update(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G) {
+k_update(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G,
+         uint32_t filter_log2) {
+    extern __shared__ unsigned long long filter_tab[];
+    Filter f{filter_tab, 32u - filter_log2};
+    if (MODE >= 3) {
+        // empty entries carry the tag 0xFFFFFFFF, never a word index (the
+        // launcher only enables the filter when the DHLA has fewer words)
+        for (uint32_t i = threadIdx.x; i < (1u << filter_log2); i += blockDim.x)
+            filter_tab[i] = 0xFFFFFFFF00000000ull;
+        __syncthreads();
+    }
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t head = (((uintptr_t)pairs & 15u) != 0 && n > 0) ? 1 : 0;
@@ -98,7 +156,7 @@ k_update(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ 
             s = pairs[2 * at];
             d = pairs[2 * at + 1];
         }
-        apply_pair<R, MODE>(grid, G, s, d, h_ok || t_ok);
+        apply_pair<R, MODE>(grid, G, s, d, h_ok || t_ok, f);
     }
 
     const uint64_t step = stride * UNROLL;
@@ -114,8 +172,8 @@ k_update(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ 
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
-            apply_pair<R, MODE>(grid, G, q[u].x, q[u].y, ok[u]);
-            apply_pair<R, MODE>(grid, G, q[u].z, q[u].w, ok[u]);
+            apply_pair<R, MODE>(grid, G, q[u].x, q[u].y, ok[u], f);
+            apply_pair<R, MODE>(grid, G, q[u].z, q[u].w, ok[u], f);
         }
     }
 }
@@ -127,16 +185,24 @@ __global__ void __launch_bounds__(256)
 k_update_unaligned(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid,
                    Geometry G) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const Filter f{nullptr, 0};
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
-        apply_pair<R, 0>(grid, G, ld_stream_u32(pairs + 2 * t), ld_stream_u32(pairs + 2 * t + 1), true);
+        apply_pair<R, 0>(grid, G, ld_stream_u32(pairs + 2 * t), ld_stream_u32(pairs + 2 * t + 1), true, f);
 }
 
 template <int R, int MODE, int UNROLL>
 static cudaError_t launch3(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                            const Tuning &T, int num_sms, cudaStream_t s) {
     auto kern = k_update<R, MODE, UNROLL>;
+    const uint32_t flog = MODE >= 3 ? T.filter_log2 : 0u;
+    const size_t smem = MODE >= 3 ? ((size_t)8 << flog) : 0;
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T.block_threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T.block_threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int want = T.blocks_per_sm ? (int)T.blocks_per_sm : per_sm;
@@ -146,7 +212,7 @@ static cudaError_t launch3(const uint32_t *pairs, uint64_t n, uint32_t *grid, co
     uint64_t blocks = (uint64_t)num_sms * bps;
     const uint64_t need = (loads + T.block_threads - 1) / T.block_threads;
     if (need < blocks) blocks = need > 0 ? need : 1;
-    kern<<<(unsigned)blocks, T.block_threads, 0, s>>>(pairs, n, grid, G);
+    kern<<<(unsigned)blocks, T.block_threads, smem, s>>>(pairs, n, grid, G, flog);
     return cudaGetLastError();
 }
 
@@ -170,9 +236,14 @@ static cudaError_t launch1(const uint32_t *pairs, uint64_t n, uint32_t *grid, co
         k_update_unaligned<R><<<blocks, 256, 0, s>>>(pairs, n, grid, G);
         return cudaGetLastError();
     }
-    switch (T.mode) {
+    uint32_t mode = T.mode;
+    // the filter tags words with 32-bit indices; 0xFFFFFFFF marks empty slots
+    if (mode >= 3 && (uint64_t)G.dirs * G.dir_words >= 0xFFFFFFFFull) mode = 1;
+    switch (mode) {
         case 1: return launch2<R, 1>(pairs, n, grid, G, T, num_sms, s);
         case 2: return launch2<R, 2>(pairs, n, grid, G, T, num_sms, s);
+        case 3: return launch2<R, 3>(pairs, n, grid, G, T, num_sms, s);
+        case 4: return launch2<R, 4>(pairs, n, grid, G, T, num_sms, s);
         default: return launch2<R, 0>(pairs, n, grid, G, T, num_sms, s);
     }
 }

@@ -66,7 +66,8 @@ class sd_report(ctypes.Structure):
 
 class sd_tuning(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("unroll", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint32), ("unroll", ctypes.c_uint32),
+                ("filter_log2", ctypes.c_uint32)]
 
 
 HIT_DTYPE = np.dtype([("ip", "<u4"), ("sz", "<u4"), ("dir", "<u4"), ("reserved", "<u4"),
@@ -289,8 +290,10 @@ def sd_get_tuning(h: Handle) -> sd_tuning:
     return t
 
 
-def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0) -> None:
-    t = sd_tuning(mode=mode, block_threads=block_threads, blocks_per_sm=blocks_per_sm, unroll=unroll)
+def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0,
+                  filter_log2=0) -> None:
+    t = sd_tuning(mode=mode, block_threads=block_threads, blocks_per_sm=blocks_per_sm, unroll=unroll,
+                  filter_log2=filter_log2)
     _check(lib().sd_set_tuning(h.ptr, ctypes.byref(t)), h.ptr)
 
 

@@ -1,0 +1,53 @@
+"""Autotuner for the update kernel's launch knobs (sd_tuning).
+
+Each candidate setting is timed with CUDA events on the handle's stream over
+the caller's own pair buffer, starting from an empty DHLA every time (a
+window close clears it), and the fastest setting is applied to the handle.
+"""
+from __future__ import annotations
+
+import itertools
+
+from . import sd
+
+MODES = (0, 1, 2, 3, 4)
+UNROLLS = (1, 2, 4)
+THREADS = (256, 512, 1024)
+FILTERS = (12, 13, 14)   # log2 entries of the shared-memory filter (modes 3, 4)
+
+
+def _space(modes, unrolls, threads, filters):
+    for mode, unroll, nthr in itertools.product(modes, unrolls, threads):
+        for flog in (filters if mode >= 3 else (13,)):
+            yield mode, unroll, nthr, flog
+
+
+def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, threads=THREADS,
+             filters=FILTERS, verbose: bool = False) -> dict:
+    """Time every (mode, unroll, block_threads, filter_log2) on `pairs_dev`;
+    apply and return the best as a dict with the knobs, "ms" and "table"."""
+    import torch
+
+    table = []
+    for mode, unroll, nthr, flog in _space(modes, unrolls, threads, filters):
+        sd.sd_set_tuning(h, mode=mode, unroll=unroll, block_threads=nthr, filter_log2=flog)
+        times = []
+        for _ in range(reps):
+            sd.sd_close_window(h)  # clears the DHLA: every trial starts from zero
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sd.sd_update(h, pairs_dev)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = sorted(times)[len(times) // 2]
+        table.append({"mode": mode, "unroll": unroll, "block_threads": nthr, "filter_log2": flog,
+                      "ms": ms})
+        if verbose:
+            print(table[-1], flush=True)
+    sd.sd_close_window(h)
+    best = min(table, key=lambda r: r["ms"])
+    sd.sd_set_tuning(h, mode=best["mode"], unroll=best["unroll"], block_threads=best["block_threads"],
+                     filter_log2=best["filter_log2"])
+    return dict(best, table=table)

@@ -97,13 +97,25 @@ def test_tiny_window_full_parity(sd, O, torch_mod):
     assert ref["n_hits"] > 20
 
 
-@pytest.mark.parametrize("mode,unroll,threads", [(0, 1, 256), (0, 4, 1024), (1, 2, 512), (2, 2, 512),
-                                                 (2, 4, 256), (1, 1, 128)])
-def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, threads):
+@pytest.mark.parametrize("mode,unroll,threads,flog", [
+    (0, 1, 256, 13), (0, 4, 1024, 13), (1, 2, 512, 13), (2, 2, 512, 13), (2, 4, 256, 13),
+    (1, 1, 128, 13), (3, 2, 512, 13), (3, 1, 1024, 14), (3, 4, 256, 8), (4, 2, 512, 12),
+    (4, 1, 64, 8)])
+def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, threads, flog):
     w = T.WORKLOADS["tiny"].with_(dirs=2, n=(1 << 19) + 3)
     win = T.make_window(w, 8)
     _full_check(sd, O, torch_mod, w, win,
-                tuning=dict(mode=mode, unroll=unroll, block_threads=threads))
+                tuning=dict(mode=mode, unroll=unroll, block_threads=threads, filter_log2=flog))
+
+
+def test_filter_modes_on_heavy_hitters(sd, O, torch_mod):
+    """A few hosts carry most of the traffic, so the shared-memory filter of
+    modes 3 and 4 is hit constantly and blocks see bits others have set."""
+    w = T.WORKLOADS["core"].with_(n=1 << 21, src_pool=64, zipf_s=1.3, dst_pool=1 << 12,
+                                  planted=4, planted_c=("uniform", 3000, 5000))
+    win = T.make_window(w, 19)
+    for mode in (3, 4):
+        _full_check(sd, O, torch_mod, w, win, tuning=dict(mode=mode, filter_log2=10))
 
 
 def test_ragged_and_misaligned_inputs(sd, O, torch_mod):
