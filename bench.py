@@ -210,7 +210,8 @@ def run_ours(args, rank, world, local):
     h = sd.sd_create(p)
     tuned = None
     if args.mode is not None or args.unroll or args.threads:
-        sd.sd_set_tuning(h, mode=args.mode or 0, unroll=args.unroll, block_threads=args.threads)
+        sd.sd_set_tuning(h, mode=args.mode if args.mode is not None else sd.sd_get_tuning(h).mode,
+                         unroll=args.unroll, block_threads=args.threads)
     elif args.autotune:
         from paper_1803_11449_gb300.tune import autotune
         tuned = autotune(h, pairs_dev, stream, verbose=args.verbose)
@@ -287,9 +288,8 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (512 MiB of pairs per step)",
                    "parallelism": f"{world} independent link(s), one per GPU",
                    "traffic": args.traffic,
-                   "tuning": {"mode": tuning.mode, "block_threads": tuning.block_threads,
-                              "blocks_per_sm": tuning.blocks_per_sm, "unroll": tuning.unroll,
-                              "autotuned": tuned is not None}},
+                   "tuning": dict({f: getattr(tuning, f) for f, _ in tuning._fields_},
+                                  autotuned=tuned is not None)},
         "gbps_at_800B": value * 1e9 * GBITS_PER_PACKET,
         "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},

@@ -113,12 +113,20 @@ typedef struct {
                                2: 1 + merge the targets of one word inside a warp;
                                3: a per-block shared-memory filter of bits known to
                                   be set, then 1;
-                               4: the filter, then 0 */
+                               4: the filter, then 0;
+                               5: binned: bit-sets sorted by DHLA slice through a
+                                  scratch buffer, each slice updated in shared memory */
     uint32_t block_threads; /* threads per block: 64..1024, multiple of 32 */
     uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (0: as
                                many as fit) */
     uint32_t unroll;        /* 16-byte pair loads in flight per thread: 1, 2 or 4 */
     uint32_t filter_log2;   /* log2 of the filter's 8-byte entries: 8..14 */
+    uint32_t bin_slice_log2; /* mode 5: DHLA words per slice, log2: 10..15 (raised
+                                automatically to keep at most 4096 slices) */
+    uint32_t bin_tile_pairs; /* mode 5: pairs per binning tile: 64..4096, multiple of 64 */
+    uint32_t bin_chunk_log2; /* mode 5: pairs per bin-then-apply round, log2: 12..28 */
+    uint32_t bin_slack_pct;  /* mode 5: bin capacity above the mean fill, percent
+                                (0xFFFFFFFF sets 0); a full bin falls back to atomics */
 } sd_tuning;
 
 /* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,

@@ -137,6 +137,11 @@ struct sd_handle {
     uint64_t last_ncand[2] = {0, 0};
     bool have_close = false;
 
+    // binned update (mode 5): scratch sized for the current tuning
+    uint32_t *bin_mem = nullptr;       // bins [S][cap], then count [S], then work [1]
+    uint64_t bin_mem_words = 0;
+    BinArgs bin{};
+
     uint64_t stage_pairs = 0;
     uint32_t *dstage[2] = {nullptr, nullptr};
     uint32_t *hstage[2] = {nullptr, nullptr};  // pinned
@@ -226,6 +231,7 @@ static void release(sd_handle *h) {
     cudaFree(h->cand);
     cudaFree(h->hits);
     cudaFree(h->hits_tmp);
+    cudaFree(h->bin_mem);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     for (int b = 0; b < 2; b++) {
@@ -257,7 +263,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         G.h[d].B1 = splitmix64(&st);
         G.h[d].A0inv = inverse_odd(G.h[d].A0);
     }
-    h->T = Tuning{3, 512, 0, 2, 13};
+    h->T = Tuning{1, 512, 0, 2, 13, 14, 1024, 23, 100};
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -324,6 +330,78 @@ static int ensure_staging(sd_handle *h) {
     return SD_OK;
 }
 
+// Geometry of the binned update for the current tuning: slices of
+// 2^slice_log2 words (at most 4096 of them, so a (slice, rank) pair packs in
+// 32 bits), bins sized for 2^chunk_log2 pairs per round plus the slack.
+// Returns false when the DHLA is too large for binning.
+static bool bin_layout(const sd_handle *h, BinArgs *B, uint64_t *words) {
+    const Geometry &G = h->G;
+    const uint64_t total = (uint64_t)G.dirs * G.dir_words;
+    uint32_t sl = h->T.bin_slice_log2;
+    while (((total + (1ull << sl) - 1) >> sl) > 4096 && sl < 15) sl++;
+    const uint64_t S = (total + (1ull << sl) - 1) >> sl;
+    if (S > 4096 || (1ull << sl) > total) return false;
+    const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
+    const uint64_t mean = (chunk * G.dirs * G.r + S - 1) / S;
+    uint64_t cap = mean + mean * h->T.bin_slack_pct / 100 + 256;
+    cap = (cap + 3) & ~3ull;
+    if (cap > 0xFFFFFFFFull) return false;
+    std::memset(B, 0, sizeof *B);
+    B->S = (uint32_t)S;
+    B->slice_log2 = sl;
+    B->cap = (uint32_t)cap;
+    B->tile_pairs = h->T.bin_tile_pairs;
+    B->total_words = total;
+    *words = S * cap + S + 4;
+    return true;
+}
+
+static int ensure_bins(sd_handle *h, bool *ok) {
+    BinArgs B;
+    uint64_t words = 0;
+    *ok = bin_layout(h, &B, &words);
+    if (!*ok) return SD_OK;
+    if (words > h->bin_mem_words) {
+        SD_CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->bin_mem);
+        h->bin_mem = nullptr;
+        h->bin_mem_words = 0;
+        SD_CK(h, cudaMalloc(&h->bin_mem, words * 4));
+        h->bin_mem_words = words;
+        SD_CK(h, cudaMemsetAsync(h->bin_mem + (uint64_t)B.S * B.cap, 0, ((uint64_t)B.S + 4) * 4, h->stream));
+    } else if (B.S != h->bin.S || B.cap != h->bin.cap) {
+        SD_CK(h, cudaMemsetAsync(h->bin_mem + (uint64_t)B.S * B.cap, 0, ((uint64_t)B.S + 4) * 4, h->stream));
+    }
+    B.bins = h->bin_mem;
+    B.count = h->bin_mem + (uint64_t)B.S * B.cap;
+    B.work = B.count + B.S;
+    h->bin = B;
+    return SD_OK;
+}
+
+// Algorithm 1 over n device-resident pairs, with the handle's tuning.
+static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+    if (h->T.mode == 5) {
+        bool ok = false;
+        const int rc = ensure_bins(h, &ok);
+        if (rc != SD_OK) return rc;
+        if (ok) {
+            const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
+            for (uint64_t off = 0; off < n; off += chunk) {
+                const uint64_t m = std::min(chunk, n - off);
+                SD_CK(h, launch_binned_chunk(pairs + 2 * off, m, h->grid, h->G, h->bin, h->num_sms, h->stream));
+            }
+            return SD_OK;
+        }
+        Tuning T = h->T;  // DHLA too large to bin: test-then-set
+        T.mode = 1;
+        SD_CK(h, launch_update(pairs, n, h->grid, h->G, T, h->num_sms, h->stream));
+        return SD_OK;
+    }
+    SD_CK(h, launch_update(pairs, n, h->grid, h->G, h->T, h->num_sms, h->stream));
+    return SD_OK;
+}
+
 int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
     if (!h) return SD_ERR_ARG;
     if (n == 0) return SD_OK;
@@ -339,7 +417,8 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
         if (attr.type == cudaMemoryTypeDevice && attr.device != h->p.device)
             return h->fail(SD_ERR_ARG, "sd_update: pairs live on device %d, handle on %d", attr.device,
                            h->p.device);
-        SD_CK(h, launch_update(pairs, n, h->grid, h->G, h->T, h->num_sms, h->stream));
+        const int rc = update_device(h, pairs, n);
+        if (rc != SD_OK) return rc;
         h->n_pairs += n;
         return SD_OK;
     }
@@ -361,7 +440,8 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
         SD_CK(h, cudaMemcpyAsync(h->dstage[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream));
         SD_CK(h, cudaEventRecord(h->ev_h2d[b], h->copy_stream));
         SD_CK(h, cudaStreamWaitEvent(h->stream, h->ev_h2d[b], 0));
-        SD_CK(h, launch_update(h->dstage[b], m, h->grid, h->G, h->T, h->num_sms, h->stream));
+        const int urc = update_device(h, h->dstage[b], m);
+        if (urc != SD_OK) return urc;
         SD_CK(h, cudaEventRecord(h->ev_kern[b], h->stream));
     }
     // the caller may reuse a pinned buffer only once its copies are done
@@ -589,13 +669,17 @@ int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     out->blocks_per_sm = h->T.blocks_per_sm;
     out->unroll = h->T.unroll;
     out->filter_log2 = h->T.filter_log2;
+    out->bin_slice_log2 = h->T.bin_slice_log2;
+    out->bin_tile_pairs = h->T.bin_tile_pairs;
+    out->bin_chunk_log2 = h->T.bin_chunk_log2;
+    out->bin_slack_pct = h->T.bin_slack_pct;
     return SD_OK;
 }
 
 int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
     if (!h || !t) return SD_ERR_ARG;
     Tuning T = h->T;
-    if (t->mode > 4) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..4");
+    if (t->mode > 5) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..5");
     T.mode = t->mode;
     if (t->block_threads) {
         if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
@@ -612,6 +696,31 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
         if (t->filter_log2 < 8 || t->filter_log2 > 14)
             return h->fail(SD_ERR_ARG, "sd_set_tuning: filter_log2 must be in [8, 14]");
         T.filter_log2 = t->filter_log2;
+    }
+    if (t->bin_slice_log2) {
+        if (t->bin_slice_log2 < 10 || t->bin_slice_log2 > 15)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_slice_log2 must be in [10, 15]");
+        T.bin_slice_log2 = t->bin_slice_log2;
+    }
+    if (t->bin_tile_pairs) {
+        if (t->bin_tile_pairs < 64 || t->bin_tile_pairs > 4096 || (t->bin_tile_pairs & 63))
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_tile_pairs must be a multiple of 64 in [64, 4096]");
+        T.bin_tile_pairs = t->bin_tile_pairs;
+    }
+    if (t->bin_chunk_log2) {
+        if (t->bin_chunk_log2 < 12 || t->bin_chunk_log2 > 28)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_chunk_log2 must be in [12, 28]");
+        T.bin_chunk_log2 = t->bin_chunk_log2;
+    }
+    if (t->bin_slack_pct) T.bin_slack_pct = t->bin_slack_pct == 0xFFFFFFFFu ? 0u : t->bin_slack_pct;
+    if (T.mode == 5) {
+        // the binning tile must fit one block's shared memory
+        const uint64_t total = (uint64_t)h->G.dirs * h->G.dir_words;
+        uint32_t sl = T.bin_slice_log2;
+        while (((total + (1ull << sl) - 1) >> sl) > 4096 && sl < 15) sl++;
+        const uint32_t S = (uint32_t)((total + (1ull << sl) - 1) >> sl);
+        if (bin_smem_bytes(T.bin_tile_pairs, h->G.dirs * h->G.r, S) > 200 * 1024)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: binning tile too large for shared memory");
     }
     h->T = T;
     return SD_OK;

@@ -30,12 +30,28 @@ struct Geometry {
 
 struct Tuning {
     uint32_t mode;           // 0 plain, 1 test-then-set, 2 test + warp de-dup,
-                             // 3 filter + test, 4 filter + plain
+                             // 3 filter + test, 4 filter + plain, 5 binned
     uint32_t block_threads;
     uint32_t blocks_per_sm;
     uint32_t unroll;
     uint32_t filter_log2;    // log2 of the shared-memory filter entries (modes 3, 4)
+    uint32_t bin_slice_log2; // mode 5: DHLA words per slice = 2^bin_slice_log2
+    uint32_t bin_tile_pairs; // mode 5: pairs per binning tile
+    uint32_t bin_chunk_log2; // mode 5: pairs per bin/apply round = 2^bin_chunk_log2
+    uint32_t bin_slack_pct;  // mode 5: bin capacity over the mean fill, in percent
 };
+
+struct BinArgs {
+    uint32_t *bins;          // [S][cap]
+    uint32_t *count;         // [S] entries appended this chunk (may exceed cap)
+    uint32_t *work;          // apply's slice counter
+    uint32_t S;              // slices
+    uint32_t slice_log2;     // words per slice = 2^slice_log2
+    uint32_t cap;            // entries per bin
+    uint32_t tile_pairs;     // pairs per bin tile
+    uint64_t total_words;    // dirs * dir_words
+};
+
 
 constexpr int kSortSmall = 8192;  // hits per direction sorted in one block
 
@@ -132,5 +148,8 @@ cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, u
                             cudaStream_t s, unsigned long long **out);
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
+size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
+cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                                const BinArgs &B, int num_sms, cudaStream_t s);
 
 }  // namespace sd

@@ -67,7 +67,9 @@ class sd_report(ctypes.Structure):
 class sd_tuning(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("unroll", ctypes.c_uint32),
-                ("filter_log2", ctypes.c_uint32)]
+                ("filter_log2", ctypes.c_uint32), ("bin_slice_log2", ctypes.c_uint32),
+                ("bin_tile_pairs", ctypes.c_uint32), ("bin_chunk_log2", ctypes.c_uint32),
+                ("bin_slack_pct", ctypes.c_uint32)]
 
 
 HIT_DTYPE = np.dtype([("ip", "<u4"), ("sz", "<u4"), ("dir", "<u4"), ("reserved", "<u4"),
@@ -290,10 +292,12 @@ def sd_get_tuning(h: Handle) -> sd_tuning:
     return t
 
 
-def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0,
-                  filter_log2=0) -> None:
+def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0, filter_log2=0,
+                  bin_slice_log2=0, bin_tile_pairs=0, bin_chunk_log2=0, bin_slack_pct=0) -> None:
     t = sd_tuning(mode=mode, block_threads=block_threads, blocks_per_sm=blocks_per_sm, unroll=unroll,
-                  filter_log2=filter_log2)
+                  filter_log2=filter_log2, bin_slice_log2=bin_slice_log2,
+                  bin_tile_pairs=bin_tile_pairs, bin_chunk_log2=bin_chunk_log2,
+                  bin_slack_pct=bin_slack_pct)
     _check(lib().sd_set_tuning(h.ptr, ctypes.byref(t)), h.ptr)
 
 

@@ -10,27 +10,39 @@ import itertools
 
 from . import sd
 
-MODES = (0, 1, 2, 3, 4)
+MODES = (0, 1, 2, 3, 4, 5)
 UNROLLS = (1, 2, 4)
 THREADS = (256, 512, 1024)
 FILTERS = (12, 13, 14)   # log2 entries of the shared-memory filter (modes 3, 4)
 
 
+BINNED = [dict(bin_slice_log2=sl, bin_tile_pairs=tp, bin_chunk_log2=ch, bin_slack_pct=100)
+          for sl in (13, 14, 15) for tp in (512, 1024) for ch in (22, 23, 24)]
+
+
 def _space(modes, unrolls, threads, filters):
-    for mode, unroll, nthr in itertools.product(modes, unrolls, threads):
-        for flog in (filters if mode >= 3 else (13,)):
-            yield mode, unroll, nthr, flog
+    for mode in modes:
+        if mode == 5:
+            for b in BINNED:
+                yield dict(mode=5, **b)
+            continue
+        for unroll, nthr in itertools.product(unrolls, threads):
+            for flog in (filters if mode >= 3 else (13,)):
+                yield dict(mode=mode, unroll=unroll, block_threads=nthr, filter_log2=flog)
 
 
 def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, threads=THREADS,
              filters=FILTERS, verbose: bool = False) -> dict:
-    """Time every (mode, unroll, block_threads, filter_log2) on `pairs_dev`;
-    apply and return the best as a dict with the knobs, "ms" and "table"."""
+    """Time every setting of the search space on `pairs_dev`; apply and
+    return the best as a dict with its knobs, "ms" and "table"."""
     import torch
 
     table = []
-    for mode, unroll, nthr, flog in _space(modes, unrolls, threads, filters):
-        sd.sd_set_tuning(h, mode=mode, unroll=unroll, block_threads=nthr, filter_log2=flog)
+    for knobs in _space(modes, unrolls, threads, filters):
+        try:
+            sd.sd_set_tuning(h, **knobs)
+        except sd.SdError:
+            continue  # a setting this DHLA cannot take (e.g. a binning tile too large)
         times = []
         for _ in range(reps):
             sd.sd_close_window(h)  # clears the DHLA: every trial starts from zero
@@ -42,12 +54,10 @@ def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, 
             b.synchronize()
             times.append(a.elapsed_time(b))
         ms = sorted(times)[len(times) // 2]
-        table.append({"mode": mode, "unroll": unroll, "block_threads": nthr, "filter_log2": flog,
-                      "ms": ms})
+        table.append(dict(knobs, ms=ms))
         if verbose:
             print(table[-1], flush=True)
     sd.sd_close_window(h)
     best = min(table, key=lambda r: r["ms"])
-    sd.sd_set_tuning(h, mode=best["mode"], unroll=best["unroll"], block_threads=best["block_threads"],
-                     filter_log2=best["filter_log2"])
+    sd.sd_set_tuning(h, **{k: v for k, v in best.items() if k != "ms"})
     return dict(best, table=table)

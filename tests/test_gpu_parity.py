@@ -100,7 +100,7 @@ def test_tiny_window_full_parity(sd, O, torch_mod):
 @pytest.mark.parametrize("mode,unroll,threads,flog", [
     (0, 1, 256, 13), (0, 4, 1024, 13), (1, 2, 512, 13), (2, 2, 512, 13), (2, 4, 256, 13),
     (1, 1, 128, 13), (3, 2, 512, 13), (3, 1, 1024, 14), (3, 4, 256, 8), (4, 2, 512, 12),
-    (4, 1, 64, 8)])
+    (4, 1, 64, 8), (5, 2, 512, 13)])
 def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, threads, flog):
     w = T.WORKLOADS["tiny"].with_(dirs=2, n=(1 << 19) + 3)
     win = T.make_window(w, 8)
@@ -110,12 +110,29 @@ def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, th
 
 def test_filter_modes_on_heavy_hitters(sd, O, torch_mod):
     """A few hosts carry most of the traffic, so the shared-memory filter of
-    modes 3 and 4 is hit constantly and blocks see bits others have set."""
+    modes 3 and 4 is hit constantly and blocks see bits others have set; in
+    the binned mode 5 a few slices get most bit-sets and their bins overflow
+    into the atomic fallback."""
     w = T.WORKLOADS["core"].with_(n=1 << 21, src_pool=64, zipf_s=1.3, dst_pool=1 << 12,
                                   planted=4, planted_c=("uniform", 3000, 5000))
     win = T.make_window(w, 19)
-    for mode in (3, 4):
-        _full_check(sd, O, torch_mod, w, win, tuning=dict(mode=mode, filter_log2=10))
+    for tuning in (dict(mode=3, filter_log2=10), dict(mode=4, filter_log2=10),
+                   dict(mode=5, bin_chunk_log2=19, bin_slack_pct=0xFFFFFFFF),
+                   dict(mode=5, bin_chunk_log2=21, bin_slack_pct=400)):
+        _full_check(sd, O, torch_mod, w, win, tuning=tuning)
+
+
+@pytest.mark.parametrize("slice_log2,tile,chunk_log2,slack", [
+    (14, 1024, 23, 100), (10, 256, 16, 0xFFFFFFFF), (15, 512, 18, 50), (12, 64, 12, 10),
+    (13, 2048, 20, 100)])
+def test_binned_update_variants(sd, O, torch_mod, slice_log2, tile, chunk_log2, slack):
+    """Mode 5 with slices, tiles, rounds and bin slack from tiny (many rounds,
+    overflowing bins) to large; ragged pair count."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2, n=(1 << 19) + 5)
+    win = T.make_window(w, 23)
+    _full_check(sd, O, torch_mod, w, win,
+                tuning=dict(mode=5, bin_slice_log2=slice_log2, bin_tile_pairs=tile,
+                            bin_chunk_log2=chunk_log2, bin_slack_pct=slack))
 
 
 def test_ragged_and_misaligned_inputs(sd, O, torch_mod):
@@ -211,12 +228,24 @@ def test_core_and_paper_parameters_small_window(sd, O, torch_mod, name):
     _full_check(sd, O, torch_mod, w, T.make_window(w, 99))
 
 
-def test_core_link_window_full_size(sd, O, torch_mod):
+@pytest.mark.parametrize("mode", [None, 1, 5])
+def test_core_link_window_full_size(sd, O, torch_mod, mode):
     """The benchmarked workload itself: 2^26 pairs, g=512, r=4, k=16, both
-    directions, default launch configuration."""
+    directions; the default launch configuration and the update modes the
+    benchmark may pick."""
     w = T.WORKLOADS["core"]
-    rep, ref = _full_check(sd, O, torch_mod, w, T.make_window(w, T.window_seed(2)))
+    win = _core_window()
+    rep, ref = _full_check(sd, O, torch_mod, w, win, tuning=None if mode is None else dict(mode=mode))
     assert rep.n_hits_total > 500
+
+
+_CORE = {}
+
+
+def _core_window():
+    if "win" not in _CORE:
+        _CORE["win"] = T.make_window(T.WORKLOADS["core"], T.window_seed(2))
+    return _CORE["win"]
 
 
 def test_saturated_row(sd, O, torch_mod):
