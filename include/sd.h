@@ -123,7 +123,8 @@ typedef struct {
     uint32_t filter_log2;   /* log2 of the filter's 8-byte entries: 8..14 */
     uint32_t bin_slice_log2; /* mode 5: DHLA words per slice, log2: 10..15 (raised
                                 automatically to keep at most 4096 slices) */
-    uint32_t bin_tile_pairs; /* mode 5: pairs per binning tile: 64..4096, multiple of 64 */
+    uint32_t bin_tile_pairs; /* mode 5: pairs per binning tile: a power of two, 64..2048
+                                (64..1024 when dirs*r > 8) */
     uint32_t bin_chunk_log2; /* mode 5: pairs per bin-then-apply round, log2: 12..28 */
     uint32_t bin_slack_pct;  /* mode 5: bin capacity above the mean fill, percent
                                 (0xFFFFFFFF sets 0); a full bin falls back to atomics */

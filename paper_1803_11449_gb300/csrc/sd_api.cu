@@ -703,9 +703,11 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
         T.bin_slice_log2 = t->bin_slice_log2;
     }
     if (t->bin_tile_pairs) {
-        if (t->bin_tile_pairs < 64 || t->bin_tile_pairs > 4096 || (t->bin_tile_pairs & 63))
-            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_tile_pairs must be a multiple of 64 in [64, 4096]");
-        T.bin_tile_pairs = t->bin_tile_pairs;
+        const uint32_t tp = t->bin_tile_pairs;
+        const uint32_t tmax = h->G.dirs * h->G.r > 8 ? 1024u : 2048u;
+        if (tp < 64 || tp > tmax || (tp & (tp - 1)))
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_tile_pairs must be a power of two in [64, %u]", tmax);
+        T.bin_tile_pairs = tp;
     }
     if (t->bin_chunk_log2) {
         if (t->bin_chunk_log2 < 12 || t->bin_chunk_log2 > 28)

@@ -32,7 +32,7 @@ namespace sd {
 struct DirConst {
     uint32_t A0;
     uint64_t A1, B1;
-    uint64_t base;  // first word of the direction
+    uint32_t base;  // first word of the direction (the DHLA has < 2^32 words here)
 };
 
 __device__ __forceinline__ DirConst dir_const(const Geometry &G, uint32_t d) {
@@ -40,55 +40,66 @@ __device__ __forceinline__ DirConst dir_const(const Geometry &G, uint32_t d) {
     c.A0 = d ? G.h[1].A0 : G.h[0].A0;
     c.A1 = d ? G.h[1].A1 : G.h[0].A1;
     c.B1 = d ? G.h[1].B1 : G.h[0].B1;
-    c.base = d ? G.dir_words : 0ull;
+    c.base = d ? (uint32_t)G.dir_words : 0u;
     return c;
 }
 
-__device__ __forceinline__ uint64_t bit_word(const Geometry &G, const DirConst &c, uint32_t i, uint32_t key,
-                                             uint32_t c0, uint32_t b) {
-    const uint32_t ci = (i == 0) ? c0 : dh_row(G, i, key, c0);
-    return c.base + (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc + (b >> 5);
-}
-
-// Shared memory of k_bin: tile pairs (2 words each), per-update (slice,
-// rank), the slice-sorted entries, and per-slice histogram / offsets / bases.
+// k_bin: a block handles tiles of blockDim*PPT pairs; each thread keeps the
+// DIRS*R bit-sets of its PPT pairs in registers while the block counts them
+// per slice, scans the counts, reserves runs in the bins, and scatters the
+// entries into slice order in shared memory.  The write-out then walks the
+// sorted entries with one thread per entry, so each slice's run is written
+// with consecutive addresses.  A sorted entry is slice << 20 | local, where
+// local = (word mod 2^slice_log2) << 5 | bit (slice_log2 <= 15, at most 4096
+// slices).
+template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
-k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B) {
+k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
+      uint32_t lwpc) {
+    constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
     extern __shared__ uint32_t sm[];
-    const uint32_t TP = B.tile_pairs;
-    const uint32_t upd_per_pair = G.dirs * G.r;
-    const uint32_t U = TP * upd_per_pair;  // bit-sets per tile
-    uint32_t *spairs = sm;                 // [2*TP]
-    uint32_t *meta = spairs + 2 * TP;      // [U]: slice << 20 | rank
-    uint32_t *sorted = meta + U;           // [U]
-    uint32_t *hist = sorted + U;           // [S]
-    uint32_t *offs = hist + B.S;           // [S]
-    uint32_t *base = offs + B.S;           // [S]
+    uint32_t *sorted = sm;                               // [blockDim * UPT]
+    uint32_t *hist = sorted + blockDim.x * UPT;          // [S]
+    uint32_t *offs = hist + B.S;                         // [S]
+    uint32_t *base = offs + B.S;                         // [S]
     __shared__ uint32_t warp_tot[32];
 
-    for (uint32_t s = threadIdx.x; s < B.S; s += blockDim.x) hist[s] = 0;
+    const uint32_t TP = blockDim.x * PPT;
     const uint64_t ntiles = (n + TP - 1) / TP;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t smask = (1u << B.slice_log2) - 1u;
+    const uint32_t sl = B.slice_log2, smask = (1u << sl) - 1u;
+    const uint32_t kmask = (1u << G.k) - 1u, rw = (uint32_t)G.row_words;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *B.work = 0;  // k_apply's slice counter
+    for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
 
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t p0 = t * TP;
-        const uint32_t np = (uint32_t)((n - p0) < TP ? (n - p0) : TP);
-        __syncthreads();  // previous tile fully written out; hist is zero
-        for (uint32_t q = threadIdx.x; q < 2 * np; q += blockDim.x) spairs[q] = ld_stream_u32(pairs + 2 * p0 + q);
-        __syncthreads();
-        // pass 1: slice of every bit-set and its rank inside the slice.
-        // Update (d, i) of pair p is stored at meta[(d*r + i)*TP + p].
-        for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
-            const uint32_t src = spairs[2 * p], dst = spairs[2 * p + 1];
-            for (uint32_t d = 0; d < G.dirs; d++) {
+        const uint64_t p0 = t * TP + (uint64_t)threadIdx.x * PPT;
+        uint32_t src[PPT], dst[PPT];
+        bool ok[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; j++) {
+            ok[j] = p0 + j < n;
+            src[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j)) : 0u;
+            dst[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j) + 1) : 0u;
+        }
+        __syncthreads();  // previous tile written out, hist zero again
+        uint32_t ent[UPT], met[UPT];
+#pragma unroll
+        for (int j = 0; j < PPT; j++) {
+#pragma unroll
+            for (int d = 0; d < DIRS; d++) {
                 const DirConst c = dir_const(G, d);
-                const uint32_t key = d ? dst : src, elem = d ? src : dst;
+                const uint32_t key = d ? dst[j] : src[j], elem = d ? src[j] : dst[j];
                 const uint32_t b = (uint32_t)((c.A1 * (uint64_t)elem + c.B1) >> (64u - G.lg));
                 const uint32_t c0 = dh0(c.A0, G.k, key);
-                for (uint32_t i = 0; i < G.r; i++) {
-                    const uint32_t s = (uint32_t)(bit_word(G, c, i, key, c0, b) >> B.slice_log2);
-                    meta[(d * G.r + i) * TP + p] = (s << 20) | atomicAdd(&hist[s], 1u);
+#pragma unroll
+                for (int i = 0; i < R; i++) {
+                    const uint32_t ci = (i == 0) ? c0 : ((shr_clamp(key, (i - 1) * G.alpha) & kmask) ^ c0);
+                    const uint32_t w = c.base + (uint32_t)i * rw + (ci << lwpc) + (b >> 5);
+                    const uint32_t s = w >> sl;
+                    const int u = (j * DIRS + d) * R + i;
+                    ent[u] = (s << 20) | ((w & smask) << 5) | (b & 31u);
+                    met[u] = ok[j] ? atomicAdd(&hist[s], 1u) : 0u;
                 }
             }
         }
@@ -96,9 +107,9 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
             const uint32_t per = (B.S + blockDim.x - 1) / blockDim.x;
-            const uint32_t s0 = threadIdx.x * per, s1 = min(s0 + per, B.S);
+            const uint32_t s0 = min(threadIdx.x * per, B.S), s1 = min(s0 + per, B.S);
             uint32_t cnt = 0;
-            for (uint32_t s = s0; s < s1; s++) cnt += hist[s];
+            for (uint32_t q = s0; q < s1; q++) cnt += hist[q];
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -118,46 +129,34 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             }
             __syncthreads();
             uint32_t run = incl - cnt + (wid ? warp_tot[wid - 1] : 0);
-            for (uint32_t s = s0; s < s1; s++) {
-                offs[s] = run;
-                run += hist[s];
-                base[s] = hist[s] ? atomicAdd(&B.count[s], hist[s]) : 0u;
+            for (uint32_t q = s0; q < s1; q++) {
+                const uint32_t hq = hist[q];
+                offs[q] = run;
+                run += hq;
+                base[q] = hq ? atomicAdd(&B.count[q], hq) : 0u;
             }
         }
         __syncthreads();
-        // pass 2: place every entry at its slice's offset + rank
-        for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
-            const uint32_t src = spairs[2 * p], dst = spairs[2 * p + 1];
-            for (uint32_t d = 0; d < G.dirs; d++) {
-                const DirConst c = dir_const(G, d);
-                const uint32_t key = d ? dst : src, elem = d ? src : dst;
-                const uint32_t b = (uint32_t)((c.A1 * (uint64_t)elem + c.B1) >> (64u - G.lg));
-                const uint32_t c0 = dh0(c.A0, G.k, key);
-                for (uint32_t i = 0; i < G.r; i++) {
-                    const uint64_t w = bit_word(G, c, i, key, c0, b);
-                    const uint32_t m = meta[(d * G.r + i) * TP + p];
-                    sorted[offs[m >> 20] + (m & 0xFFFFFu)] = (((uint32_t)w & smask) << 5) | (b & 31u);
-                }
-            }
-        }
+        // scatter into slice order
+#pragma unroll
+        for (int u = 0; u < UPT; u++)
+            if (ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
         __syncthreads();
-        // write-out: one warp per slice run, coalesced; overflow -> red.or
-        for (uint32_t s = wid; s < B.S; s += nwarps) {
-            const uint32_t len = hist[s];
-            if (!len) continue;
-            const uint32_t o = offs[s], bs = base[s];
-            for (uint32_t k = lane; k < len; k += 32) {
-                const uint32_t e = sorted[o + k];
-                if (bs + k < B.cap) {
-                    B.bins[(uint64_t)s * B.cap + bs + k] = e;
-                } else {
-                    const uint64_t w = ((uint64_t)s << B.slice_log2) | (e >> 5);
-                    red_or(grid + w, 1u << (e & 31u));
-                }
+        // write-out, one thread per entry; full bins fall back to red.or
+        const uint64_t left = n - t * TP;
+        const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
+        for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
+            const uint32_t e = sorted[q];
+            const uint32_t s = e >> 20;
+            const uint32_t pos = base[s] + (q - offs[s]);
+            if (pos < B.cap) {
+                B.bins[(uint64_t)s * B.cap + pos] = e;
+            } else {
+                const uint32_t w = (s << sl) | ((e & 0xFFFFFu) >> 5);
+                red_or(grid + w, 1u << (e & 31u));
             }
-            __syncwarp();
-            if (lane == 0) hist[s] = 0;
         }
+        for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
     }
 }
 
@@ -177,18 +176,25 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
         __syncthreads();
         const uint32_t cnt = min(B.count[s], B.cap);
         const uint32_t *bin = B.bins + (uint64_t)s * B.cap;
-        // entries: 16-byte loads where aligned (cap is a multiple of 4)
-        for (uint32_t q = threadIdx.x; q < cnt / 4; q += blockDim.x) {
-            const uint4 e = ld_stream_v4(reinterpret_cast<const uint4 *>(bin) + q);
-            atomicOr(&slice[e.x >> 5], 1u << (e.x & 31u));
-            atomicOr(&slice[e.y >> 5], 1u << (e.y & 31u));
-            atomicOr(&slice[e.z >> 5], 1u << (e.z & 31u));
-            atomicOr(&slice[e.w >> 5], 1u << (e.w & 31u));
+        const uint4 *bin4 = reinterpret_cast<const uint4 *>(bin);
+        const uint32_t n4 = cnt / 4;  // cap is a multiple of 4: 16-byte aligned rows
+#define SD_APPLY1(e) atomicOr(&slice[((e) & 0xFFFFFu) >> 5], 1u << ((e) & 31u))
+        uint32_t q = threadIdx.x;
+        for (; q + blockDim.x < n4; q += 2 * blockDim.x) {
+            const uint4 a = ld_stream_v4(bin4 + q);
+            const uint4 b = ld_stream_v4(bin4 + q + blockDim.x);
+            SD_APPLY1(a.x); SD_APPLY1(a.y); SD_APPLY1(a.z); SD_APPLY1(a.w);
+            SD_APPLY1(b.x); SD_APPLY1(b.y); SD_APPLY1(b.z); SD_APPLY1(b.w);
         }
-        for (uint32_t q = (cnt & ~3u) + threadIdx.x; q < cnt; q += blockDim.x) {
-            const uint32_t e = ld_stream_u32(bin + q);
-            atomicOr(&slice[e >> 5], 1u << (e & 31u));
+        for (; q < n4; q += blockDim.x) {
+            const uint4 a = ld_stream_v4(bin4 + q);
+            SD_APPLY1(a.x); SD_APPLY1(a.y); SD_APPLY1(a.z); SD_APPLY1(a.w);
         }
+        for (uint32_t r = 4 * n4 + threadIdx.x; r < cnt; r += blockDim.x) {
+            const uint32_t e = ld_stream_u32(bin + r);
+            SD_APPLY1(e);
+        }
+#undef SD_APPLY1
         __syncthreads();
         // OR the slice into the DHLA (this block is the slice's only writer)
         const uint64_t w0 = (uint64_t)s << B.slice_log2;
@@ -207,34 +213,63 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
     }
 }
 
-__global__ void k_zero_u32(uint32_t *p, uint32_t n) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
-}
-
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S) {
-    return ((size_t)2 * tile_pairs + 2ull * tile_pairs * upd_per_pair + 3ull * S) * 4;
+    return ((size_t)tile_pairs * upd_per_pair + 3ull * S) * 4;
 }
 
-// One chunk: bin then apply.  `scratch` holds bins, counts and the work
-// counter as laid out by the caller (see BinLayout in the API).
-cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
-                                const BinArgs &B, int num_sms, cudaStream_t s) {
-    const size_t smem_bin = bin_smem_bytes(B.tile_pairs, G.dirs * G.r, B.S);
-    const size_t smem_apply = (size_t)4 << B.slice_log2;
-    cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bin);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_apply);
+template <int R, int DIRS, int PPT>
+static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                              const BinArgs &B, int num_sms, cudaStream_t s) {
+    auto kern = k_bin<R, DIRS, PPT>;
+    const uint32_t threads = B.tile_pairs / PPT;
+    const size_t smem = bin_smem_bytes(B.tile_pairs, DIRS * R, B.S);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin, 512, smem_bin);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = (n + B.tile_pairs - 1) / B.tile_pairs;
     uint64_t blocks = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     if (tiles < blocks) blocks = tiles ? tiles : 1;
-    k_bin<<<(unsigned)blocks, 512, smem_bin, s>>>(pairs, n, grid, G, B);
-    e = cudaGetLastError();
+    uint32_t lwpc = 0;
+    while ((1u << lwpc) < G.wpc) lwpc++;
+    kern<<<(unsigned)blocks, threads, smem, s>>>(pairs, n, grid, G, B, lwpc);
+    return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_bin_r(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                                const BinArgs &B, int num_sms, cudaStream_t s) {
+    // 2 pairs per thread up to 1024-pair tiles (512 threads), else 4; the
+    // API keeps tiles at 1024 pairs when dirs*r > 8 so registers suffice
+    const bool two = B.tile_pairs <= 1024 || G.dirs * G.r > 8;
+    if (G.dirs == 2) {
+        if constexpr (2 * R <= 8) {
+            if (!two) return launch_bin<R, 2, 4>(pairs, n, grid, G, B, num_sms, s);
+        }
+        return launch_bin<R, 2, 2>(pairs, n, grid, G, B, num_sms, s);
+    }
+    return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s)
+               : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s);
+}
+
+// One chunk: bin then apply (stream-ordered).
+cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                                const BinArgs &B, int num_sms, cudaStream_t s) {
+    cudaError_t e;
+    switch (G.r) {
+        case 3: e = launch_bin_r<3>(pairs, n, grid, G, B, num_sms, s); break;
+        case 4: e = launch_bin_r<4>(pairs, n, grid, G, B, num_sms, s); break;
+        case 5: e = launch_bin_r<5>(pairs, n, grid, G, B, num_sms, s); break;
+        case 6: e = launch_bin_r<6>(pairs, n, grid, G, B, num_sms, s); break;
+        case 7: e = launch_bin_r<7>(pairs, n, grid, G, B, num_sms, s); break;
+        case 8: e = launch_bin_r<8>(pairs, n, grid, G, B, num_sms, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return e;
-    k_zero_u32<<<1, 32, 0, s>>>(B.work, 1);
+    const size_t smem_apply = (size_t)4 << B.slice_log2;
+    e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_apply);
+    if (e != cudaSuccess) return e;
     int per_sm_a = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_apply, 1024, smem_apply);
     if (e != cudaSuccess) return e;

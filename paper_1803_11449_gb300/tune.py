@@ -17,7 +17,7 @@ FILTERS = (12, 13, 14)   # log2 entries of the shared-memory filter (modes 3, 4)
 
 
 BINNED = [dict(bin_slice_log2=sl, bin_tile_pairs=tp, bin_chunk_log2=ch, bin_slack_pct=100)
-          for sl in (13, 14, 15) for tp in (512, 1024) for ch in (22, 23, 24)]
+          for sl in (13, 14, 15) for tp in (512, 1024, 2048) for ch in (21, 22, 23, 24)]
 
 
 def _space(modes, unrolls, threads, filters):
