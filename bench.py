@@ -39,6 +39,32 @@ GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
 CPU_SAMPLE_PAIRS = 1 << 23
 
 
+def profiled_traffic(mode: int, n: int):
+    """DRAM bytes per launch set of the update for `n` pairs, from the
+    committed ncu summary of the same kernel source; None when no summary
+    matches the current source (the counters no longer describe it)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1803_11449_gb300", "csrc")
+    files = ["sd_binned.cu", "sd_common.cuh"] if mode == 5 else ["sd_update.cu", "sd_common.cuh"]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    name = "update_binned_core_window.txt" if mode == 5 else "update_inplace_core_window.txt"
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("source_sha256") != h.hexdigest() or "dram_bytes_per_pair" not in fields:
+        return None
+    return float(fields["dram_bytes_per_pair"]) * n
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -209,7 +235,11 @@ def run_ours(args, rank, world, local):
     p = sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream.cuda_stream)
     h = sd.sd_create(p)
     tuned = None
-    if args.mode is not None or args.unroll or args.threads:
+    if args.tuning:
+        knobs = {kv.split("=")[0]: int(kv.split("=")[1], 0) for kv in args.tuning.split(",")}
+        knobs.setdefault("mode", sd.sd_get_tuning(h).mode)
+        sd.sd_set_tuning(h, **knobs)
+    elif args.mode is not None or args.unroll or args.threads:
         sd.sd_set_tuning(h, mode=args.mode if args.mode is not None else sd.sd_get_tuning(h).mode,
                          unroll=args.unroll, block_threads=args.threads)
     elif args.autotune:
@@ -294,10 +324,13 @@ def run_ours(args, rank, world, local):
         "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
         "update_ms": 1e3 * t_upd,
-        "bitsets_per_s": p.r * p.dirs * n / t_upd,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_update", "peak_source": f"hbm_gbs, {peak_kind}"},
+                     "frac": achieved / peak, "traffic": profiled_traffic(tuning.mode, n),
+                     "kernel": "k_bin+k_apply" if tuning.mode == 5 else "k_update",
+                     "peak_source": f"hbm_gbs, {peak_kind}",
+                     "algorithmic_bytes_per_pair": BYTES_PER_PAIR},
+        "l2_random_op_roofline": {"ops_per_pair": p.r * p.dirs,
+                                  "achieved_ops_per_s": p.r * p.dirs * n / t_upd},
         "e2e": {"value": e2e, "unit": "Gpps", "h2d_bytes_per_step": BYTES_PER_PAIR * n,
                 "d2h_bytes_per_step": int(d2h / max(1, args.e2e_steps))},
         "gpu_launches": 6 * args.steps,
@@ -324,6 +357,8 @@ def main():
     ap.add_argument("--mode", type=int, default=None)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tuning", default="",
+                    help="update-kernel knobs, e.g. mode=5,bin_slice_log2=15,bin_chunk_log2=24")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the update kernel's launch knobs by timing them first")
     ap.add_argument("--traffic", default="core", choices=["core", "uniform"],

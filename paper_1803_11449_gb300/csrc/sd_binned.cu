@@ -58,10 +58,16 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
       uint32_t lwpc) {
     constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
     extern __shared__ uint32_t sm[];
-    uint32_t *sorted = sm;                               // [blockDim * UPT]
+    // per slice: destination of sorted entry q is dst + q while q < lim
+    struct Slot {
+        uint32_t *dst;
+        uint32_t lim;
+        uint32_t pad;
+    };
+    Slot *slot = reinterpret_cast<Slot *>(sm);           // [S], 16-byte aligned
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(slot + B.S);  // [blockDim * UPT]
     uint32_t *hist = sorted + blockDim.x * UPT;          // [S]
     uint32_t *offs = hist + B.S;                         // [S]
-    uint32_t *base = offs + B.S;                         // [S]
     __shared__ uint32_t warp_tot[32];
 
     const uint32_t TP = blockDim.x * PPT;
@@ -132,8 +138,16 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             for (uint32_t q = s0; q < s1; q++) {
                 const uint32_t hq = hist[q];
                 offs[q] = run;
+                if (hq) {
+                    const uint32_t b0 = atomicAdd(&B.count[q], hq);
+                    // entries q' = run + k go to bins[q][b0 + k] while b0 + k < cap
+                    Slot sq;
+                    sq.dst = B.bins + (uint64_t)q * B.cap + b0 - run;
+                    sq.lim = b0 < B.cap ? run + (B.cap - b0) : run;
+                    sq.pad = 0;
+                    slot[q] = sq;
+                }
                 run += hq;
-                base[q] = hq ? atomicAdd(&B.count[q], hq) : 0u;
             }
         }
         __syncthreads();
@@ -148,9 +162,9 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
             const uint32_t e = sorted[q];
             const uint32_t s = e >> 20;
-            const uint32_t pos = base[s] + (q - offs[s]);
-            if (pos < B.cap) {
-                B.bins[(uint64_t)s * B.cap + pos] = e;
+            const Slot sq = slot[s];
+            if (q < sq.lim) {
+                sq.dst[q] = e;
             } else {
                 const uint32_t w = (s << sl) | ((e & 0xFFFFFu) >> 5);
                 red_or(grid + w, 1u << (e & 31u));
@@ -180,11 +194,14 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
         const uint32_t n4 = cnt / 4;  // cap is a multiple of 4: 16-byte aligned rows
 #define SD_APPLY1(e) atomicOr(&slice[((e) & 0xFFFFFu) >> 5], 1u << ((e) & 31u))
         uint32_t q = threadIdx.x;
-        for (; q + blockDim.x < n4; q += 2 * blockDim.x) {
-            const uint4 a = ld_stream_v4(bin4 + q);
-            const uint4 b = ld_stream_v4(bin4 + q + blockDim.x);
-            SD_APPLY1(a.x); SD_APPLY1(a.y); SD_APPLY1(a.z); SD_APPLY1(a.w);
-            SD_APPLY1(b.x); SD_APPLY1(b.y); SD_APPLY1(b.z); SD_APPLY1(b.w);
+        for (; q + 3 * blockDim.x < n4; q += 4 * blockDim.x) {
+            uint4 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] = ld_stream_v4(bin4 + q + j * blockDim.x);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                SD_APPLY1(v[j].x); SD_APPLY1(v[j].y); SD_APPLY1(v[j].z); SD_APPLY1(v[j].w);
+            }
         }
         for (; q < n4; q += blockDim.x) {
             const uint4 a = ld_stream_v4(bin4 + q);
@@ -214,7 +231,7 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
 }
 
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S) {
-    return ((size_t)tile_pairs * upd_per_pair + 3ull * S) * 4;
+    return (size_t)S * 16 + ((size_t)tile_pairs * upd_per_pair + 2ull * S) * 4;
 }
 
 template <int R, int DIRS, int PPT>

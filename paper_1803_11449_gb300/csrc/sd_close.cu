@@ -45,6 +45,13 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 __global__ void __launch_bounds__(256)
 k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *__restrict__ hotmap,
             StatBlock *__restrict__ st) {
+    __shared__ unsigned long long s_zr[2 * kMaxRows];
+    __shared__ unsigned s_nhot[2 * kMaxRows];
+    if (threadIdx.x < 2 * kMaxRows) {
+        s_zr[threadIdx.x] = 0;
+        s_nhot[threadIdx.x] = 0;
+    }
+    __syncthreads();
     const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint32_t lane = threadIdx.x & 31u;
@@ -64,11 +71,18 @@ k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *_
         const unsigned hot = __ballot_sync(0xFFFFFFFFu, (int)z0 <= zhot);
         const uint32_t zsum = warp_sum(z0);
         if (lane == 0) {
-            const uint64_t row = q >> G.k;  // dir * r + i
+            const uint32_t row = (uint32_t)(q >> G.k);  // dir * r + i
             hotmap[q >> 5] = hot;
-            atomicAdd(&st->zr[0][0] + (row / G.r) * kMaxRows + row % G.r, (unsigned long long)zsum);
-            if (hot) atomicAdd(&st->nhot[0][0] + (row / G.r) * kMaxRows + row % G.r, (unsigned)__popc(hot));
+            atomicAdd(&s_zr[row], (unsigned long long)zsum);
+            atomicAdd(&s_nhot[row], (unsigned)__popc(hot));
         }
+    }
+    __syncthreads();
+    // one global atomic per block and row
+    for (uint32_t row = threadIdx.x; row < G.dirs * G.r; row += blockDim.x) {
+        const uint32_t d = row / G.r, i = row % G.r;
+        if (s_zr[row]) atomicAdd(&st->zr[d][i], s_zr[row]);
+        if (s_nhot[row]) atomicAdd(&st->nhot[d][i], s_nhot[row]);
     }
 }
 
@@ -145,12 +159,12 @@ k_restore(Geometry G, RestoreArgs A) {
 
     // rows 2..r-1 of the hot bitmap; row i is at hot2 + (i-2)*nw
     const uint32_t *hot2 = bm_dir + 2 * nw;
-    uint32_t *tile = smem;
     if (A.smem_hot) {
-        uint32_t *sb = smem + A.tile0;
+        uint32_t *sb = smem;
         const uint32_t words = (G.r - 2) * nw;
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sb[w] = hot2[w];
         hot2 = sb;
+        __syncthreads();
     }
 
     const uint32_t lane = threadIdx.x & 31u;
@@ -168,9 +182,6 @@ k_restore(Geometry G, RestoreArgs A) {
         const uint64_t jc = t % nchunk;
         const uint32_t c0_base = t0 * A.tile0;
         const uint32_t nc0 = min(A.tile0, n0 - c0_base);
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < nc0; q += blockDim.x) tile[q] = he0[c0_base + q];
-        __syncthreads();
         for (uint32_t m = 0; m < iters; m++) {
             const uint64_t j = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
             const bool jvalid = j < J;
@@ -178,7 +189,7 @@ k_restore(Geometry G, RestoreArgs A) {
             const uint32_t tt = (uint32_t)(j & ((1ull << A.ulog) - 1ull));
             const uint32_t c1 = jvalid ? he1[i1] : 0u;
             for (uint32_t q = 0; q < nc0; q++) {
-                const uint32_t c0 = tile[q];
+                const uint32_t c0 = __ldg(he0 + c0_base + q);  // same for the whole block
                 const uint32_t L = c0 ^ c1;                 // BL(1): the low k bits of a
                 const uint32_t Q = A0 * L;
                 const uint32_t Qh = Q >> k, Ql = Q & kmask;
@@ -245,6 +256,20 @@ __device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long 
     }
 }
 
+// Bitonic sort of s[0, P) (P a power of two) by the whole block: each stage
+// visits the P/2 compare-exchange pairs (i, i + j) directly.
+__device__ __forceinline__ void bitonic_smem(unsigned long long *s, unsigned P) {
+    for (unsigned kk = 2; kk <= P; kk <<= 1) {
+        for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+            for (unsigned t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const unsigned i = 2 * t - (t & (j - 1));  // low index of the t-th pair
+                cswap(s[i], s[i + j], (i & kk) == 0);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One block per direction: bitonic sort of up to kSortSmall hits in shared
 // memory (padding with all-ones keys, which sort last).
 __global__ void __launch_bounds__(1024)
@@ -264,15 +289,7 @@ k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 r
     unsigned long long *hd = hits + (uint64_t)dir * hits_cap;
     for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < nn ? hd[i] : ~0ull;
     __syncthreads();
-    for (unsigned kk = 2; kk <= P; kk <<= 1) {
-        for (unsigned j = kk >> 1; j > 0; j >>= 1) {
-            for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
-                const unsigned ix = i ^ j;
-                if (ix > i) cswap(s[i], s[ix], (i & kk) == 0);
-            }
-            __syncthreads();
-        }
-    }
+    bitonic_smem(s, P);
     for (unsigned i = threadIdx.x; i < nn; i += blockDim.x) hd[i] = s[i];
 }
 
@@ -290,15 +307,7 @@ k_sort_segments(unsigned long long *keys, uint64_t n) {
     unsigned long long *kd = keys + base;
     for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? kd[i] : ~0ull;
     __syncthreads();
-    for (unsigned kk = 2; kk <= P; kk <<= 1) {
-        for (unsigned j = kk >> 1; j > 0; j >>= 1) {
-            for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
-                const unsigned ix = i ^ j;
-                if (ix > i) cswap(s[i], s[ix], (i & kk) == 0);
-            }
-            __syncthreads();
-        }
-    }
+    bitonic_smem(s, P);
     for (unsigned i = threadIdx.x; i < len; i += blockDim.x) kd[i] = s[i];
 }
 
@@ -373,12 +382,12 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
     const unsigned threads = 256;
     A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
-    A.tile0 = 32;
-    A.jchunk = threads * 8;
+    A.tile0 = 4;
+    A.jchunk = threads;
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
-    size_t smem = A.tile0 * 4;
-    A.smem_hot = (hot_bytes + smem) <= (size_t)200 * 1024;
-    if (A.smem_hot) smem += hot_bytes;
+    size_t smem = 16;
+    A.smem_hot = hot_bytes <= (size_t)200 * 1024;
+    if (A.smem_hot) smem = hot_bytes;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_restore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
