@@ -52,6 +52,43 @@ __device__ __forceinline__ DirConst dir_const(const Geometry &G, uint32_t d) {
 // with consecutive addresses.  A sorted entry is slice << 20 | local, where
 // local = (word mod 2^slice_log2) << 5 | bit (slice_log2 <= 15, at most 4096
 // slices).
+template <int R, int DIRS, int PPT, bool FULL>
+__device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&base5)[DIRS][R], uint32_t cshift,
+                                         uint32_t kmask, uint32_t sl5, const uint32_t (&src)[PPT],
+                                         const uint32_t (&dst)[PPT], const bool (&ok)[PPT], uint32_t *hist,
+                                         uint32_t (&ent)[PPT * DIRS * R], uint32_t (&met)[PPT * DIRS * R]) {
+    const uint32_t lmask = (1u << sl5) - 1u;
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+#pragma unroll
+        for (int d = 0; d < DIRS; d++) {
+            const uint32_t A0 = d ? G.h[1].A0 : G.h[0].A0;
+            const uint64_t A1 = d ? G.h[1].A1 : G.h[0].A1;
+            const uint64_t B1 = d ? G.h[1].B1 : G.h[0].B1;
+            const uint32_t key = d ? dst[j] : src[j], elem = d ? src[j] : dst[j];
+            const uint32_t b = (uint32_t)((A1 * (uint64_t)elem + B1) >> (64u - G.lg));
+            const uint32_t c0 = dh0(A0, G.k, key);
+#pragma unroll
+            for (int i = 0; i < R; i++) {
+                const uint32_t ci = (i == 0) ? c0 : ((shr_clamp(key, (i - 1) * G.alpha) & kmask) ^ c0);
+                const uint32_t bitidx = base5[d][i] + (ci << cshift) + b;  // global bit index
+                const uint32_t s = bitidx >> sl5;
+                const int u = (j * DIRS + d) * R + i;
+                ent[u] = (s << 20) | (bitidx & lmask);
+                if (FULL || ok[j]) met[u] = atomicAdd(&hist[s], 1u);
+            }
+        }
+    }
+}
+
+// k_bin: a block handles tiles of blockDim*PPT pairs; each thread keeps the
+// DIRS*R bit-sets of its PPT pairs in registers while the block counts them
+// per slice, scans the counts, reserves runs in the bins, and scatters the
+// entries into slice order in shared memory.  The write-out then walks the
+// sorted entries with one thread per entry, so each slice's run is written
+// with consecutive addresses.  A sorted entry is slice << 20 | local, where
+// local = (bit index within the slice) = (word mod 2^slice_log2) << 5 | bit
+// (slice_log2 <= 15, at most 4096 slices, fewer than 2^32 DHLA bits).
 template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
 k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
@@ -73,42 +110,52 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
     const uint32_t TP = blockDim.x * PPT;
     const uint64_t ntiles = (n + TP - 1) / TP;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t sl = B.slice_log2, smask = (1u << sl) - 1u;
-    const uint32_t kmask = (1u << G.k) - 1u, rw = (uint32_t)G.row_words;
+    const uint32_t sl = B.slice_log2, sl5 = sl + 5;
+    const uint32_t kmask = (1u << G.k) - 1u, cshift = lwpc + 5;
+    // first bit of row i of direction d
+    uint32_t base5[DIRS][R];
+#pragma unroll
+    for (int d = 0; d < DIRS; d++)
+#pragma unroll
+        for (int i = 0; i < R; i++)
+            base5[d][i] = ((d ? (uint32_t)G.dir_words : 0u) + (uint32_t)i * (uint32_t)G.row_words) << 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) *B.work = 0;  // k_apply's slice counter
     for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
+    const bool vec = ((uintptr_t)pairs & 15u) == 0;  // 16-byte loads of 2 pairs
 
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t p0 = t * TP + (uint64_t)threadIdx.x * PPT;
+        const bool full = (t + 1) * TP <= n;
         uint32_t src[PPT], dst[PPT];
         bool ok[PPT];
+        if (full && vec) {
+            if (PPT == 2) {
+                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p0));
+                src[0] = v.x; dst[0] = v.y; src[PPT - 1] = v.z; dst[PPT - 1] = v.w;
+            } else {
 #pragma unroll
-        for (int j = 0; j < PPT; j++) {
-            ok[j] = p0 + j < n;
-            src[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j)) : 0u;
-            dst[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j) + 1) : 0u;
+                for (int j = 0; j < PPT; j += 2) {
+                    const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * (p0 + j)));
+                    src[j] = v.x; dst[j] = v.y; src[j + 1] = v.z; dst[j + 1] = v.w;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PPT; j++) ok[j] = true;
+        } else {
+            // partial tile, or pairs only 4- or 8-byte aligned: 32-bit loads
+#pragma unroll
+            for (int j = 0; j < PPT; j++) {
+                ok[j] = p0 + j < n;
+                src[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j)) : 0u;
+                dst[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j) + 1) : 0u;
+            }
         }
         __syncthreads();  // previous tile written out, hist zero again
         uint32_t ent[UPT], met[UPT];
-#pragma unroll
-        for (int j = 0; j < PPT; j++) {
-#pragma unroll
-            for (int d = 0; d < DIRS; d++) {
-                const DirConst c = dir_const(G, d);
-                const uint32_t key = d ? dst[j] : src[j], elem = d ? src[j] : dst[j];
-                const uint32_t b = (uint32_t)((c.A1 * (uint64_t)elem + c.B1) >> (64u - G.lg));
-                const uint32_t c0 = dh0(c.A0, G.k, key);
-#pragma unroll
-                for (int i = 0; i < R; i++) {
-                    const uint32_t ci = (i == 0) ? c0 : ((shr_clamp(key, (i - 1) * G.alpha) & kmask) ^ c0);
-                    const uint32_t w = c.base + (uint32_t)i * rw + (ci << lwpc) + (b >> 5);
-                    const uint32_t s = w >> sl;
-                    const int u = (j * DIRS + d) * R + i;
-                    ent[u] = (s << 20) | ((w & smask) << 5) | (b & 31u);
-                    met[u] = ok[j] ? atomicAdd(&hist[s], 1u) : 0u;
-                }
-            }
-        }
+        if (full)
+            bin_hash<R, DIRS, PPT, true>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
+        else
+            bin_hash<R, DIRS, PPT, false>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
         __syncthreads();
         // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
@@ -154,19 +201,18 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         // scatter into slice order
 #pragma unroll
         for (int u = 0; u < UPT; u++)
-            if (ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
+            if (full || ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
         __syncthreads();
         // write-out, one thread per entry; full bins fall back to red.or
         const uint64_t left = n - t * TP;
         const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
         for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
             const uint32_t e = sorted[q];
-            const uint32_t s = e >> 20;
-            const Slot sq = slot[s];
+            const Slot sq = slot[e >> 20];
             if (q < sq.lim) {
                 sq.dst[q] = e;
             } else {
-                const uint32_t w = (s << sl) | ((e & 0xFFFFFu) >> 5);
+                const uint32_t w = ((e >> 20) << sl) | ((e & 0xFFFFFu) >> 5);
                 red_or(grid + w, 1u << (e & 31u));
             }
         }

@@ -135,7 +135,8 @@ def test_binned_update_variants(sd, O, torch_mod, slice_log2, tile, chunk_log2, 
                             bin_chunk_log2=chunk_log2, bin_slack_pct=slack))
 
 
-def test_ragged_and_misaligned_inputs(sd, O, torch_mod):
+@pytest.mark.parametrize("mode", [1, 3, 5])
+def test_ragged_and_misaligned_inputs(sd, O, torch_mod, mode):
     """Odd pair counts and buffers starting 8 or 4 bytes past a 16-byte
     boundary take the head/tail and unaligned paths."""
     w = T.WORKLOADS["tiny"].with_(dirs=2)
@@ -146,6 +147,7 @@ def test_ragged_and_misaligned_inputs(sd, O, torch_mod):
     for off_words, count in ((0, n - 7), (2, n - 2), (1, 5), (2, 1), (0, 1), (3, 999)):
         p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
         h = sd.sd_create(p)
+        sd.sd_set_tuning(h, mode=mode, bin_chunk_log2=16)
         try:
             if off_words % 2 == 0:
                 view = flat[off_words: off_words + 2 * count]
