@@ -48,6 +48,7 @@ extern "C" {
 #define SD_ERR_SATURATED (-4)       /* some row had ZR(i) = 0: psi = 1, Eq. 4 undefined */
 #define SD_ERR_OVERLOAD (-5)        /* restore work or candidates over their caps */
 #define SD_ERR_REPORT_OVERFLOW (-6) /* more hits than report_cap; count still exact */
+#define SD_ERR_TOO_LARGE (-7)       /* sd_update_noalloc: the DHLA exceeds its fixed scratch */
 
 /* Per-direction flags, in sd_report.flags at bit offset 8*dir. */
 #define SD_FLAG_SATURATED 1u
@@ -201,6 +202,30 @@ int sd_merge(sd_handle *dst, sd_handle *src);
 /* Read or change the update-kernel launch knobs. */
 int sd_get_tuning(const sd_handle *h, sd_tuning *out);
 int sd_set_tuning(sd_handle *h, const sd_tuning *t);
+
+/* The binned update of sd_update (tuning mode 5) without any device
+ * allocation, for callers that cannot allocate: an ingest thread on a
+ * latency budget (cudaMalloc can synchronise the device and take
+ * milliseconds) or a program whose device memory is owned entirely by
+ * another allocator.  There is no counterpart in the paper; it is the same
+ * Algorithm 1 as sd_update.
+ *
+ * Sets, for both directions of *p, the DHLA bits of n (src, dst) pairs.
+ * `grid` is a caller-owned device DHLA of dirs * sd_grid_words(p) words in
+ * the sd_get_grid layout (direction 0 first), 16-byte aligned; `pairs` holds
+ * 2n device words, 4-byte aligned.  Runs on `cuda_stream` (NULL: the legacy
+ * default stream) of the current device and returns once the work is queued.
+ *
+ * Scratch: a 16 MiB array inside the library (every GPU that loads the
+ * library holds it until the process exits).  The first call on a device
+ * looks up that array's address on the device, so make it before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Returns SD_ERR_TOO_LARGE when
+ * the DHLA has more than 512 MiB (4096 slices of 128 KiB) or its bins would
+ * not fit the scratch, SD_ERR_ARG for invalid parameters or pointers,
+ * SD_ERR_CUDA when a CUDA call fails. */
+int sd_update_noalloc(const sd_params *p, uint32_t *grid, const uint32_t *pairs, uint64_t n,
+                      void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ SD_ERR_CUDA = -3
 SD_ERR_SATURATED = -4
 SD_ERR_OVERLOAD = -5
 SD_ERR_REPORT_OVERFLOW = -6
+SD_ERR_TOO_LARGE = -7
 
 SD_FLAG_SATURATED = 1
 SD_FLAG_OVERLOAD_PAIRS = 2
@@ -38,7 +39,7 @@ SD_FLAG_REPORT_OVERFLOW = 8
 EXPORTS = ["sd_default_params", "sd_check_params", "sd_grid_words", "sd_device_bytes", "sd_create",
            "sd_update", "sd_close_window", "sd_sync", "sd_destroy", "sd_last_error", "sd_get_grid",
            "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_get_tuning",
-           "sd_set_tuning"]
+           "sd_set_tuning", "sd_update_noalloc"]
 
 
 class sd_params(ctypes.Structure):
@@ -116,6 +117,7 @@ def lib():
                 "sd_merge": (ctypes.c_int, [_VP, _VP]),
                 "sd_get_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_set_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
+                "sd_update_noalloc": (ctypes.c_int, [_P(sd_params), _VP, _VP, ctypes.c_uint64, _VP]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -299,6 +301,16 @@ def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0,
                   bin_tile_pairs=bin_tile_pairs, bin_chunk_log2=bin_chunk_log2,
                   bin_slack_pct=bin_slack_pct)
     _check(lib().sd_set_tuning(h.ptr, ctypes.byref(t)), h.ptr)
+
+
+def sd_update_noalloc(p: sd_params, grid, pairs, stream=None) -> int:
+    """Binned update into a caller-owned device DHLA `grid` (torch tensor of
+    dirs * sd_grid_words(p) 4-byte words) with no device allocation; returns
+    the C status code.  See include/sd.h for the scratch rules."""
+    gptr, _, _g = _buffer(grid)
+    ptr, n, _keep = _buffer(pairs)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    return lib().sd_update_noalloc(ctypes.byref(p), gptr, ptr if n else None, n, s)
 
 
 def params_for(workload, seed: int, device: int = 0, **over) -> sd_params:
