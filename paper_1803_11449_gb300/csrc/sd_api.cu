@@ -263,7 +263,8 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         G.h[d].B1 = splitmix64(&st);
         G.h[d].A0inv = inverse_odd(G.h[d].A0);
     }
-    h->T = Tuning{1, 512, 0, 2, 13, 14, 1024, 23, 100};
+    // binned update, 128 KiB slices, 1024-pair tiles, 2^24-pair rounds (autotuned on GB300)
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100};
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
