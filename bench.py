@@ -51,6 +51,7 @@ def profiled_traffic(mode: int, n: int):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     name = "update_binned_core_window.txt" if mode == 5 else "update_inplace_core_window.txt"
+    # the counters were taken for one mode-5 round; in-place modes have none committed
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -259,6 +260,7 @@ def run_ours(args, rank, world, local):
     close_ms = []
     dist_barrier(world)
     torch.cuda.synchronize()
+    launches0 = sd.sd_kernel_launches()
     with ClockSampler(local) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
@@ -272,6 +274,7 @@ def run_ours(args, rank, world, local):
             close_ms.append(1e3 * (time.perf_counter() - c0))
         t_end.record(stream)
         torch.cuda.synchronize()
+    launches = sd.sd_kernel_launches() - launches0
     dist_barrier(world)
     elapsed = t_start.elapsed_time(t_end) / 1e3
     upd = [a.elapsed_time(b_) / 1e3 for a, b_ in ev]
@@ -333,7 +336,7 @@ def run_ours(args, rank, world, local):
                                   "achieved_ops_per_s": p.r * p.dirs * n / t_upd},
         "e2e": {"value": e2e, "unit": "Gpps", "h2d_bytes_per_step": BYTES_PER_PAIR * n,
                 "d2h_bytes_per_step": int(d2h / max(1, args.e2e_steps))},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
         "report": {"hits": int(rep.n_hits_total), "n_cand": rep.n_cand,
                    "n_hot_row0": [int(x) for x in rep.n_hot[:, 0]]},
@@ -345,7 +348,7 @@ def run_ours(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)

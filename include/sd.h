@@ -199,6 +199,11 @@ int64_t sd_get_candidates(sd_handle *h, uint32_t dir, uint32_t *host_dst, uint64
  * streams.  Stream-ordered after the work already queued on both handles. */
 int sd_merge(sd_handle *dst, sd_handle *src);
 
+/* Number of CUDA kernels the library has launched in this process, over all
+ * handles (the init clear of sd_create included); for benchmarks that report
+ * their launch count. */
+uint64_t sd_kernel_launches(void);
+
 /* Read or change the update-kernel launch knobs. */
 int sd_get_tuning(const sd_handle *h, sd_tuning *out);
 int sd_set_tuning(sd_handle *h, const sd_tuning *t);

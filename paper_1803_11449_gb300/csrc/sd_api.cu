@@ -10,6 +10,7 @@
 // formulas with the same libm agrees bit for bit.  All per-pair, per-
 // estimator and per-candidate work runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -25,6 +26,9 @@ using namespace sd;
 namespace {
 
 thread_local std::string g_create_error;
+std::atomic<uint64_t> g_launches{0};  // kernels launched by this library, all handles
+
+void launched(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // splitmix64 (Steele, Lea, Flood 2014): the published generator.
 uint64_t splitmix64(uint64_t *state) {
@@ -391,15 +395,18 @@ static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
             for (uint64_t off = 0; off < n; off += chunk) {
                 const uint64_t m = std::min(chunk, n - off);
                 SD_CK(h, launch_binned_chunk(pairs + 2 * off, m, h->grid, h->G, h->bin, h->num_sms, h->stream));
+                launched(2);
             }
             return SD_OK;
         }
         Tuning T = h->T;  // DHLA too large to bin: test-then-set
         T.mode = 1;
         SD_CK(h, launch_update(pairs, n, h->grid, h->G, T, h->num_sms, h->stream));
+        launched(1);
         return SD_OK;
     }
     SD_CK(h, launch_update(pairs, n, h->grid, h->G, h->T, h->num_sms, h->stream));
+    launched(1);
     return SD_OK;
 }
 
@@ -470,6 +477,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
     // hot estimators and row statistics (Algorithm 2, first loop; §4.2)
     SD_CK(h, launch_row_stats(h->grid, G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
     SD_CK(h, launch_compact(h->hotmap, G, h->he, h->stream));
+    launched(2);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
 
@@ -513,6 +521,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         A.hits_cap = h->hits_cap;
         SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
         SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, dirs, h->stream));
+        launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 2 : 1);
         SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
         for (uint32_t d = 0; d < dirs; d++)
             if (A.run[d])
@@ -535,6 +544,9 @@ int sd_close_window(sd_handle *h, sd_report *out) {
                 unsigned long long *sorted = nullptr;
                 SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp, nh, h->num_sms,
                                          h->stream, &sorted));
+                uint64_t rounds = 0;
+                for (uint64_t L = kSortSmall; L < nh; L <<= 1) rounds++;
+                launched(1 + rounds);
                 h->big_h.resize(nh);
                 SD_CK(h, cudaMemcpyAsync(h->big_h.data(), sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
                 SD_CK(h, cudaStreamSynchronize(h->stream));
@@ -562,6 +574,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
 
     // clear the DHLA and the counters for the next window (stream-ordered)
     SD_CK(h, launch_reset(h->grid, (uint64_t)dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
+    launched(1);
 
     out->n_hits_total = h->report.size();
     if (h->report.size() > h->report_cap) {
@@ -653,8 +666,10 @@ int sd_merge(sd_handle *dst, sd_handle *src) {
     SD_CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     cudaError_t e = cudaEventRecord(ev, src->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
         e = launch_merge(dst->grid, src->grid, (uint64_t)a.dirs * dst->G.dir_words, dst->num_sms, dst->stream);
+        if (e == cudaSuccess) launched(1);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev, dst->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);  // src may not change until merged
     cudaEventDestroy(ev);
@@ -662,6 +677,8 @@ int sd_merge(sd_handle *dst, sd_handle *src) {
     dst->n_pairs += src->n_pairs;
     return SD_OK;
 }
+
+uint64_t sd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     if (!h || !out) return SD_ERR_ARG;

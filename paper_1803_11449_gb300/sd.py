@@ -38,8 +38,8 @@ SD_FLAG_REPORT_OVERFLOW = 8
 # every function the header declares, in declaration order
 EXPORTS = ["sd_default_params", "sd_check_params", "sd_grid_words", "sd_device_bytes", "sd_create",
            "sd_update", "sd_close_window", "sd_sync", "sd_destroy", "sd_last_error", "sd_get_grid",
-           "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_get_tuning",
-           "sd_set_tuning", "sd_update_noalloc"]
+           "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_kernel_launches",
+           "sd_get_tuning", "sd_set_tuning", "sd_update_noalloc"]
 
 
 class sd_params(ctypes.Structure):
@@ -115,6 +115,7 @@ def lib():
                 "sd_get_hot": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, _VP]),
                 "sd_get_candidates": (ctypes.c_int64, [_VP, ctypes.c_uint32, _VP, ctypes.c_uint64]),
                 "sd_merge": (ctypes.c_int, [_VP, _VP]),
+                "sd_kernel_launches": (ctypes.c_uint64, []),
                 "sd_get_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_set_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_update_noalloc": (ctypes.c_int, [_P(sd_params), _VP, _VP, ctypes.c_uint64, _VP]),
@@ -286,6 +287,10 @@ def sd_get_candidates(h: Handle, direction: int, cap: int | None = None):
 
 def sd_merge(dst: Handle, src: Handle) -> None:
     _check(lib().sd_merge(dst.ptr, src.ptr), dst.ptr)
+
+
+def sd_kernel_launches() -> int:
+    return int(lib().sd_kernel_launches())
 
 
 def sd_get_tuning(h: Handle) -> sd_tuning:
