@@ -142,7 +142,6 @@ struct sd_handle {
     bool have_close = false;
 
     // binned update (mode 5): scratch sized for the current tuning
-    uint32_t *fullmap = nullptr;       // 1 bit per estimator: all g bits set
     uint32_t *bin_mem = nullptr;       // bins [S][cap], then count [S], then work [1]
     uint64_t bin_mem_words = 0;
     BinArgs bin{};
@@ -237,7 +236,6 @@ static void release(sd_handle *h) {
     cudaFree(h->hits);
     cudaFree(h->hits_tmp);
     cudaFree(h->bin_mem);
-    cudaFree(h->fullmap);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     for (int b = 0; b < 2; b++) {
@@ -379,14 +377,9 @@ static int ensure_bins(sd_handle *h, bool *ok) {
     } else if (B.S != h->bin.S || B.cap != h->bin.cap) {
         SD_CK(h, cudaMemsetAsync(h->bin_mem + (uint64_t)B.S * B.cap, 0, ((uint64_t)B.S + 4) * 4, h->stream));
     }
-    if (!h->fullmap) {
-        const uint64_t cells = ((uint64_t)h->G.dirs * h->G.r) << h->G.k;
-        SD_CK(h, cudaMalloc(&h->fullmap, cells / 8));
-    }
     B.bins = h->bin_mem;
     B.count = h->bin_mem + (uint64_t)B.S * B.cap;
     B.work = B.count + B.S;
-    B.fullmap = h->fullmap;
     h->bin = B;
     return SD_OK;
 }
@@ -401,10 +394,8 @@ static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
             const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
             for (uint64_t off = 0; off < n; off += chunk) {
                 const uint64_t m = std::min(chunk, n - off);
-                // which estimators are already full, as of the previous round
-                SD_CK(h, launch_fullmap(h->grid, h->G, h->fullmap, h->num_sms, h->stream));
                 SD_CK(h, launch_binned_chunk(pairs + 2 * off, m, h->grid, h->G, h->bin, h->num_sms, h->stream));
-                launched(3);
+                launched(2);
             }
             return SD_OK;
         }

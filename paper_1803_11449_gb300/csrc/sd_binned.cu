@@ -56,7 +56,6 @@ template <int R, int DIRS, int PPT, bool FULL>
 __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&base5)[DIRS][R], uint32_t cshift,
                                          uint32_t kmask, uint32_t sl5, const uint32_t (&src)[PPT],
                                          const uint32_t (&dst)[PPT], const bool (&ok)[PPT], uint32_t *hist,
-                                         const uint32_t *__restrict__ fullmap,
                                          uint32_t (&ent)[PPT * DIRS * R], uint32_t (&met)[PPT * DIRS * R]) {
     const uint32_t lmask = (1u << sl5) - 1u;
 #pragma unroll
@@ -76,13 +75,7 @@ __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&bas
                 const uint32_t s = bitidx >> sl5;
                 const int u = (j * DIRS + d) * R + i;
                 ent[u] = (s << 20) | (bitidx & lmask);
-                // an estimator whose g bits are all set needs nothing
-                bool live = FULL || ok[j];
-                if (fullmap && live) {
-                    const uint32_t cell = ((uint32_t)(d * R + i) << G.k) | ci;
-                    live = !((__ldg(fullmap + (cell >> 5)) >> (cell & 31u)) & 1u);
-                }
-                met[u] = live ? atomicAdd(&hist[s], 1u) : 0xFFFFFFFFu;
+                if (FULL || ok[j]) met[u] = atomicAdd(&hist[s], 1u);
             }
         }
     }
@@ -160,9 +153,9 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         __syncthreads();  // previous tile written out, hist zero again
         uint32_t ent[UPT], met[UPT];
         if (full)
-            bin_hash<R, DIRS, PPT, true>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, B.fullmap, ent, met);
+            bin_hash<R, DIRS, PPT, true>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
         else
-            bin_hash<R, DIRS, PPT, false>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, B.fullmap, ent, met);
+            bin_hash<R, DIRS, PPT, false>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
         __syncthreads();
         // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
@@ -205,13 +198,14 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             }
         }
         __syncthreads();
-        // scatter into slice order (skipped bit-sets carry met = all ones)
+        // scatter into slice order
 #pragma unroll
         for (int u = 0; u < UPT; u++)
-            if (met[u] != 0xFFFFFFFFu) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
-        const uint32_t nu = warp_tot[nwarps - 1];  // entries in this tile
+            if (full || ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
         __syncthreads();
         // write-out, one thread per entry; full bins fall back to red.or
+        const uint64_t left = n - t * TP;
+        const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
         for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
             const uint32_t e = sorted[q];
             const Slot sq = slot[e >> 20];
@@ -320,38 +314,6 @@ static cudaError_t launch_bin_r(const uint32_t *pairs, uint64_t n, uint32_t *gri
     }
     return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s)
                : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s);
-}
-
-// Bit per estimator (global index over directions and rows), set when all
-// g bits of the estimator are 1.  One thread per estimator; a warp covers 32
-// consecutive estimators (2^k >= 32), so a ballot writes one word.
-__global__ void __launch_bounds__(256)
-k_fullmap(const uint32_t *__restrict__ grid, Geometry G, uint32_t *__restrict__ fullmap) {
-    const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ncell; q += stride) {
-        const uint32_t *cell = grid + q * G.wpc;
-        uint32_t all = 0xFFFFFFFFu;
-        if ((G.wpc & 3u) == 0) {
-            const uint4 *c4 = reinterpret_cast<const uint4 *>(cell);
-            for (uint32_t w = 0; w < G.wpc / 4; w++) {
-                const uint4 v = __ldg(c4 + w);
-                all &= v.x & v.y & v.z & v.w;
-            }
-        } else {
-            for (uint32_t w = 0; w < G.wpc; w++) all &= __ldg(cell + w);
-        }
-        const unsigned full = __ballot_sync(0xFFFFFFFFu, all == 0xFFFFFFFFu);
-        if ((threadIdx.x & 31u) == 0) fullmap[q >> 5] = full;
-    }
-}
-
-cudaError_t launch_fullmap(const uint32_t *grid, const Geometry &G, uint32_t *fullmap, int num_sms, cudaStream_t s) {
-    const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
-    uint64_t blocks = (ncell + 255) / 256;
-    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
-    k_fullmap<<<(unsigned)blocks, 256, 0, s>>>(grid, G, fullmap);
-    return cudaGetLastError();
 }
 
 // One chunk: bin then apply (stream-ordered).

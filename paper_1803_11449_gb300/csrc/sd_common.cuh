@@ -50,7 +50,6 @@ struct BinArgs {
     uint32_t cap;            // entries per bin
     uint32_t tile_pairs;     // pairs per bin tile
     uint64_t total_words;    // dirs * dir_words
-    const uint32_t *fullmap; // 1 bit per estimator (global index), set when all g bits are 1; or NULL
 };
 
 
@@ -152,6 +151,5 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
 cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                                 const BinArgs &B, int num_sms, cudaStream_t s);
-cudaError_t launch_fullmap(const uint32_t *grid, const Geometry &G, uint32_t *fullmap, int num_sms, cudaStream_t s);
 
 }  // namespace sd
