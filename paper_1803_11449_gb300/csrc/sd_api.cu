@@ -11,7 +11,9 @@
 // estimator and per-candidate work runs in the kernels.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -465,9 +467,30 @@ int sd_sync(sd_handle *h) {
     return SD_OK;
 }
 
+// Host wall-clock of the close phases, printed to stderr when the
+// environment variable SD_TRACE is set (diagnostics; no effect on results).
+struct CloseTrace {
+    bool on = std::getenv("SD_TRACE") != nullptr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
+    double ph[6] = {0, 0, 0, 0, 0, 0};
+    void mark(int i) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        ph[i] += std::chrono::duration<double, std::micro>(now - last).count();
+        last = now;
+    }
+    ~CloseTrace() {
+        if (on)
+            std::fprintf(stderr, "sd_close_window us: stats %.1f restore %.1f bigsort %.1f report %.1f reset %.1f total %.1f\n",
+                         ph[0], ph[1], ph[2], ph[3], ph[4],
+                         std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count());
+    }
+};
+
 int sd_close_window(sd_handle *h, sd_report *out) {
     if (!h || !out) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
+    CloseTrace trace;
     std::memset(out, 0, sizeof *out);
     const Geometry &G = h->G;
     const uint32_t dirs = G.dirs;
@@ -480,6 +503,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
     launched(2);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
+    trace.mark(0);
 
     uint32_t flags = 0;
     RestoreArgs A;
@@ -529,6 +553,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
                                          std::min<uint64_t>(kSortSmall, h->hits_cap) * 8, cudaMemcpyDeviceToHost,
                                          h->stream));
         SD_CK(h, cudaStreamSynchronize(h->stream));
+        trace.mark(1);
         for (uint32_t d = 0; d < dirs; d++) {
             if (!A.run[d]) continue;
             const uint64_t nk = h->st_h->ncand[d];
@@ -551,6 +576,7 @@ int sd_close_window(sd_handle *h, sd_report *out) {
                 SD_CK(h, cudaMemcpyAsync(h->big_h.data(), sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
                 SD_CK(h, cudaStreamSynchronize(h->stream));
                 keys = h->big_h.data();
+                trace.mark(2);
             }
             // Eq. 4 depends on SZ alone within a window: one evaluation per
             // distinct SZ value (hits have SZ <= szmax), bit-identical to
@@ -571,10 +597,12 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         }
     }
     h->have_close = true;
+    trace.mark(3);
 
     // clear the DHLA and the counters for the next window (stream-ordered)
     SD_CK(h, launch_reset(h->grid, (uint64_t)dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
     launched(1);
+    trace.mark(4);
 
     out->n_hits_total = h->report.size();
     if (h->report.size() > h->report_cap) {

@@ -137,9 +137,41 @@ __device__ __forceinline__ bool hot_at(const uint32_t *bm_row, uint32_t c) {
     return (bm_row[c >> 5] >> (c & 31u)) & 1u;
 }
 
+// Per-warp output buffers of k_restore: candidates and hits are reserved in
+// the global lists 32 at a time (one atomic per flush instead of one per
+// finding warp, which serialised on the two counters).
+constexpr int kWarpBuf = 64;
+
+__device__ __forceinline__ void flush_cands(const RestoreArgs &A, uint32_t dir, uint32_t *cbuf, uint32_t &ccount,
+                                            uint32_t lane, bool &overloaded) {
+    if (ccount == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&A.stats->ncand[dir], (unsigned long long)ccount);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t q = lane; q < ccount; q += 32)
+        if (base + q < A.cand_cap) A.cand[(uint64_t)dir * A.cand_cap + base + q] = cbuf[q];
+    if (base + ccount > A.cand_cap) overloaded = true;
+    ccount = 0;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void flush_hits(const RestoreArgs &A, uint32_t dir, unsigned long long *hbuf,
+                                           uint32_t &hcount, uint32_t lane) {
+    if (hcount == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&A.stats->nhits[dir], (unsigned long long)hcount);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t q = lane; q < hcount; q += 32)
+        if (base + q < A.hits_cap) A.hits[(uint64_t)dir * A.hits_cap + base + q] = hbuf[q];
+    hcount = 0;
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(256)
 k_restore(Geometry G, RestoreArgs A) {
     extern __shared__ uint32_t smem[];
+    __shared__ uint32_t s_cbuf[8][kWarpBuf];
+    __shared__ unsigned long long s_hbuf[8][kWarpBuf];
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
     const uint32_t dir = blockIdx.y;
@@ -168,6 +200,10 @@ k_restore(Geometry G, RestoreArgs A) {
     }
 
     const uint32_t lane = threadIdx.x & 31u;
+    uint32_t *cbuf = s_cbuf[threadIdx.x >> 5];
+    unsigned long long *hbuf = s_hbuf[threadIdx.x >> 5];
+    uint32_t ccount = 0, hcount = 0;  // warp-uniform
+    bool overloaded = false;
     const uint64_t J = (uint64_t)n1 << A.ulog;
     const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
     const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
@@ -207,17 +243,12 @@ k_restore(Geometry G, RestoreArgs A) {
                     found = hot_at(hot2 + (uint64_t)(i - 2) * nw, dh_row(G, i, a, c0));
                 const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
                 if (!fb) continue;
-                // append the candidates of this warp to K
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&A.stats->ncand[dir], (unsigned long long)__popc(fb));
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (found) {
-                    const unsigned long long slot = base + __popc(fb & ((1u << lane) - 1u));
-                    if (slot < A.cand_cap) A.cand[(uint64_t)dir * A.cand_cap + slot] = a;
-                }
-                // past the candidate cap the direction is reported as overloaded
-                // and its hits are dropped: keep counting K, skip SZ
-                if (base + __popc(fb) > A.cand_cap) continue;
+                // append the candidates to the warp's buffer; flush 32 at a time
+                if (found) cbuf[ccount + __popc(fb & ((1u << lane) - 1u))] = a;
+                ccount += __popc(fb);
+                __syncwarp();
+                if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane, overloaded);
+                if (overloaded) continue;  // hits of an overloaded direction are dropped
                 // SZ of each candidate, one warp-wide AND + popcount at a time
                 unsigned rest = fb;
                 while (rest) {
@@ -235,16 +266,19 @@ k_restore(Geometry G, RestoreArgs A) {
                     }
                     ones = warp_sum(ones);
                     const uint32_t SZ = G.g - ones;
-                    if (lane == 0 && (int)SZ <= szmax) {
-                        const unsigned long long slot = atomicAdd(&A.stats->nhits[dir], 1ull);
-                        if (slot < A.hits_cap)
-                            A.hits[(uint64_t)dir * A.hits_cap + slot] =
-                                ((unsigned long long)x << 32) | SZ;
+                    if ((int)SZ <= szmax) {
+                        if (lane == 0) hbuf[hcount] = ((unsigned long long)x << 32) | SZ;
+                        hcount++;
+                        __syncwarp();
+                        if (hcount >= 32) flush_hits(A, dir, hbuf, hcount, lane);
                     }
                 }
             }
         }
     }
+    __syncwarp();
+    flush_cands(A, dir, cbuf, ccount, lane, overloaded);
+    if (!overloaded) flush_hits(A, dir, hbuf, hcount, lane);
 }
 
 // ------------------------------------------------------------------- sort

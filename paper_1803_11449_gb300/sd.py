@@ -241,9 +241,9 @@ def sd_close_window(h: Handle, allow=(SD_OK, SD_ERR_SATURATED, SD_ERR_OVERLOAD,
     p = h.params
     n = int(rep.n_hits)
     if n:
-        buf = (ctypes.c_char * (n * HIT_DTYPE.itemsize)).from_address(
-            ctypes.addressof(rep.hits.contents))
-        hits = np.frombuffer(bytes(buf), dtype=HIT_DTYPE)
+        raw = np.ctypeslib.as_array(ctypes.cast(rep.hits, ctypes.POINTER(ctypes.c_uint8)),
+                                    shape=(n * HIT_DTYPE.itemsize,))
+        hits = raw.view(HIT_DTYPE).copy()
     else:
         hits = np.zeros(0, dtype=HIT_DTYPE)
     return Report(
