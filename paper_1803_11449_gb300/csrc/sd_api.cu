@@ -137,7 +137,7 @@ struct sd_handle {
     unsigned long long *hits_tmp = nullptr;  // [hits_cap]: scratch of the large-list sort
     unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
     uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
-    std::vector<unsigned long long> big_h;
+    unsigned long long *big_h = nullptr;  // pinned [hits_cap]: a large sorted hit list
     std::vector<sd_hit> report;
     std::vector<double> est_tbl;
     uint64_t last_ncand[2] = {0, 0};
@@ -240,6 +240,7 @@ static void release(sd_handle *h) {
     cudaFree(h->bin_mem);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
+    cudaFreeHost(h->big_h);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->dstage[b]);
         cudaFreeHost(h->hstage[b]);
@@ -572,10 +573,10 @@ int sd_close_window(sd_handle *h, sd_report *out) {
                 uint64_t rounds = 0;
                 for (uint64_t L = kSortSmall; L < nh; L <<= 1) rounds++;
                 launched(1 + rounds);
-                h->big_h.resize(nh);
-                SD_CK(h, cudaMemcpyAsync(h->big_h.data(), sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
+                if (!h->big_h) SD_CK(h, cudaMallocHost(&h->big_h, h->hits_cap * 8));
+                SD_CK(h, cudaMemcpyAsync(h->big_h, sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
                 SD_CK(h, cudaStreamSynchronize(h->stream));
-                keys = h->big_h.data();
+                keys = h->big_h;
                 trace.mark(2);
             }
             // Eq. 4 depends on SZ alone within a window: one evaluation per
@@ -584,15 +585,19 @@ int sd_close_window(sd_handle *h, sd_report *out) {
             std::vector<double> &tbl = h->est_tbl;
             tbl.assign((size_t)(A.szmax[d] >= 0 ? A.szmax[d] + 1 : 0), 0.0);
             for (size_t z = 0; z < tbl.size(); z++) tbl[z] = eq4(G.g, G.r, psi[d], (uint32_t)z);
-            h->report.reserve(h->report.size() + nh);
+            const size_t at = h->report.size();
+            h->report.resize(at + nh);
+            sd_hit *out_h = h->report.data() + at;
+            const double *t = tbl.data();
+            const size_t tn = tbl.size();
             for (uint64_t q = 0; q < nh; q++) {
-                sd_hit hit;
-                hit.ip = (uint32_t)(keys[q] >> 32);
-                hit.sz = (uint32_t)(keys[q] & 0xFFFFFFFFull);
-                hit.dir = d;
-                hit.reserved = 0;
-                hit.est = hit.sz < tbl.size() ? tbl[hit.sz] : eq4(G.g, G.r, psi[d], hit.sz);
-                h->report.push_back(hit);
+                const unsigned long long key = keys[q];
+                const uint32_t sz = (uint32_t)(key & 0xFFFFFFFFull);
+                out_h[q].ip = (uint32_t)(key >> 32);
+                out_h[q].sz = sz;
+                out_h[q].dir = d;
+                out_h[q].reserved = 0;
+                out_h[q].est = sz < tn ? t[sz] : eq4(G.g, G.r, psi[d], sz);
             }
         }
     }

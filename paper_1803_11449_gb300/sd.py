@@ -246,13 +246,12 @@ def sd_close_window(h: Handle, allow=(SD_OK, SD_ERR_SATURATED, SD_ERR_OVERLOAD,
         hits = raw.view(HIT_DTYPE).copy()
     else:
         hits = np.zeros(0, dtype=HIT_DTYPE)
+    zr = np.frombuffer(rep.zr, dtype=np.uint64).reshape(2, 8)[: p.dirs, : p.r].copy()
+    n_hot = np.frombuffer(rep.n_hot, dtype=np.uint32).reshape(2, 8)[: p.dirs, : p.r].astype(np.int64)
     return Report(
-        rc=rc, n_pairs=int(rep.n_pairs),
-        zr=np.array([[rep.zr[d][i] for i in range(p.r)] for d in range(p.dirs)], dtype=np.uint64),
-        psi=[rep.psi[d] for d in range(p.dirs)],
-        n_hot=np.array([[rep.n_hot[d][i] for i in range(p.r)] for d in range(p.dirs)]),
-        n_cand=[int(rep.n_cand[d]) for d in range(p.dirs)], zhot=int(rep.zhot),
-        szmax=[int(rep.szmax[d]) for d in range(p.dirs)], flags=int(rep.flags),
+        rc=rc, n_pairs=int(rep.n_pairs), zr=zr, psi=list(rep.psi)[: p.dirs], n_hot=n_hot,
+        n_cand=[int(x) for x in list(rep.n_cand)[: p.dirs]], zhot=int(rep.zhot),
+        szmax=[int(x) for x in list(rep.szmax)[: p.dirs]], flags=int(rep.flags),
         n_hits_total=int(rep.n_hits_total), hits=hits)
 
 
