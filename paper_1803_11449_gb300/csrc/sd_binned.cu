@@ -44,8 +44,14 @@ __device__ __forceinline__ DirConst dir_const(const Geometry &G, uint32_t d) {
     return c;
 }
 
-// Hashes of one tile: every bit-set's entry and its rank among the tile's
-// bit-sets of the same slice (an atomic on the slice's shared-memory count).
+// k_bin: a block handles tiles of blockDim*PPT pairs; each thread keeps the
+// DIRS*R bit-sets of its PPT pairs in registers while the block counts them
+// per slice, scans the counts, reserves runs in the bins, and scatters the
+// entries into slice order in shared memory.  The write-out then walks the
+// sorted entries with one thread per entry, so each slice's run is written
+// with consecutive addresses.  A sorted entry is slice << 20 | local, where
+// local = (word mod 2^slice_log2) << 5 | bit (slice_log2 <= 15, at most 4096
+// slices).
 template <int R, int DIRS, int PPT, bool FULL>
 __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&base5)[DIRS][R], uint32_t cshift,
                                          uint32_t kmask, uint32_t sl5, const uint32_t (&src)[PPT],
@@ -78,23 +84,27 @@ __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&bas
 // k_bin: a block handles tiles of blockDim*PPT pairs; each thread keeps the
 // DIRS*R bit-sets of its PPT pairs in registers while the block counts them
 // per slice, scans the counts, reserves runs in the bins, and scatters the
-// entries into slice order in shared memory.  Each slice's run is then
-// written to its bin by one bulk asynchronous copy (TMA), issued by the
-// thread that owns the slice.  Runs are padded to a multiple of 4 entries
-// (16 bytes, the bulk-copy granule) with copies of the run's first entry,
-// which OR the same bit again.  A sorted entry is slice << 20 | local, where
-// local = (word mod 2^slice_log2) << 5 | bit (slice_log2 <= 15, at most 4096
-// slices, fewer than 2^32 DHLA bits).
+// entries into slice order in shared memory.  The write-out then walks the
+// sorted entries with one thread per entry, so each slice's run is written
+// with consecutive addresses.  A sorted entry is slice << 20 | local, where
+// local = (bit index within the slice) = (word mod 2^slice_log2) << 5 | bit
+// (slice_log2 <= 15, at most 4096 slices, fewer than 2^32 DHLA bits).
 template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
 k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
       uint32_t lwpc) {
     constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
-    extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *sorted = sm;                               // [blockDim*UPT + 3*S], 16-byte aligned
-    uint32_t *hist = sorted + blockDim.x * UPT + 3 * B.S;  // [S]
-    uint32_t *offs = hist + B.S;                         // [S] start of the slice's run (multiple of 4)
-    uint32_t *base = offs + B.S;                         // [S] reserved position in the bin
+    extern __shared__ uint32_t sm[];
+    // per slice: destination of sorted entry q is dst + q while q < lim
+    struct Slot {
+        uint32_t *dst;
+        uint32_t lim;
+        uint32_t pad;
+    };
+    Slot *slot = reinterpret_cast<Slot *>(sm);           // [S], 16-byte aligned
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(slot + B.S);  // [blockDim * UPT]
+    uint32_t *hist = sorted + blockDim.x * UPT;          // [S]
+    uint32_t *offs = hist + B.S;                         // [S]
     __shared__ uint32_t warp_tot[32];
 
     const uint32_t TP = blockDim.x * PPT;
@@ -119,10 +129,15 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         uint32_t src[PPT], dst[PPT];
         bool ok[PPT];
         if (full && vec) {
+            if (PPT == 2) {
+                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p0));
+                src[0] = v.x; dst[0] = v.y; src[PPT - 1] = v.z; dst[PPT - 1] = v.w;
+            } else {
 #pragma unroll
-            for (int j = 0; j < PPT; j += 2) {
-                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * (p0 + j)));
-                src[j] = v.x; dst[j] = v.y; src[j + 1] = v.z; dst[j + 1] = v.w;
+                for (int j = 0; j < PPT; j += 2) {
+                    const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * (p0 + j)));
+                    src[j] = v.x; dst[j] = v.y; src[j + 1] = v.z; dst[j + 1] = v.w;
+                }
             }
 #pragma unroll
             for (int j = 0; j < PPT; j++) ok[j] = true;
@@ -135,22 +150,19 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
                 dst[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j) + 1) : 0u;
             }
         }
-        __syncthreads();  // previous tile's counts consumed, hist zero again
+        __syncthreads();  // previous tile written out, hist zero again
         uint32_t ent[UPT], met[UPT];
         if (full)
             bin_hash<R, DIRS, PPT, true>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
         else
             bin_hash<R, DIRS, PPT, false>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
-        // this thread's bulk copies of the previous tile must be done reading
-        // `sorted` before anyone scatters into it again
-        bulk_wait_read();
         __syncthreads();
-        // exclusive scan of the padded counts; reserve each slice's run in its bin
+        // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
             const uint32_t per = (B.S + blockDim.x - 1) / blockDim.x;
             const uint32_t s0 = min(threadIdx.x * per, B.S), s1 = min(s0 + per, B.S);
             uint32_t cnt = 0;
-            for (uint32_t q = s0; q < s1; q++) cnt += (hist[q] + 3u) & ~3u;
+            for (uint32_t q = s0; q < s1; q++) cnt += hist[q];
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -171,10 +183,18 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             __syncthreads();
             uint32_t run = incl - cnt + (wid ? warp_tot[wid - 1] : 0);
             for (uint32_t q = s0; q < s1; q++) {
-                const uint32_t hp = (hist[q] + 3u) & ~3u;
+                const uint32_t hq = hist[q];
                 offs[q] = run;
-                base[q] = hp ? atomicAdd(&B.count[q], hp) : 0u;
-                run += hp;
+                if (hq) {
+                    const uint32_t b0 = atomicAdd(&B.count[q], hq);
+                    // entries q' = run + k go to bins[q][b0 + k] while b0 + k < cap
+                    Slot sq;
+                    sq.dst = B.bins + (uint64_t)q * B.cap + b0 - run;
+                    sq.lim = b0 < B.cap ? run + (B.cap - b0) : run;
+                    sq.pad = 0;
+                    slot[q] = sq;
+                }
+                run += hq;
             }
         }
         __syncthreads();
@@ -182,33 +202,22 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
 #pragma unroll
         for (int u = 0; u < UPT; u++)
             if (full || ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
-        fence_proxy_async_smem();
         __syncthreads();
-        // write-out: one bulk copy per slice run; a run that does not fit its
-        // bin is ORed into the DHLA directly
-        for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) {
-            const uint32_t hq = hist[q];
-            hist[q] = 0;
-            if (!hq) continue;
-            const uint32_t hp = (hq + 3u) & ~3u;
-            uint32_t *run = sorted + offs[q];
-            for (uint32_t k = hq; k < hp; k++) run[k] = run[0];
-            // the part of the reservation below cap is always written, since
-            // k_apply reads the first min(count, cap) entries of the bin
-            const uint32_t b0 = base[q];
-            const uint32_t fit = b0 >= B.cap ? 0u : min(hp, B.cap - b0);  // multiple of 4
-            if (fit) {
-                fence_proxy_async_smem();
-                bulk_store_s2g(B.bins + (uint64_t)q * B.cap + b0, run, fit * 4u);
-                bulk_commit();
-            }
-            for (uint32_t k = fit; k < hq; k++) {
-                const uint32_t e = run[k];
-                red_or(grid + (((uint64_t)q << sl) | ((e & 0xFFFFFu) >> 5)), 1u << (e & 31u));
+        // write-out, one thread per entry; full bins fall back to red.or
+        const uint64_t left = n - t * TP;
+        const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
+        for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
+            const uint32_t e = sorted[q];
+            const Slot sq = slot[e >> 20];
+            if (q < sq.lim) {
+                sq.dst[q] = e;
+            } else {
+                const uint32_t w = ((e >> 20) << sl) | ((e & 0xFFFFFu) >> 5);
+                red_or(grid + w, 1u << (e & 31u));
             }
         }
+        for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
     }
-    bulk_wait_all();
 }
 
 __global__ void __launch_bounds__(1024)
@@ -231,12 +240,12 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
         const uint32_t n4 = cnt / 4;  // cap is a multiple of 4: 16-byte aligned rows
 #define SD_APPLY1(e) atomicOr(&slice[((e) & 0xFFFFFu) >> 5], 1u << ((e) & 31u))
         uint32_t q = threadIdx.x;
-        for (; q + 7 * blockDim.x < n4; q += 8 * blockDim.x) {
-            uint4 v[8];
+        for (; q + 3 * blockDim.x < n4; q += 4 * blockDim.x) {
+            uint4 v[4];
 #pragma unroll
-            for (int j = 0; j < 8; j++) v[j] = ld_stream_v4(bin4 + q + j * blockDim.x);
+            for (int j = 0; j < 4; j++) v[j] = ld_stream_v4(bin4 + q + j * blockDim.x);
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
+            for (int j = 0; j < 4; j++) {
                 SD_APPLY1(v[j].x); SD_APPLY1(v[j].y); SD_APPLY1(v[j].z); SD_APPLY1(v[j].w);
             }
         }
@@ -268,8 +277,7 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
 }
 
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S) {
-    // the sorted entries with room for the padding, then hist, offs, base
-    return ((size_t)tile_pairs * upd_per_pair + 3ull * S + 3ull * S) * 4;
+    return (size_t)S * 16 + ((size_t)tile_pairs * upd_per_pair + 2ull * S) * 4;
 }
 
 template <int R, int DIRS, int PPT>

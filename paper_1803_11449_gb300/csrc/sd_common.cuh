@@ -127,24 +127,6 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Bulk asynchronous copy (TMA engine) of `bytes` from shared to global
-// memory; both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, uint32_t bytes) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Wait until this thread's bulk copies have finished reading shared memory.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// Wait until this thread's bulk copies have completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// Make this thread's generic-proxy shared-memory writes visible to the
-// asynchronous (bulk copy) proxy.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Weak cached load of a DHLA word.  A stale 0 only costs a redundant OR; a
 // stale 1 cannot happen because bits are never cleared inside a window.
 __device__ __forceinline__ uint32_t ld_weak(const uint32_t *p) {
