@@ -545,8 +545,9 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         A.cand_cap = h->cand_cap;
         A.hits_cap = h->hits_cap;
         SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
+        SD_CK(h, launch_estimate(G, A, h->num_sms, h->stream));
         SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, dirs, h->stream));
-        launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 2 : 1);
+        launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 3 : 2);
         SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
         for (uint32_t d = 0; d < dirs; d++)
             if (A.run[d])

@@ -171,14 +171,12 @@ __global__ void __launch_bounds__(256)
 k_restore(Geometry G, RestoreArgs A) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_cbuf[8][kWarpBuf];
-    __shared__ unsigned long long s_hbuf[8][kWarpBuf];
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
     const uint32_t dir = blockIdx.y;
     if (!(dir ? A.run[1] : A.run[0])) return;
     const uint32_t n0 = dir ? A.n0[1] : A.n0[0];
     const uint32_t n1 = dir ? A.n1[1] : A.n1[0];
-    const int szmax = dir ? A.szmax[1] : A.szmax[0];
     if (n0 == 0 || n1 == 0) return;
     const uint32_t k = G.k, kmask = (1u << k) - 1u;
     const uint32_t hmask = (k >= 32u) ? 0u : ((1u << (32u - k)) - 1u);  // 32-k high bits
@@ -201,14 +199,12 @@ k_restore(Geometry G, RestoreArgs A) {
 
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *cbuf = s_cbuf[threadIdx.x >> 5];
-    unsigned long long *hbuf = s_hbuf[threadIdx.x >> 5];
-    uint32_t ccount = 0, hcount = 0;  // warp-uniform
+    uint32_t ccount = 0;  // warp-uniform
     bool overloaded = false;
     const uint64_t J = (uint64_t)n1 << A.ulog;
     const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
     const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
     const uint64_t ntiles = (uint64_t)ntile0 * nchunk;
-    const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
     const uint32_t lowbits = (k >= 16u) ? (2u * k - 32u) : 0u;
     const uint32_t lowmask = (1u << lowbits) - 1u;
     const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
@@ -248,37 +244,55 @@ k_restore(Geometry G, RestoreArgs A) {
                 ccount += __popc(fb);
                 __syncwarp();
                 if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane, overloaded);
-                if (overloaded) continue;  // hits of an overloaded direction are dropped
-                // SZ of each candidate, one warp-wide AND + popcount at a time
-                unsigned rest = fb;
-                while (rest) {
-                    const int src = __ffs(rest) - 1;
-                    rest &= rest - 1u;
-                    const uint32_t x = __shfl_sync(0xFFFFFFFFu, a, src);
-                    uint32_t ones = 0;
-                    for (uint32_t w = lane; w < G.wpc; w += 32) {
-                        uint32_t ule = 0xFFFFFFFFu;
-                        for (uint32_t i = 0; i < G.r; i++) {
-                            const uint32_t ci = (i == 0) ? c0 : dh_row(G, i, x, c0);
-                            ule &= __ldg(gdir + (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc + w);
-                        }
-                        ones += __popc(ule);
-                    }
-                    ones = warp_sum(ones);
-                    const uint32_t SZ = G.g - ones;
-                    if ((int)SZ <= szmax) {
-                        if (lane == 0) hbuf[hcount] = ((unsigned long long)x << 32) | SZ;
-                        hcount++;
-                        __syncwarp();
-                        if (hcount >= 32) flush_hits(A, dir, hbuf, hcount, lane);
-                    }
-                }
             }
         }
     }
     __syncwarp();
     flush_cands(A, dir, cbuf, ccount, lane, overloaded);
-    if (!overloaded) flush_hits(A, dir, hbuf, hcount, lane);
+}
+
+// k_estimate: SZ(a) = zero bits of ULE(a), the AND of a's r estimators, for
+// every candidate in K (one warp per candidate, lanes over the estimator's
+// words); keeps (a, SZ) when SZ <= szmax.  A direction whose K overflowed its
+// capacity is skipped (it reports nothing).
+__global__ void __launch_bounds__(256)
+k_estimate(Geometry G, RestoreArgs A) {
+    __shared__ unsigned long long s_hbuf[8][kWarpBuf];
+    const uint32_t dir = blockIdx.y;
+    if (!(dir ? A.run[1] : A.run[0])) return;
+    const unsigned long long nk = A.stats->ncand[dir];
+    if (nk > A.cand_cap) return;
+    const int szmax = dir ? A.szmax[1] : A.szmax[0];
+    const uint32_t A0 = dir ? G.h[1].A0 : G.h[0].A0;
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned long long *hbuf = s_hbuf[threadIdx.x >> 5];
+    uint32_t hcount = 0;
+    const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
+    const uint32_t *cand = A.cand + (uint64_t)dir * A.cand_cap;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nk; q += nwarps) {
+        const uint32_t x = cand[q];
+        const uint32_t c0 = dh0(A0, G.k, x);
+        uint32_t ones = 0;
+        for (uint32_t w = lane; w < G.wpc; w += 32) {
+            uint32_t ule = 0xFFFFFFFFu;
+            for (uint32_t i = 0; i < G.r; i++) {
+                const uint32_t ci = (i == 0) ? c0 : dh_row(G, i, x, c0);
+                ule &= __ldg(gdir + (uint64_t)i * G.row_words + (uint64_t)ci * G.wpc + w);
+            }
+            ones += __popc(ule);
+        }
+        ones = warp_sum(ones);
+        const uint32_t SZ = G.g - ones;
+        if ((int)SZ <= szmax) {
+            if (lane == 0) hbuf[hcount] = ((unsigned long long)x << 32) | SZ;
+            hcount++;
+            __syncwarp();
+            if (hcount >= 32) flush_hits(A, dir, hbuf, hcount, lane);
+        }
+    }
+    __syncwarp();
+    flush_hits(A, dir, hbuf, hcount, lane);
 }
 
 // ------------------------------------------------------------------- sort
@@ -442,6 +456,12 @@ cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaSt
     if (most < blocks) blocks = most;
     dim3 grid((unsigned)blocks, G.dirs);
     k_restore<<<grid, threads, smem, s>>>(G, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms, cudaStream_t s) {
+    dim3 grid((unsigned)num_sms * 4, G.dirs);
+    k_estimate<<<grid, 256, 0, s>>>(G, A);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ struct BinArgs {
 };
 
 
-constexpr int kSortSmall = 8192;  // hits per direction sorted in one block
+constexpr int kSortSmall = 2048;  // keys sorted by one block in shared memory
 
 // Per-window counters, copied to the host in one transfer.
 struct StatBlock {
@@ -142,6 +142,7 @@ cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, 
                              StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, cudaStream_t s);
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
+cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s);
 cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
