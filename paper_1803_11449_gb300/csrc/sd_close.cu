@@ -137,6 +137,8 @@ __device__ __forceinline__ bool hot_at(const uint32_t *bm_row, uint32_t c) {
     return (bm_row[c >> 5] >> (c & 31u)) & 1u;
 }
 
+constexpr uint32_t kRestoreTileMax = 256;  // c0 values per k_restore tile
+
 // Per-warp output buffers of k_restore: candidates and hits are reserved in
 // the global lists 32 at a time (one atomic per flush instead of one per
 // finding warp, which serialised on the two counters).
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(256)
 k_restore(Geometry G, RestoreArgs A) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_cbuf[8][kWarpBuf];
+    __shared__ uint32_t s_c0[kRestoreTileMax];
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
     const uint32_t dir = blockIdx.y;
@@ -214,6 +217,9 @@ k_restore(Geometry G, RestoreArgs A) {
         const uint64_t jc = t % nchunk;
         const uint32_t c0_base = t0 * A.tile0;
         const uint32_t nc0 = min(A.tile0, n0 - c0_base);
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nc0; q += blockDim.x) s_c0[q] = he0[c0_base + q];
+        __syncthreads();
         for (uint32_t m = 0; m < iters; m++) {
             const uint64_t j = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
             const bool jvalid = j < J;
@@ -221,7 +227,7 @@ k_restore(Geometry G, RestoreArgs A) {
             const uint32_t tt = (uint32_t)(j & ((1ull << A.ulog) - 1ull));
             const uint32_t c1 = jvalid ? he1[i1] : 0u;
             for (uint32_t q = 0; q < nc0; q++) {
-                const uint32_t c0 = __ldg(he0 + c0_base + q);  // same for the whole block
+                const uint32_t c0 = s_c0[q];  // same for the whole block
                 const uint32_t L = c0 ^ c1;                 // BL(1): the low k bits of a
                 const uint32_t Q = A0 * L;
                 const uint32_t Qh = Q >> k, Ql = Q & kmask;
@@ -430,8 +436,16 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
     const unsigned threads = 256;
     A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
-    A.tile0 = 4;
     A.jchunk = threads;
+    // c0 values per tile: enough work per tile to amortise its set-up, while
+    // still giving every resident block about one tile
+    {
+        uint64_t tests = 0;
+        for (uint32_t d = 0; d < G.dirs; d++)
+            if (A.run[d]) tests += (uint64_t)A.n0[d] * ((uint64_t)A.n1[d] << A.ulog);
+        const uint64_t per_block = tests / ((uint64_t)num_sms * 8 * threads) + 1;
+        A.tile0 = (uint32_t)(per_block < kRestoreTileMax ? per_block : kRestoreTileMax);
+    }
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
     size_t smem = 16;
     A.smem_hot = hot_bytes <= (size_t)200 * 1024;
