@@ -352,6 +352,99 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def _batch_window(args):
+    """(pairs, planted count) of link `link` of the batching workload."""
+    link, n, planted = args
+    w = T.WORKLOADS[WORKLOAD].with_(n=n, planted=planted)
+    return T.make_window(w, T.window_seed(3, link=link)).pairs
+
+
+def run_batching(args, rank, world, local):
+    """Many links of uneven size: one window at a time through one handle
+    versus all links batched (sd_update_many + sd_close_many).  Every link
+    uses the core-link sketch; links differ by traffic."""
+    import multiprocessing as mp
+
+    rng = np.random.default_rng(0x5D5A0300 + rank)
+    sizes = np.clip(np.exp(rng.normal(np.log(4 << 20), 1.0, size=args.links)), 256 << 10, 64 << 20)
+    sizes = (sizes.astype(np.int64) // 2) * 2
+    planted = rng.integers(50, 301, size=args.links)
+    jobs = [(rank * args.links + i, int(n), int(p)) for i, (n, p) in enumerate(zip(sizes, planted))]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        wins = pool.map(_batch_window, jobs)
+
+    import torch
+
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    devs = [torch.from_numpy(wn.reshape(-1).view(np.int32)).cuda() for wn in wins]
+    total = int(sum(len(wn) for wn in wins))
+    w = T.WORKLOADS[WORKLOAD]
+    seed = T.window_seed(2)
+    hs = [sd.sd_create(sd.params_for(w, seed=seed, device=local, cuda_stream=stream.cuda_stream))
+          for _ in wins]
+    one = hs[0]
+
+    def one_at_a_time():
+        lat = []
+        for d in devs:
+            sd.sd_update(one, d)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sd.sd_close_window(one)
+            lat.append(time.perf_counter() - t0)
+        return lat
+
+    def batched():
+        sd.sd_update_many(hs, devs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sd.sd_close_many(hs)
+        return time.perf_counter() - t0
+
+    for _ in range(max(1, args.warmup // 3)):
+        one_at_a_time()
+        batched()
+    torch.cuda.synchronize()
+    t_one, t_bat, lat_one, lat_bat = [], [], [], []
+    for _ in range(args.batch_reps):
+        t0 = time.perf_counter()
+        lat_one += one_at_a_time()
+        torch.cuda.synchronize()
+        t_one.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        lat_bat.append(batched())
+        torch.cuda.synchronize()
+        t_bat.append(time.perf_counter() - t0)
+    for h in hs:
+        sd.sd_destroy(h)
+    one_v = dist_max(min(t_one), world)
+    bat_v = dist_max(min(t_bat), world)
+    if rank != 0:
+        return
+    line = {
+        "metric": "packets/s (Gpps), batched windows", "value": world * total / bat_v / 1e9,
+        "unit": "Gpps", "n_gpus": args.gpus, "steps": args.batch_reps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * bat_v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"batching: {args.links} links, window sizes lognormal (median 4M pairs, "
+                               "clipped to [256K, 64M]), 50-300 planted each, core-link sketch per link",
+                   "pairs_per_step_per_gpu": total},
+        "one_window_at_a_time": {"value": world * total / one_v / 1e9, "unit": "Gpps",
+                                 "ms_per_step": 1e3 * one_v,
+                                 "close_ms_per_window": {"p50": 1e3 * float(np.percentile(lat_one, 50)),
+                                                         "p99": 1e3 * float(np.percentile(lat_one, 99))}},
+        "batched_close_ms_all_links": {"p50": 1e3 * float(np.percentile(lat_bat, 50)),
+                                       "p99": 1e3 * float(np.percentile(lat_bat, 99))},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +467,10 @@ def main():
     ap.add_argument("--traffic", default="core", choices=["core", "uniform"],
                     help="uniform: every pair random (no Zipf, no planted hosts)")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--batching", action="store_true",
+                    help="many links of uneven size: batched versus one window at a time")
+    ap.add_argument("--links", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -382,6 +479,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.batching:
+        run_batching(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

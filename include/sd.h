@@ -75,7 +75,7 @@ typedef struct {
     uint64_t cand_cap;    /* capacity for the candidate set K per direction;
                              default 2^20 */
     uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
-    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^23 */
+    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^24 */
     void *cuda_stream;    /* cudaStream_t for all device work, or NULL for a
                              handle-owned stream */
 } sd_params;
@@ -169,6 +169,26 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n);
  * SD_ERR_REPORT_OVERFLOW with *out still filled (flags say which direction);
  * the window is closed in every one of these cases. */
 int sd_close_window(sd_handle *h, sd_report *out);
+
+/* Close the windows of `count` handles at once: the same work and results
+ * as sd_close_window on each, with the handles' GPU work overlapped across
+ * their streams and one host synchronisation per close phase for all of
+ * them (batched serving of many links).  outs[i] and rcs[i] receive handle
+ * i's report and return code; the call returns SD_OK, or the first hard
+ * error (SD_ERR_ARG / SD_ERR_NOMEM / SD_ERR_CUDA) among the rcs. */
+int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rcs);
+
+/* Algorithm 1 for `count` handles at once (batched windows of many links):
+ * handle i gets the ns[i] pairs at pairs[i], exactly as sd_update would give
+ * it.  When hs[0] uses the binned update (tuning mode 5), every link whose
+ * pairs are device-resident on hs[0]'s device and whose DHLA has hs[0]'s
+ * shape (g, r, k, alpha, dirs) is binned with the others: rounds of up to
+ * 2^bin_chunk_log2 pairs shared among up to 4096/(slices per DHLA) links,
+ * one bin launch and one apply launch per round, on hs[0]'s stream and with
+ * hs[0]'s scratch (ordered after each member's earlier work, and each
+ * member's later work after it).  The other links take sd_update.  Returns
+ * the first error, if any. */
+int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count);
 
 /* Wait for all work queued on the handle's stream. */
 int sd_sync(sd_handle *h);

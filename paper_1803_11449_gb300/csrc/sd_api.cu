@@ -117,6 +117,15 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Per-window state carried between the close phases.
+struct CloseState {
+    uint32_t flags;
+    RestoreArgs A;
+    double psi[2];
+    uint64_t nh[2];                        // hits per direction
+    const unsigned long long *keys[2];     // their sorted keys in pinned host memory
+};
+
 struct sd_handle {
     sd_params p{};
     Geometry G{};
@@ -134,19 +143,26 @@ struct sd_handle {
     uint32_t *he = nullptr;            // [dirs][2][2^k]
     uint32_t *cand = nullptr;          // [dirs][cand_cap]
     unsigned long long *hits = nullptr;   // [dirs][hits_cap]
-    unsigned long long *hits_tmp = nullptr;  // [hits_cap]: scratch of the large-list sort
+    unsigned long long *hits_tmp = nullptr;  // [dirs][hits_cap]: scratch of the large-list sort
     unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
     uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
-    unsigned long long *big_h = nullptr;  // pinned [hits_cap]: a large sorted hit list
+    unsigned long long *big_h = nullptr;  // pinned [2][hits_cap]: large sorted hit lists
     std::vector<sd_hit> report;
     std::vector<double> est_tbl;
     uint64_t last_ncand[2] = {0, 0};
     bool have_close = false;
+    CloseState cs{};
 
     // binned update (mode 5): scratch sized for the current tuning
     uint32_t *bin_mem = nullptr;       // bins [S][cap], then count [S], then work [1]
     uint64_t bin_mem_words = 0;
     BinArgs bin{};
+
+    // batched update (sd_update_many): link table and an event for stream joins
+    LinkDesc *links_dev = nullptr;
+    LinkDesc *links_h = nullptr;       // pinned
+    uint32_t links_cap = 0;
+    cudaEvent_t ev_batch = nullptr;
 
     uint64_t stage_pairs = 0;
     uint32_t *dstage[2] = {nullptr, nullptr};
@@ -215,7 +231,7 @@ static void resolve_caps(const sd_params *p, uint64_t *pair_cap, uint64_t *cand_
     *cand_cap = p->cand_cap ? p->cand_cap : (1ull << 20);
     *hits_cap = next_pow2(*cand_cap);
     *report_cap = p->report_cap ? p->report_cap : (uint64_t)p->dirs * *cand_cap;
-    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 23);
+    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 24);
 }
 
 uint64_t sd_device_bytes(const sd_params *p) {
@@ -223,8 +239,8 @@ uint64_t sd_device_bytes(const sd_params *p) {
     uint64_t pc, cc, hc, rc, sp;
     resolve_caps(p, &pc, &cc, &hc, &rc, &sp);
     const uint64_t cells = (uint64_t)p->r << p->k;
-    return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + hc * 8) +
-           hc * 8 + sizeof(StatBlock) + 2 * sp * 8;
+    return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + 2 * hc * 8) +
+           sizeof(StatBlock) + 2 * sp * 8;
 }
 
 static void release(sd_handle *h) {
@@ -247,6 +263,9 @@ static void release(sd_handle *h) {
         if (h->ev_h2d[b]) cudaEventDestroy(h->ev_h2d[b]);
         if (h->ev_kern[b]) cudaEventDestroy(h->ev_kern[b]);
     }
+    cudaFree(h->links_dev);
+    cudaFreeHost(h->links_h);
+    if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -288,6 +307,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         SD_CK(h, cudaEventCreateWithFlags(&h->ev_h2d[b], cudaEventDisableTiming));
         SD_CK(h, cudaEventCreateWithFlags(&h->ev_kern[b], cudaEventDisableTiming));
     }
+    SD_CK(h, cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
     const uint64_t words = (uint64_t)p->dirs * G.dir_words;
     const uint64_t nw = ((uint64_t)1 << p->k) >> 5;
     SD_CK(h, cudaMalloc(&h->grid, words * 4));
@@ -296,7 +316,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     SD_CK(h, cudaMalloc(&h->he, (uint64_t)p->dirs * 2 * ((uint64_t)4 << p->k)));
     SD_CK(h, cudaMalloc(&h->cand, (uint64_t)p->dirs * h->cand_cap * 4));
     SD_CK(h, cudaMalloc(&h->hits, (uint64_t)p->dirs * h->hits_cap * 8));
-    SD_CK(h, cudaMalloc(&h->hits_tmp, h->hits_cap * 8));
+    SD_CK(h, cudaMalloc(&h->hits_tmp, (uint64_t)p->dirs * h->hits_cap * 8));
     SD_CK(h, cudaMallocHost(&h->st_h, sizeof(StatBlock)));
     SD_CK(h, cudaMallocHost(&h->hits_h, (uint64_t)2 * kSortSmall * 8));
     SD_CK(h, launch_reset(h->grid, words, h->st_d, h->num_sms, h->stream));
@@ -364,11 +384,9 @@ static bool bin_layout(const sd_handle *h, BinArgs *B, uint64_t *words) {
     return true;
 }
 
-static int ensure_bins(sd_handle *h, bool *ok) {
-    BinArgs B;
-    uint64_t words = 0;
-    *ok = bin_layout(h, &B, &words);
-    if (!*ok) return SD_OK;
+// Bin scratch for S slices of `cap` entries (grows, never shrinks).
+static int ensure_bin_mem(sd_handle *h, BinArgs &B) {
+    const uint64_t words = (uint64_t)B.S * B.cap + B.S + 4;
     if (words > h->bin_mem_words) {
         SD_CK(h, cudaStreamSynchronize(h->stream));
         cudaFree(h->bin_mem);
@@ -385,6 +403,14 @@ static int ensure_bins(sd_handle *h, bool *ok) {
     B.work = B.count + B.S;
     h->bin = B;
     return SD_OK;
+}
+
+static int ensure_bins(sd_handle *h, bool *ok) {
+    BinArgs B;
+    uint64_t words = 0;
+    *ok = bin_layout(h, &B, &words);
+    if (!*ok) return SD_OK;
+    return ensure_bin_mem(h, B);
 }
 
 // Algorithm 1 over n device-resident pairs, with the handle's tuning.
@@ -461,6 +487,150 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
     return SD_OK;
 }
 
+// Slices of one handle's DHLA for the binned update: (S, slice_log2), or
+// false when the DHLA is too large to bin.
+static bool link_slices(const sd_handle *h, uint32_t *S, uint32_t *sl_out) {
+    BinArgs B;
+    uint64_t words = 0;
+    if (!bin_layout(h, &B, &words)) return false;
+    *S = B.S;
+    *sl_out = B.slice_log2;
+    return true;
+}
+
+int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count) {
+    if (!count) return SD_OK;
+    if (!hs || !pairs || !ns) return SD_ERR_ARG;
+    for (uint32_t i = 0; i < count; i++)
+        if (!hs[i]) return SD_ERR_ARG;
+    sd_handle *d = hs[0];
+    DeviceGuard dg(d->p.device);
+    const sd_params &P = d->p;
+    uint32_t S_link = 0, sl = 0;
+    const bool binnable = d->T.mode == 5 && link_slices(d, &S_link, &sl);
+    const uint32_t per_group = binnable ? std::max(1u, 4096u / S_link) : 1u;
+
+    // which links join the batch: device-resident pairs on hs[0]'s device,
+    // the same DHLA shape, each handle once; the others update on their own
+    std::vector<uint32_t> batch;
+    for (uint32_t i = 0; i < count; i++) {
+        const sd_handle *h = hs[i];
+        bool ok = binnable && ns[i] > 0 && pairs[i] && !((uintptr_t)pairs[i] & 3u) && h->p.g == P.g &&
+                  h->p.r == P.r && h->p.k == P.k && h->p.alpha == P.alpha && h->p.dirs == P.dirs &&
+                  h->p.device == P.device;
+        for (uint32_t q : batch)
+            if (hs[q] == h) ok = false;
+        if (ok) {
+            cudaPointerAttributes attr;
+            if (cudaPointerGetAttributes(&attr, pairs[i]) != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+            } else {
+                ok = attr.type == cudaMemoryTypeDevice && attr.device == P.device;
+            }
+        }
+        if (ok) {
+            batch.push_back(i);
+        } else {
+            const int rc = sd_update(hs[i], pairs[i], ns[i]);
+            if (rc != SD_OK) return rc;
+        }
+    }
+    if (batch.empty()) return SD_OK;
+
+    // the rounds' link tables live side by side in one buffer
+    const uint64_t chunk = 1ull << d->T.bin_chunk_log2;
+    uint64_t rounds_upper = 0;
+    {
+        const uint64_t members = std::min<uint64_t>(per_group, batch.size());
+        uint64_t total = 0;
+        for (uint32_t q : batch) total += ns[q];
+        rounds_upper = total / std::max<uint64_t>(1, chunk / members) + batch.size() + 1;
+    }
+    const uint64_t need = rounds_upper * per_group;
+    SD_CK(d, cudaStreamSynchronize(d->stream));  // an earlier batch may still read the table
+    if (d->links_cap < need) {
+        cudaFree(d->links_dev);
+        cudaFreeHost(d->links_h);
+        d->links_dev = nullptr;
+        d->links_h = nullptr;
+        d->links_cap = 0;
+        SD_CK(d, cudaMalloc(&d->links_dev, need * sizeof(LinkDesc)));
+        SD_CK(d, cudaMallocHost(&d->links_h, need * sizeof(LinkDesc)));
+        d->links_cap = (uint32_t)need;
+    }
+    // the members' earlier work comes first, on the driver's stream
+    for (uint32_t q : batch) {
+        sd_handle *h = hs[q];
+        if (h == d) continue;
+        SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
+        SD_CK(d, cudaStreamWaitEvent(d->stream, h->ev_batch, 0));
+    }
+
+    const uint32_t TP = d->T.bin_tile_pairs;
+    const uint64_t upd = (uint64_t)P.dirs * P.r;
+    std::vector<uint64_t> done(batch.size(), 0);
+    size_t cursor = 0, tab_used = 0;
+    for (;;) {
+        // up to per_group links with pairs left, round-robin
+        std::vector<uint32_t> mem;
+        for (size_t t = 0; t < batch.size() && mem.size() < per_group; t++) {
+            const size_t q = (cursor + t) % batch.size();
+            if (done[q] < ns[batch[q]]) mem.push_back((uint32_t)q);
+        }
+        if (mem.empty()) break;
+        cursor = (mem.back() + 1) % batch.size();
+        const uint64_t budget = std::max<uint64_t>(TP, chunk / mem.size());
+        LinkDesc *tab = d->links_h + tab_used;
+        uint64_t tiles = 0;
+        for (uint32_t m = 0; m < mem.size(); m++) {
+            const uint32_t i = batch[mem[m]];
+            const sd_handle *h = hs[i];
+            const uint64_t take = std::min(budget, ns[i] - done[mem[m]]);
+            LinkDesc &L = tab[m];
+            L.pairs = pairs[i] + 2 * done[mem[m]];
+            L.n = take;
+            L.grid = h->grid;
+            L.tile_start = tiles;
+            L.slice0 = m * S_link;
+            for (int dd = 0; dd < 2; dd++) {
+                L.A0[dd] = h->G.h[dd].A0;
+                L.A1[dd] = h->G.h[dd].A1;
+                L.B1[dd] = h->G.h[dd].B1;
+            }
+            tiles += (take + TP - 1) / TP;
+            done[mem[m]] += take;
+        }
+        if (tab_used + mem.size() > d->links_cap) return d->fail(SD_ERR_ARG, "sd_update_many: link table overflow");
+        SD_CK(d, cudaMemcpyAsync(d->links_dev + tab_used, tab, mem.size() * sizeof(LinkDesc), cudaMemcpyHostToDevice,
+                                 d->stream));
+        BinArgs B;
+        std::memset(&B, 0, sizeof B);
+        B.S = (uint32_t)mem.size() * S_link;
+        B.slice_log2 = sl;
+        const uint64_t mean = (budget * upd + S_link - 1) / S_link;
+        const uint64_t cap = mean + mean * d->T.bin_slack_pct / 100 + 256;
+        B.cap = (uint32_t)((cap + 3) & ~3ull);
+        B.tile_pairs = TP;
+        B.total_words = (uint64_t)P.dirs * d->G.dir_words;  // words of one link's DHLA
+        const int rc = ensure_bin_mem(d, B);
+        if (rc != SD_OK) return rc;
+        SD_CK(d, launch_binned_links(d->links_dev + tab_used, (uint32_t)mem.size(), tiles, S_link, d->G, d->bin,
+                                     d->num_sms, d->stream));
+        launched(2);
+        tab_used += mem.size();
+    }
+    // later work on each member waits for the batch
+    SD_CK(d, cudaEventRecord(d->ev_batch, d->stream));
+    for (uint32_t q : batch) {
+        sd_handle *h = hs[q];
+        h->n_pairs += ns[q];
+        if (h == d) continue;
+        SD_CK(h, cudaStreamWaitEvent(h->stream, d->ev_batch, 0));
+    }
+    return SD_OK;
+}
+
 int sd_sync(sd_handle *h) {
     if (!h) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
@@ -482,50 +652,53 @@ struct CloseTrace {
     }
     ~CloseTrace() {
         if (on)
-            std::fprintf(stderr, "sd_close_window us: stats %.1f restore %.1f bigsort %.1f report %.1f reset %.1f total %.1f\n",
-                         ph[0], ph[1], ph[2], ph[3], ph[4],
+            std::fprintf(stderr, "sd_close_window us: stats %.1f restore %.1f bigsort %.1f report+reset %.1f total %.1f\n",
+                         ph[0], ph[1], ph[2], ph[3],
                          std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count());
     }
 };
 
-int sd_close_window(sd_handle *h, sd_report *out) {
-    if (!h || !out) return SD_ERR_ARG;
-    DeviceGuard dg(h->p.device);
-    CloseTrace trace;
+// The window close in four phases, so that many handles can overlap their
+// GPU work and share host synchronisations (sd_close_many).  Each phase only
+// queues work on the handle's stream; the caller synchronises the stream
+// between phases.
+//   A: hot estimators and row statistics (Algorithm 2, first loop; §4.2)
+//   B: host decisions (psi, szmax, caps), then restore K, estimate SZ,
+//      order small hit lists (Algorithm 2 / Algorithms 3-4, §4.2)
+//   C: order the large hit lists
+//   D: build the report (Eq. 4), clear the DHLA for the next window
+static int close_phase_a(sd_handle *h, sd_report *out) {
     std::memset(out, 0, sizeof *out);
-    const Geometry &G = h->G;
-    const uint32_t dirs = G.dirs;
+    std::memset(&h->cs, 0, sizeof h->cs);
     h->report.clear();
     h->last_ncand[0] = h->last_ncand[1] = 0;
-
-    // hot estimators and row statistics (Algorithm 2, first loop; §4.2)
-    SD_CK(h, launch_row_stats(h->grid, G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
-    SD_CK(h, launch_compact(h->hotmap, G, h->he, h->stream));
+    SD_CK(h, launch_row_stats(h->grid, h->G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
+    SD_CK(h, launch_compact(h->hotmap, h->G, h->he, h->stream));
     launched(2);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
-    SD_CK(h, cudaStreamSynchronize(h->stream));
-    trace.mark(0);
+    return SD_OK;
+}
 
-    uint32_t flags = 0;
-    RestoreArgs A;
-    std::memset(&A, 0, sizeof A);
-    double psi[2] = {0.0, 0.0};
-    for (uint32_t d = 0; d < dirs; d++) {
+static int close_phase_b(sd_handle *h, sd_report *out) {
+    const Geometry &G = h->G;
+    CloseState &c = h->cs;
+    RestoreArgs &A = c.A;
+    for (uint32_t d = 0; d < G.dirs; d++) {
         for (uint32_t i = 0; i < G.r; i++) {
             out->zr[d][i] = h->st_h->zr[d][i];
             out->n_hot[d][i] = h->st_h->nhot[d][i];
         }
-        psi[d] = psi_of(G.g, G.r, G.k, h->st_h->zr[d]);
-        out->psi[d] = psi[d];
-        if (psi[d] < 0.0) {
-            flags |= SD_FLAG_SATURATED << (8 * d);
+        c.psi[d] = psi_of(G.g, G.r, G.k, h->st_h->zr[d]);
+        out->psi[d] = c.psi[d];
+        if (c.psi[d] < 0.0) {
+            c.flags |= SD_FLAG_SATURATED << (8 * d);
             continue;
         }
-        const int szmax = szmax_of(G.g, G.r, psi[d], h->p.theta);
+        const int szmax = szmax_of(G.g, G.r, c.psi[d], h->p.theta);
         out->szmax[d] = szmax < 0 ? 0 : (uint32_t)szmax;
         const uint64_t n0 = h->st_h->nhot[d][0], n1 = h->st_h->nhot[d][1];
         if (n0 * n1 > h->pair_cap) {
-            flags |= SD_FLAG_OVERLOAD_PAIRS << (8 * d);
+            c.flags |= SD_FLAG_OVERLOAD_PAIRS << (8 * d);
             continue;
         }
         A.run[d] = 1;
@@ -533,83 +706,93 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         A.n1[d] = (uint32_t)n1;
         A.szmax[d] = szmax;
     }
+    if (!(A.run[0] || A.run[1])) return SD_OK;
+    A.grid = h->grid;
+    A.he = h->he;
+    A.hotmap = h->hotmap;
+    A.cand = h->cand;
+    A.hits = h->hits;
+    A.stats = h->st_d;
+    A.cand_cap = h->cand_cap;
+    A.hits_cap = h->hits_cap;
+    SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
+    SD_CK(h, launch_estimate(G, A, h->num_sms, h->stream));
+    SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, G.dirs, h->stream));
+    launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 3 : 2);
+    SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
+    for (uint32_t d = 0; d < G.dirs; d++)
+        if (A.run[d])
+            SD_CK(h, cudaMemcpyAsync(h->hits_h + (uint64_t)d * kSortSmall, h->hits + (uint64_t)d * h->hits_cap,
+                                     std::min<uint64_t>(kSortSmall, h->hits_cap) * 8, cudaMemcpyDeviceToHost,
+                                     h->stream));
+    return SD_OK;
+}
 
-    if (A.run[0] || A.run[1]) {
-        // restore K and estimate each candidate (Algorithm 2 / Algorithms 3-4, §4.2)
-        A.grid = h->grid;
-        A.he = h->he;
-        A.hotmap = h->hotmap;
-        A.cand = h->cand;
-        A.hits = h->hits;
-        A.stats = h->st_d;
-        A.cand_cap = h->cand_cap;
-        A.hits_cap = h->hits_cap;
-        SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
-        SD_CK(h, launch_estimate(G, A, h->num_sms, h->stream));
-        SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, dirs, h->stream));
-        launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 3 : 2);
-        SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
-        for (uint32_t d = 0; d < dirs; d++)
-            if (A.run[d])
-                SD_CK(h, cudaMemcpyAsync(h->hits_h + (uint64_t)d * kSortSmall, h->hits + (uint64_t)d * h->hits_cap,
-                                         std::min<uint64_t>(kSortSmall, h->hits_cap) * 8, cudaMemcpyDeviceToHost,
-                                         h->stream));
-        SD_CK(h, cudaStreamSynchronize(h->stream));
-        trace.mark(1);
-        for (uint32_t d = 0; d < dirs; d++) {
-            if (!A.run[d]) continue;
-            const uint64_t nk = h->st_h->ncand[d];
-            out->n_cand[d] = nk;
-            h->last_ncand[d] = nk;
-            if (nk > h->cand_cap) {
-                flags |= SD_FLAG_OVERLOAD_CANDS << (8 * d);
-                continue;
-            }
-            const uint64_t nh = h->st_h->nhits[d];
-            const unsigned long long *keys = h->hits_h + (uint64_t)d * kSortSmall;
-            if (h->st_h->big_sort[d]) {
-                unsigned long long *sorted = nullptr;
-                SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp, nh, h->num_sms,
-                                         h->stream, &sorted));
-                uint64_t rounds = 0;
-                for (uint64_t L = kSortSmall; L < nh; L <<= 1) rounds++;
-                launched(1 + rounds);
-                if (!h->big_h) SD_CK(h, cudaMallocHost(&h->big_h, h->hits_cap * 8));
-                SD_CK(h, cudaMemcpyAsync(h->big_h, sorted, nh * 8, cudaMemcpyDeviceToHost, h->stream));
-                SD_CK(h, cudaStreamSynchronize(h->stream));
-                keys = h->big_h;
-                trace.mark(2);
-            }
-            // Eq. 4 depends on SZ alone within a window: one evaluation per
-            // distinct SZ value (hits have SZ <= szmax), bit-identical to
-            // evaluating it per hit
-            std::vector<double> &tbl = h->est_tbl;
-            tbl.assign((size_t)(A.szmax[d] >= 0 ? A.szmax[d] + 1 : 0), 0.0);
-            for (size_t z = 0; z < tbl.size(); z++) tbl[z] = eq4(G.g, G.r, psi[d], (uint32_t)z);
-            const size_t at = h->report.size();
-            h->report.resize(at + nh);
-            sd_hit *out_h = h->report.data() + at;
-            const double *t = tbl.data();
-            const size_t tn = tbl.size();
-            for (uint64_t q = 0; q < nh; q++) {
-                const unsigned long long key = keys[q];
-                const uint32_t sz = (uint32_t)(key & 0xFFFFFFFFull);
-                out_h[q].ip = (uint32_t)(key >> 32);
-                out_h[q].sz = sz;
-                out_h[q].dir = d;
-                out_h[q].reserved = 0;
-                out_h[q].est = sz < tn ? t[sz] : eq4(G.g, G.r, psi[d], sz);
-            }
+// Returns SD_OK; sets *need_sync when large sorts were queued.
+static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
+    CloseState &c = h->cs;
+    *need_sync = false;
+    for (uint32_t d = 0; d < h->G.dirs; d++) {
+        if (!c.A.run[d]) continue;
+        const uint64_t nk = h->st_h->ncand[d];
+        out->n_cand[d] = nk;
+        h->last_ncand[d] = nk;
+        if (nk > h->cand_cap) {
+            c.flags |= SD_FLAG_OVERLOAD_CANDS << (8 * d);
+            continue;
+        }
+        c.nh[d] = h->st_h->nhits[d];
+        c.keys[d] = h->hits_h + (uint64_t)d * kSortSmall;
+        if (!h->st_h->big_sort[d]) continue;
+        unsigned long long *sorted = nullptr;
+        SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp + (uint64_t)d * h->hits_cap,
+                                 c.nh[d], h->num_sms, h->stream, &sorted));
+        uint64_t rounds = 0;
+        for (uint64_t L = kSortSmall; L < c.nh[d]; L <<= 1) rounds++;
+        launched(1 + rounds);
+        if (!h->big_h) SD_CK(h, cudaMallocHost(&h->big_h, (uint64_t)2 * h->hits_cap * 8));
+        unsigned long long *dst = h->big_h + (uint64_t)d * h->hits_cap;
+        SD_CK(h, cudaMemcpyAsync(dst, sorted, c.nh[d] * 8, cudaMemcpyDeviceToHost, h->stream));
+        c.keys[d] = dst;
+        *need_sync = true;
+    }
+    return SD_OK;
+}
+
+static int close_phase_d(sd_handle *h, sd_report *out) {
+    const Geometry &G = h->G;
+    CloseState &c = h->cs;
+    for (uint32_t d = 0; d < G.dirs; d++) {
+        if (!c.A.run[d] || !c.keys[d]) continue;
+        // Eq. 4 depends on SZ alone within a window: one evaluation per
+        // distinct SZ value (hits have SZ <= szmax), bit-identical to
+        // evaluating it per hit
+        std::vector<double> &tbl = h->est_tbl;
+        tbl.assign((size_t)(c.A.szmax[d] >= 0 ? c.A.szmax[d] + 1 : 0), 0.0);
+        for (size_t z = 0; z < tbl.size(); z++) tbl[z] = eq4(G.g, G.r, c.psi[d], (uint32_t)z);
+        const uint64_t nh = c.nh[d];
+        const unsigned long long *keys = c.keys[d];
+        const size_t at = h->report.size();
+        h->report.resize(at + nh);
+        sd_hit *out_h = h->report.data() + at;
+        const double *t = tbl.data();
+        const size_t tn = tbl.size();
+        for (uint64_t q = 0; q < nh; q++) {
+            const unsigned long long key = keys[q];
+            const uint32_t sz = (uint32_t)(key & 0xFFFFFFFFull);
+            out_h[q].ip = (uint32_t)(key >> 32);
+            out_h[q].sz = sz;
+            out_h[q].dir = d;
+            out_h[q].reserved = 0;
+            out_h[q].est = sz < tn ? t[sz] : eq4(G.g, G.r, c.psi[d], sz);
         }
     }
     h->have_close = true;
-    trace.mark(3);
-
     // clear the DHLA and the counters for the next window (stream-ordered)
-    SD_CK(h, launch_reset(h->grid, (uint64_t)dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
+    SD_CK(h, launch_reset(h->grid, (uint64_t)G.dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
     launched(1);
-    trace.mark(4);
 
+    uint32_t flags = c.flags;
     out->n_hits_total = h->report.size();
     if (h->report.size() > h->report_cap) {
         for (uint64_t q = h->report_cap; q < h->report.size(); q++)
@@ -629,6 +812,77 @@ int sd_close_window(sd_handle *h, sd_report *out) {
         return h->fail(SD_ERR_OVERLOAD, "sd_close_window: restore over its pair or candidate cap");
     if (any & SD_FLAG_REPORT_OVERFLOW)
         return h->fail(SD_ERR_REPORT_OVERFLOW, "sd_close_window: more hits than report_cap");
+    return SD_OK;
+}
+
+static bool rc_is_error(int rc) { return rc == SD_ERR_ARG || rc == SD_ERR_NOMEM || rc == SD_ERR_CUDA; }
+
+int sd_close_window(sd_handle *h, sd_report *out) {
+    if (!h || !out) return SD_ERR_ARG;
+    DeviceGuard dg(h->p.device);
+    CloseTrace trace;
+    int rc = close_phase_a(h, out);
+    if (rc != SD_OK) return rc;
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    trace.mark(0);
+    rc = close_phase_b(h, out);
+    if (rc != SD_OK) return rc;
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    trace.mark(1);
+    bool big = false;
+    rc = close_phase_c(h, out, &big);
+    if (rc != SD_OK) return rc;
+    if (big) SD_CK(h, cudaStreamSynchronize(h->stream));
+    trace.mark(2);
+    rc = close_phase_d(h, out);
+    trace.mark(3);
+    return rc;
+}
+
+int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rcs) {
+    if (!hs || !outs || !rcs) return count ? SD_ERR_ARG : SD_OK;
+    for (uint32_t i = 0; i < count; i++)
+        if (!hs[i]) return SD_ERR_ARG;
+    std::vector<char> live(count, 1);
+    auto step = [&](auto &&phase) {
+        for (uint32_t i = 0; i < count; i++) {
+            if (!live[i]) continue;
+            DeviceGuard dg(hs[i]->p.device);
+            rcs[i] = phase(hs[i], &outs[i], i);
+            if (rcs[i] != SD_OK) live[i] = 0;
+        }
+    };
+    auto sync = [&](const std::vector<char> &which) {
+        for (uint32_t i = 0; i < count; i++) {
+            if (!live[i] || !which[i]) continue;
+            DeviceGuard dg(hs[i]->p.device);
+            const cudaError_t e = cudaStreamSynchronize(hs[i]->stream);
+            if (e != cudaSuccess) {
+                rcs[i] = hs[i]->fail(SD_ERR_CUDA, "sd_close_many: %s", cudaGetErrorString(e));
+                live[i] = 0;
+            }
+        }
+    };
+    std::vector<char> all(count, 1), big(count, 0);
+    for (uint32_t i = 0; i < count; i++) rcs[i] = SD_OK;
+    step([](sd_handle *h, sd_report *o, uint32_t) { return close_phase_a(h, o); });
+    sync(all);
+    step([](sd_handle *h, sd_report *o, uint32_t) { return close_phase_b(h, o); });
+    sync(all);
+    step([&](sd_handle *h, sd_report *o, uint32_t i) {
+        bool b = false;
+        const int rc = close_phase_c(h, o, &b);
+        big[i] = b;
+        return rc;
+    });
+    sync(big);
+    for (uint32_t i = 0; i < count; i++) {
+        if (!live[i]) continue;
+        DeviceGuard dg(hs[i]->p.device);
+        rcs[i] = close_phase_d(hs[i], &outs[i]);
+    }
+    for (uint32_t i = 0; i < count; i++)
+        if (rc_is_error(rcs[i])) return rcs[i];
     return SD_OK;
 }
 

@@ -52,19 +52,25 @@ __device__ __forceinline__ DirConst dir_const(const Geometry &G, uint32_t d) {
 // with consecutive addresses.  A sorted entry is slice << 20 | local, where
 // local = (word mod 2^slice_log2) << 5 | bit (slice_log2 <= 15, at most 4096
 // slices).
+struct DirHash {
+    uint32_t A0[2];
+    uint64_t A1[2], B1[2];
+};
+
 template <int R, int DIRS, int PPT, bool FULL>
-__device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&base5)[DIRS][R], uint32_t cshift,
-                                         uint32_t kmask, uint32_t sl5, const uint32_t (&src)[PPT],
-                                         const uint32_t (&dst)[PPT], const bool (&ok)[PPT], uint32_t *hist,
+__device__ __forceinline__ void bin_hash(const Geometry &G, const DirHash &H, const uint32_t (&base5)[DIRS][R],
+                                         uint32_t cshift, uint32_t kmask, uint32_t sl5, uint32_t slice0,
+                                         const uint32_t (&src)[PPT], const uint32_t (&dst)[PPT],
+                                         const bool (&ok)[PPT], uint32_t *hist,
                                          uint32_t (&ent)[PPT * DIRS * R], uint32_t (&met)[PPT * DIRS * R]) {
     const uint32_t lmask = (1u << sl5) - 1u;
 #pragma unroll
     for (int j = 0; j < PPT; j++) {
 #pragma unroll
         for (int d = 0; d < DIRS; d++) {
-            const uint32_t A0 = d ? G.h[1].A0 : G.h[0].A0;
-            const uint64_t A1 = d ? G.h[1].A1 : G.h[0].A1;
-            const uint64_t B1 = d ? G.h[1].B1 : G.h[0].B1;
+            const uint32_t A0 = H.A0[d];
+            const uint64_t A1 = H.A1[d];
+            const uint64_t B1 = H.B1[d];
             const uint32_t key = d ? dst[j] : src[j], elem = d ? src[j] : dst[j];
             const uint32_t b = (uint32_t)((A1 * (uint64_t)elem + B1) >> (64u - G.lg));
             const uint32_t c0 = dh0(A0, G.k, key);
@@ -72,7 +78,7 @@ __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&bas
             for (int i = 0; i < R; i++) {
                 const uint32_t ci = (i == 0) ? c0 : ((shr_clamp(key, (i - 1) * G.alpha) & kmask) ^ c0);
                 const uint32_t bitidx = base5[d][i] + (ci << cshift) + b;  // global bit index
-                const uint32_t s = bitidx >> sl5;
+                const uint32_t s = slice0 + (bitidx >> sl5);  // slice over all links
                 const int u = (j * DIRS + d) * R + i;
                 ent[u] = (s << 20) | (bitidx & lmask);
                 if (FULL || ok[j]) met[u] = atomicAdd(&hist[s], 1u);
@@ -89,10 +95,22 @@ __device__ __forceinline__ void bin_hash(const Geometry &G, const uint32_t (&bas
 // with consecutive addresses.  A sorted entry is slice << 20 | local, where
 // local = (bit index within the slice) = (word mod 2^slice_log2) << 5 | bit
 // (slice_log2 <= 15, at most 4096 slices, fewer than 2^32 DHLA bits).
+// Where a tile's pairs come from: one link given by the kernel parameters,
+// or a table of links (a batched update of many windows in one launch), each
+// with its own pairs, DHLA, hash constants and first slice.
+struct TileSrc {
+    const uint32_t *pairs;
+    uint64_t n;        // pairs of the link
+    uint64_t tile;     // tile index within the link
+    uint32_t *grid;
+    uint32_t slice0;   // first slice of the link in this launch
+    DirHash H;
+};
+
 template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
 k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
-      uint32_t lwpc) {
+      uint32_t lwpc, const LinkDesc *__restrict__ links, uint32_t nlinks, uint64_t ntiles_all) {
     constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
     extern __shared__ uint32_t sm[];
     // per slice: destination of sorted entry q is dst + q while q < lim
@@ -108,7 +126,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
     __shared__ uint32_t warp_tot[32];
 
     const uint32_t TP = blockDim.x * PPT;
-    const uint64_t ntiles = (n + TP - 1) / TP;
+    const uint64_t ntiles = links ? ntiles_all : (n + TP - 1) / TP;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t sl = B.slice_log2, sl5 = sl + 5;
     const uint32_t kmask = (1u << G.k) - 1u, cshift = lwpc + 5;
@@ -121,21 +139,43 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             base5[d][i] = ((d ? (uint32_t)G.dir_words : 0u) + (uint32_t)i * (uint32_t)G.row_words) << 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) *B.work = 0;  // k_apply's slice counter
     for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
-    const bool vec = ((uintptr_t)pairs & 15u) == 0;  // 16-byte loads of 2 pairs
-
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t p0 = t * TP + (uint64_t)threadIdx.x * PPT;
-        const bool full = (t + 1) * TP <= n;
+        TileSrc ts;
+        if (links) {
+            uint32_t l = 0;
+            while (l + 1 < nlinks && links[l + 1].tile_start <= t) l++;
+            const LinkDesc &L = links[l];
+            ts.pairs = L.pairs;
+            ts.n = L.n;
+            ts.tile = t - L.tile_start;
+            ts.grid = L.grid;
+            ts.slice0 = L.slice0;
+            ts.H.A0[0] = L.A0[0]; ts.H.A0[1] = L.A0[1];
+            ts.H.A1[0] = L.A1[0]; ts.H.A1[1] = L.A1[1];
+            ts.H.B1[0] = L.B1[0]; ts.H.B1[1] = L.B1[1];
+        } else {
+            ts.pairs = pairs;
+            ts.n = n;
+            ts.tile = t;
+            ts.grid = grid;
+            ts.slice0 = 0;
+            ts.H.A0[0] = G.h[0].A0; ts.H.A0[1] = G.h[1].A0;
+            ts.H.A1[0] = G.h[0].A1; ts.H.A1[1] = G.h[1].A1;
+            ts.H.B1[0] = G.h[0].B1; ts.H.B1[1] = G.h[1].B1;
+        }
+        const bool vec = ((uintptr_t)ts.pairs & 15u) == 0;  // 16-byte loads of 2 pairs
+        const uint64_t p0 = ts.tile * TP + (uint64_t)threadIdx.x * PPT;
+        const bool full = (ts.tile + 1) * TP <= ts.n;
         uint32_t src[PPT], dst[PPT];
         bool ok[PPT];
         if (full && vec) {
             if (PPT == 2) {
-                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p0));
+                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(ts.pairs + 2 * p0));
                 src[0] = v.x; dst[0] = v.y; src[PPT - 1] = v.z; dst[PPT - 1] = v.w;
             } else {
 #pragma unroll
                 for (int j = 0; j < PPT; j += 2) {
-                    const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * (p0 + j)));
+                    const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(ts.pairs + 2 * (p0 + j)));
                     src[j] = v.x; dst[j] = v.y; src[j + 1] = v.z; dst[j + 1] = v.w;
                 }
             }
@@ -145,17 +185,19 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             // partial tile, or pairs only 4- or 8-byte aligned: 32-bit loads
 #pragma unroll
             for (int j = 0; j < PPT; j++) {
-                ok[j] = p0 + j < n;
-                src[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j)) : 0u;
-                dst[j] = ok[j] ? ld_stream_u32(pairs + 2 * (p0 + j) + 1) : 0u;
+                ok[j] = p0 + j < ts.n;
+                src[j] = ok[j] ? ld_stream_u32(ts.pairs + 2 * (p0 + j)) : 0u;
+                dst[j] = ok[j] ? ld_stream_u32(ts.pairs + 2 * (p0 + j) + 1) : 0u;
             }
         }
         __syncthreads();  // previous tile written out, hist zero again
         uint32_t ent[UPT], met[UPT];
         if (full)
-            bin_hash<R, DIRS, PPT, true>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
+            bin_hash<R, DIRS, PPT, true>(G, ts.H, base5, cshift, kmask, sl5, ts.slice0, src, dst, ok, hist, ent,
+                                         met);
         else
-            bin_hash<R, DIRS, PPT, false>(G, base5, cshift, kmask, sl5, src, dst, ok, hist, ent, met);
+            bin_hash<R, DIRS, PPT, false>(G, ts.H, base5, cshift, kmask, sl5, ts.slice0, src, dst, ok, hist, ent,
+                                          met);
         __syncthreads();
         // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
@@ -204,7 +246,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             if (full || ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
         __syncthreads();
         // write-out, one thread per entry; full bins fall back to red.or
-        const uint64_t left = n - t * TP;
+        const uint64_t left = ts.n - ts.tile * TP;
         const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
         for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
             const uint32_t e = sorted[q];
@@ -212,8 +254,8 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             if (q < sq.lim) {
                 sq.dst[q] = e;
             } else {
-                const uint32_t w = ((e >> 20) << sl) | ((e & 0xFFFFFu) >> 5);
-                red_or(grid + w, 1u << (e & 31u));
+                const uint32_t w = (((e >> 20) - ts.slice0) << sl) | ((e & 0xFFFFFu) >> 5);
+                red_or(ts.grid + w, 1u << (e & 31u));
             }
         }
         for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
@@ -221,7 +263,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
 }
 
 __global__ void __launch_bounds__(1024)
-k_apply(uint32_t *__restrict__ grid, BinArgs B) {
+k_apply(uint32_t *__restrict__ grid, BinArgs B, const LinkDesc *__restrict__ links, uint32_t slices_per_link) {
     extern __shared__ uint32_t slice[];
     __shared__ uint32_t s_cur;
     const uint32_t SW = 1u << B.slice_log2;
@@ -259,11 +301,18 @@ k_apply(uint32_t *__restrict__ grid, BinArgs B) {
         }
 #undef SD_APPLY1
         __syncthreads();
-        // OR the slice into the DHLA (this block is the slice's only writer)
-        const uint64_t w0 = (uint64_t)s << B.slice_log2;
+        // OR the slice into its DHLA (this block is the slice's only writer)
+        uint32_t *g = grid;
+        uint32_t local = s;
+        if (links) {
+            const uint32_t l = s / slices_per_link;
+            local = s - l * slices_per_link;
+            g = links[l].grid;
+        }
+        const uint64_t w0 = (uint64_t)local << B.slice_log2;
         const uint64_t left = B.total_words - w0;
         const uint32_t words = left < (uint64_t)SW ? (uint32_t)left : SW;
-        uint4 *g4 = reinterpret_cast<uint4 *>(grid + w0);
+        uint4 *g4 = reinterpret_cast<uint4 *>(g + w0);
         for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) {
             const uint4 v = s4[i];
             if (v.x | v.y | v.z | v.w) {
@@ -282,7 +331,8 @@ size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S) {
 
 template <int R, int DIRS, int PPT>
 static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
-                              const BinArgs &B, int num_sms, cudaStream_t s) {
+                              const BinArgs &B, int num_sms, cudaStream_t s, const LinkDesc *links,
+                              uint32_t nlinks, uint64_t ntiles_all) {
     auto kern = k_bin<R, DIRS, PPT>;
     const uint32_t threads = B.tile_pairs / PPT;
     const size_t smem = bin_smem_bytes(B.tile_pairs, DIRS * R, B.S);
@@ -291,42 +341,46 @@ static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid,
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
     if (e != cudaSuccess) return e;
-    const uint64_t tiles = (n + B.tile_pairs - 1) / B.tile_pairs;
+    const uint64_t tiles = links ? ntiles_all : (n + B.tile_pairs - 1) / B.tile_pairs;
     uint64_t blocks = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     if (tiles < blocks) blocks = tiles ? tiles : 1;
     uint32_t lwpc = 0;
     while ((1u << lwpc) < G.wpc) lwpc++;
-    kern<<<(unsigned)blocks, threads, smem, s>>>(pairs, n, grid, G, B, lwpc);
+    kern<<<(unsigned)blocks, threads, smem, s>>>(pairs, n, grid, G, B, lwpc, links, nlinks, ntiles_all);
     return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_bin_r(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
-                                const BinArgs &B, int num_sms, cudaStream_t s) {
+                                const BinArgs &B, int num_sms, cudaStream_t s, const LinkDesc *links,
+                                uint32_t nlinks, uint64_t ntiles_all) {
     // 2 pairs per thread up to 1024-pair tiles (512 threads), else 4; the
     // API keeps tiles at 1024 pairs when dirs*r > 8 so registers suffice
     const bool two = B.tile_pairs <= 1024 || G.dirs * G.r > 8;
     if (G.dirs == 2) {
         if constexpr (2 * R <= 8) {
-            if (!two) return launch_bin<R, 2, 4>(pairs, n, grid, G, B, num_sms, s);
+            if (!two) return launch_bin<R, 2, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
         }
-        return launch_bin<R, 2, 2>(pairs, n, grid, G, B, num_sms, s);
+        return launch_bin<R, 2, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
     }
-    return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s)
-               : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s);
+    return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all)
+               : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
 }
 
-// One chunk: bin then apply (stream-ordered).
-cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
-                                const BinArgs &B, int num_sms, cudaStream_t s) {
+// One round: bin then apply (stream-ordered).  With `links` (a device table
+// of nlinks links whose tiles number ntiles_all in total), pairs/n/grid are
+// ignored and link l owns slices [l*slices_per_link, (l+1)*slices_per_link).
+static cudaError_t launch_rounds(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                                 const BinArgs &B, int num_sms, cudaStream_t s, const LinkDesc *links,
+                                 uint32_t nlinks, uint64_t ntiles_all, uint32_t slices_per_link) {
     cudaError_t e;
     switch (G.r) {
-        case 3: e = launch_bin_r<3>(pairs, n, grid, G, B, num_sms, s); break;
-        case 4: e = launch_bin_r<4>(pairs, n, grid, G, B, num_sms, s); break;
-        case 5: e = launch_bin_r<5>(pairs, n, grid, G, B, num_sms, s); break;
-        case 6: e = launch_bin_r<6>(pairs, n, grid, G, B, num_sms, s); break;
-        case 7: e = launch_bin_r<7>(pairs, n, grid, G, B, num_sms, s); break;
-        case 8: e = launch_bin_r<8>(pairs, n, grid, G, B, num_sms, s); break;
+        case 3: e = launch_bin_r<3>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 4: e = launch_bin_r<4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 5: e = launch_bin_r<5>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 6: e = launch_bin_r<6>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 7: e = launch_bin_r<7>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 8: e = launch_bin_r<8>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -338,8 +392,19 @@ cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *gri
     if (e != cudaSuccess) return e;
     uint64_t ablocks = (uint64_t)num_sms * (per_sm_a > 0 ? per_sm_a : 1);
     if (B.S < ablocks) ablocks = B.S;
-    k_apply<<<(unsigned)ablocks, 1024, smem_apply, s>>>(grid, B);
+    k_apply<<<(unsigned)ablocks, 1024, smem_apply, s>>>(grid, B, links, slices_per_link);
     return cudaGetLastError();
+}
+
+cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
+                                const BinArgs &B, int num_sms, cudaStream_t s) {
+    return launch_rounds(pairs, n, grid, G, B, num_sms, s, nullptr, 0, 0, B.S);
+}
+
+cudaError_t launch_binned_links(const LinkDesc *links_dev, uint32_t nlinks, uint64_t ntiles_all,
+                                uint32_t slices_per_link, const Geometry &G, const BinArgs &B, int num_sms,
+                                cudaStream_t s) {
+    return launch_rounds(nullptr, 0, nullptr, G, B, num_sms, s, links_dev, nlinks, ntiles_all, slices_per_link);
 }
 
 }  // namespace sd

@@ -41,6 +41,17 @@ struct Tuning {
     uint32_t bin_slack_pct;  // mode 5: bin capacity over the mean fill, in percent
 };
 
+// One link of a batched binned update (device memory table).
+struct LinkDesc {
+    const uint32_t *pairs;  // the link's pairs for this round
+    uint64_t n;
+    uint32_t *grid;         // the link's DHLA
+    uint64_t tile_start;    // first tile of the link in the launch's tile order
+    uint32_t slice0;        // first slice of the link in the launch's slice order
+    uint32_t A0[2];
+    uint64_t A1[2], B1[2];
+};
+
 struct BinArgs {
     uint32_t *bins;          // [S][cap]
     uint32_t *count;         // [S] entries appended this chunk (may exceed cap)
@@ -152,5 +163,8 @@ cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
 cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                                 const BinArgs &B, int num_sms, cudaStream_t s);
+cudaError_t launch_binned_links(const LinkDesc *links_dev, uint32_t nlinks, uint64_t ntiles_all,
+                                uint32_t slices_per_link, const Geometry &G, const BinArgs &B, int num_sms,
+                                cudaStream_t s);
 
 }  // namespace sd

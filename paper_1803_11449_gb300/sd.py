@@ -37,7 +37,8 @@ SD_FLAG_REPORT_OVERFLOW = 8
 
 # every function the header declares, in declaration order
 EXPORTS = ["sd_default_params", "sd_check_params", "sd_grid_words", "sd_device_bytes", "sd_create",
-           "sd_update", "sd_close_window", "sd_sync", "sd_destroy", "sd_last_error", "sd_get_grid",
+           "sd_update", "sd_close_window", "sd_close_many", "sd_update_many", "sd_sync", "sd_destroy",
+           "sd_last_error", "sd_get_grid",
            "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_kernel_launches",
            "sd_get_tuning", "sd_set_tuning", "sd_update_noalloc"]
 
@@ -107,6 +108,10 @@ def lib():
                 "sd_create": (ctypes.c_int, [_P(sd_params), _P(_VP)]),
                 "sd_update": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64]),
                 "sd_close_window": (ctypes.c_int, [_VP, _P(sd_report)]),
+                "sd_close_many": (ctypes.c_int, [_P(_VP), ctypes.c_uint32, _P(sd_report),
+                                                 _P(ctypes.c_int)]),
+                "sd_update_many": (ctypes.c_int, [_P(_VP), _P(_VP), _P(ctypes.c_uint64),
+                                                  ctypes.c_uint32]),
                 "sd_sync": (ctypes.c_int, [_VP]),
                 "sd_destroy": (ctypes.c_int, [_VP]),
                 "sd_last_error": (ctypes.c_char_p, [_VP]),
@@ -238,6 +243,10 @@ def sd_close_window(h: Handle, allow=(SD_OK, SD_ERR_SATURATED, SD_ERR_OVERLOAD,
     rep = sd_report()
     rc = lib().sd_close_window(h.ptr, ctypes.byref(rep))
     _check(rc, h.ptr, ok=allow)
+    return _report_of(h, rc, rep)
+
+
+def _report_of(h: Handle, rc: int, rep: sd_report) -> Report:
     p = h.params
     n = int(rep.n_hits)
     if n:
@@ -253,6 +262,28 @@ def sd_close_window(h: Handle, allow=(SD_OK, SD_ERR_SATURATED, SD_ERR_OVERLOAD,
         n_cand=[int(x) for x in list(rep.n_cand)[: p.dirs]], zhot=int(rep.zhot),
         szmax=[int(x) for x in list(rep.szmax)[: p.dirs]], flags=int(rep.flags),
         n_hits_total=int(rep.n_hits_total), hits=hits)
+
+
+def sd_update_many(hs, pairs_list) -> None:
+    """Algorithm 1 for many handles at once (batched rounds, see sd.h)."""
+    n = len(hs)
+    bufs = [_buffer(p) for p in pairs_list]
+    arr_h = (_VP * n)(*[h.ptr for h in hs])
+    arr_p = (_VP * n)(*[b[0] if b[1] else None for b in bufs])
+    arr_n = (ctypes.c_uint64 * n)(*[b[1] for b in bufs])
+    _check(lib().sd_update_many(arr_h, arr_p, arr_n, n), hs[0].ptr if hs else None)
+
+
+def sd_close_many(hs) -> list:
+    """Close the windows of many handles at once; one Report per handle."""
+    n = len(hs)
+    arr_h = (_VP * n)(*[h.ptr for h in hs])
+    reps = (sd_report * n)()
+    rcs = (ctypes.c_int * n)()
+    rc = lib().sd_close_many(arr_h, n, reps, rcs)
+    if rc not in (SD_OK, SD_ERR_SATURATED, SD_ERR_OVERLOAD, SD_ERR_REPORT_OVERFLOW):
+        _check(rc, hs[0].ptr)
+    return [_report_of(h, int(rcs[i]), reps[i]) for i, h in enumerate(hs)]
 
 
 def sd_get_grid(h: Handle, direction: int) -> np.ndarray:

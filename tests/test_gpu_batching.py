@@ -1,0 +1,97 @@
+"""Batched windows of many links (sd_update_many, sd_close_many): every
+link's DHLA and report must be exactly what the oracle gives for that link
+alone, and exactly what the one-window-at-a-time path gives."""
+import numpy as np
+import pytest
+
+from paper_1803_11449_gb300 import traffic as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd as mod
+    mod.lib()
+    return mod
+
+
+def _dev(pairs):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(pairs).reshape(-1).view(np.int32)).cuda()
+
+
+def _oracle(O, w, pairs, seed):
+    op = O.params_from(w.sketch(), seed=seed)
+    og = O.new_grid(op)
+    O.update(op, og, pairs)
+    return og, O.close_window(op, og)
+
+
+def _same_report(rep, ref, dirs):
+    assert rep.n_cand == ref["n_cand"]
+    assert [rep.dir_flags(d) for d in range(dirs)] == ref["flags"]
+    assert np.array_equal(rep.zr, ref["zr"]) and rep.psi == ref["psi"]
+    assert np.array_equal(rep.hits["ip"], ref["ip"]) and np.array_equal(rep.hits["sz"], ref["sz"])
+    assert np.array_equal(rep.hits["dir"], ref["dir"])
+    assert np.array_equal(rep.hits["est"], ref["est"])
+
+
+@pytest.mark.parametrize("tuning", [dict(mode=5), dict(mode=5, bin_chunk_log2=17), dict(mode=1)])
+def test_batched_links_equal_each_link_alone(sd, O, tuning):
+    """Seven links of uneven sizes (one of them much larger than a round's
+    share), each with its own traffic and its own hash seed."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    sizes = [1 << 14, 3 + (1 << 16), 200_001, 1 << 12, 1 << 19, 77_777, 5]
+    seeds = [1000 + i for i in range(len(sizes))]
+    wins = [T.make_window(w.with_(n=max(n, 64), planted=4 if n > 1000 else 0), s, n=n)
+            for n, s in zip(sizes, seeds)]
+    hs = [sd.sd_create(sd.params_for(w, s)) for s in seeds]
+    try:
+        for h in hs:
+            sd.sd_set_tuning(h, **tuning)
+        devs = [_dev(win.pairs) for win in wins]
+        sd.sd_update_many(hs, devs)
+        grids = [np.concatenate([sd.sd_get_grid(h, d) for d in range(2)]) for h in hs]
+        reps = sd.sd_close_many(hs)
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    for win, s, g, rep in zip(wins, seeds, grids, reps):
+        og, ref = _oracle(O, w, win.pairs, s)
+        assert np.array_equal(g, og)
+        _same_report(rep, ref, 2)
+        assert rep.n_pairs == len(win.pairs)
+
+
+def test_close_many_equals_close_window_on_core_links(sd, O):
+    """Core-link sketches (both directions, 2^16 estimators of 512 bits):
+    three links closed together report what each reports alone."""
+    w = T.WORKLOADS["core"].with_(n=1 << 20, planted=20, planted_c=("loguniform", 1024, 20000),
+                                  src_pool=1 << 18, dst_pool=1 << 20)
+    wins = [T.make_window(w, s) for s in (7, 8, 9)]
+    seeds = [71, 72, 73]
+    alone = []
+    for win, s in zip(wins, seeds):
+        h = sd.sd_create(sd.params_for(w, s))
+        try:
+            sd.sd_update(h, _dev(win.pairs))
+            alone.append(sd.sd_close_window(h))
+        finally:
+            sd.sd_destroy(h)
+    hs = [sd.sd_create(sd.params_for(w, s)) for s in seeds]
+    try:
+        sd.sd_update_many(hs, [_dev(win.pairs) for win in wins])
+        together = sd.sd_close_many(hs)
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    for a, b, win, s in zip(alone, together, wins, seeds):
+        assert a.n_cand == b.n_cand and a.flags == b.flags
+        assert np.array_equal(a.hits, b.hits)
+        _, ref = _oracle(O, w, win.pairs, s)
+        _same_report(b, ref, 2)
