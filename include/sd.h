@@ -182,11 +182,12 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
  * handle i gets the ns[i] pairs at pairs[i], exactly as sd_update would give
  * it.  When hs[0] uses the binned update (tuning mode 5), every link whose
  * pairs are device-resident on hs[0]'s device and whose DHLA has hs[0]'s
- * shape (g, r, k, alpha, dirs) is binned with the others: rounds of up to
- * 2^bin_chunk_log2 pairs shared among up to 4096/(slices per DHLA) links,
- * one bin launch and one apply launch per round, on hs[0]'s stream and with
- * hs[0]'s scratch (ordered after each member's earlier work, and each
- * member's later work after it).  The other links take sd_update.  Returns
+ * shape (g, r, k, alpha, dirs) is binned with the others: in each round up
+ * to 4096/(slices per DHLA) links (fewer when their bins would pass 8 GiB)
+ * contribute up to 2^bin_chunk_log2 pairs each, with one bin launch and one
+ * apply launch per round, on hs[0]'s stream and with hs[0]'s scratch
+ * (ordered after each member's earlier work, and each member's later work
+ * after it).  The other links take sd_update.  Returns
  * the first error, if any. */
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count);
 

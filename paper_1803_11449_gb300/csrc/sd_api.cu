@@ -508,7 +508,20 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     const sd_params &P = d->p;
     uint32_t S_link = 0, sl = 0;
     const bool binnable = d->T.mode == 5 && link_slices(d, &S_link, &sl);
-    const uint32_t per_group = binnable ? std::max(1u, 4096u / S_link) : 1u;
+    // a round gives every member a full binning round of pairs (each member's
+    // apply sweeps its whole DHLA once per round, so smaller shares would
+    // multiply that sweep); the group is bounded by 4096 slices and by
+    // kBatchBinBytes of bins
+    constexpr uint64_t kBatchBinBytes = 8ull << 30;
+    const uint64_t chunk = 1ull << d->T.bin_chunk_log2;
+    const uint64_t upd = (uint64_t)P.dirs * P.r;
+    const uint64_t cap_mean = binnable ? (chunk * upd + S_link - 1) / S_link : 0;
+    const uint64_t cap_link = (((cap_mean + cap_mean * d->T.bin_slack_pct / 100 + 256) + 3) & ~3ull);
+    uint32_t per_group = 1;
+    if (binnable) {
+        const uint64_t by_mem = kBatchBinBytes / std::max<uint64_t>(1, (uint64_t)S_link * cap_link * 4);
+        per_group = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4096u / S_link, by_mem));
+    }
 
     // which links join the batch: device-resident pairs on hs[0]'s device,
     // the same DHLA shape, each handle once; the others update on their own
@@ -539,14 +552,8 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     if (batch.empty()) return SD_OK;
 
     // the rounds' link tables live side by side in one buffer
-    const uint64_t chunk = 1ull << d->T.bin_chunk_log2;
-    uint64_t rounds_upper = 0;
-    {
-        const uint64_t members = std::min<uint64_t>(per_group, batch.size());
-        uint64_t total = 0;
-        for (uint32_t q : batch) total += ns[q];
-        rounds_upper = total / std::max<uint64_t>(1, chunk / members) + batch.size() + 1;
-    }
+    uint64_t rounds_upper = 1;
+    for (uint32_t q : batch) rounds_upper += (ns[q] + chunk - 1) / chunk;
     const uint64_t need = rounds_upper * per_group;
     SD_CK(d, cudaStreamSynchronize(d->stream));  // an earlier batch may still read the table
     if (d->links_cap < need) {
@@ -568,7 +575,6 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     }
 
     const uint32_t TP = d->T.bin_tile_pairs;
-    const uint64_t upd = (uint64_t)P.dirs * P.r;
     std::vector<uint64_t> done(batch.size(), 0);
     size_t cursor = 0, tab_used = 0;
     for (;;) {
@@ -580,7 +586,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         }
         if (mem.empty()) break;
         cursor = (mem.back() + 1) % batch.size();
-        const uint64_t budget = std::max<uint64_t>(TP, chunk / mem.size());
+        const uint64_t budget = chunk;
         LinkDesc *tab = d->links_h + tab_used;
         uint64_t tiles = 0;
         for (uint32_t m = 0; m < mem.size(); m++) {
@@ -608,9 +614,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         std::memset(&B, 0, sizeof B);
         B.S = (uint32_t)mem.size() * S_link;
         B.slice_log2 = sl;
-        const uint64_t mean = (budget * upd + S_link - 1) / S_link;
-        const uint64_t cap = mean + mean * d->T.bin_slack_pct / 100 + 256;
-        B.cap = (uint32_t)((cap + 3) & ~3ull);
+        B.cap = (uint32_t)cap_link;
         B.tile_pairs = TP;
         B.total_words = (uint64_t)P.dirs * d->G.dir_words;  // words of one link's DHLA
         const int rc = ensure_bin_mem(d, B);
