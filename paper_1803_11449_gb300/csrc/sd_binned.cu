@@ -78,10 +78,10 @@ __device__ __forceinline__ void bin_hash(const Geometry &G, const DirHash &H, co
             for (int i = 0; i < R; i++) {
                 const uint32_t ci = (i == 0) ? c0 : ((shr_clamp(key, (i - 1) * G.alpha) & kmask) ^ c0);
                 const uint32_t bitidx = base5[d][i] + (ci << cshift) + b;  // global bit index
-                const uint32_t s = slice0 + (bitidx >> sl5);  // slice over all links
+                const uint32_t sloc = bitidx >> sl5;  // slice within the link
                 const int u = (j * DIRS + d) * R + i;
-                ent[u] = (s << 20) | (bitidx & lmask);
-                if (FULL || ok[j]) met[u] = atomicAdd(&hist[s], 1u);
+                ent[u] = ((slice0 + sloc) << 20) | (bitidx & lmask);
+                if (FULL || ok[j]) met[u] = atomicAdd(&hist[sloc], 1u);
             }
         }
     }
@@ -110,7 +110,7 @@ struct TileSrc {
 template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
 k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
-      uint32_t lwpc, const LinkDesc *__restrict__ links, uint32_t nlinks, uint64_t ntiles_all) {
+      uint32_t lwpc, const LinkDesc *__restrict__ links, uint32_t nlinks, uint64_t ntiles_all, uint32_t SL) {
     constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
     extern __shared__ uint32_t sm[];
     // per slice: destination of sorted entry q is dst + q while q < lim
@@ -119,10 +119,12 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         uint32_t lim;
         uint32_t pad;
     };
-    Slot *slot = reinterpret_cast<Slot *>(sm);           // [S], 16-byte aligned
-    uint32_t *sorted = reinterpret_cast<uint32_t *>(slot + B.S);  // [blockDim * UPT]
-    uint32_t *hist = sorted + blockDim.x * UPT;          // [S]
-    uint32_t *offs = hist + B.S;                         // [S]
+    // indexed by the slice within the tile's link: a tile only touches the
+    // SL slices of its own link
+    Slot *slot = reinterpret_cast<Slot *>(sm);           // [SL], 16-byte aligned
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(slot + SL);  // [blockDim * UPT]
+    uint32_t *hist = sorted + blockDim.x * UPT;          // [SL]
+    uint32_t *offs = hist + SL;                          // [SL]
     __shared__ uint32_t warp_tot[32];
 
     const uint32_t TP = blockDim.x * PPT;
@@ -138,7 +140,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         for (int i = 0; i < R; i++)
             base5[d][i] = ((d ? (uint32_t)G.dir_words : 0u) + (uint32_t)i * (uint32_t)G.row_words) << 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) *B.work = 0;  // k_apply's slice counter
-    for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
+    for (uint32_t q = threadIdx.x; q < SL; q += blockDim.x) hist[q] = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         TileSrc ts;
         if (links) {
@@ -201,8 +203,8 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         __syncthreads();
         // exclusive scan of hist into offs; reserve each slice's run in its bin
         {
-            const uint32_t per = (B.S + blockDim.x - 1) / blockDim.x;
-            const uint32_t s0 = min(threadIdx.x * per, B.S), s1 = min(s0 + per, B.S);
+            const uint32_t per = (SL + blockDim.x - 1) / blockDim.x;
+            const uint32_t s0 = min(threadIdx.x * per, SL), s1 = min(s0 + per, SL);
             uint32_t cnt = 0;
             for (uint32_t q = s0; q < s1; q++) cnt += hist[q];
             uint32_t incl = cnt;
@@ -228,10 +230,11 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
                 const uint32_t hq = hist[q];
                 offs[q] = run;
                 if (hq) {
-                    const uint32_t b0 = atomicAdd(&B.count[q], hq);
-                    // entries q' = run + k go to bins[q][b0 + k] while b0 + k < cap
+                    const uint32_t qg = ts.slice0 + q;  // slice in this launch
+                    const uint32_t b0 = atomicAdd(&B.count[qg], hq);
+                    // entries q' = run + k go to bins[qg][b0 + k] while b0 + k < cap
                     Slot sq;
-                    sq.dst = B.bins + (uint64_t)q * B.cap + b0 - run;
+                    sq.dst = B.bins + (uint64_t)qg * B.cap + b0 - run;
                     sq.lim = b0 < B.cap ? run + (B.cap - b0) : run;
                     sq.pad = 0;
                     slot[q] = sq;
@@ -243,14 +246,14 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
         // scatter into slice order
 #pragma unroll
         for (int u = 0; u < UPT; u++)
-            if (full || ok[u / (DIRS * R)]) sorted[offs[ent[u] >> 20] + met[u]] = ent[u];
+            if (full || ok[u / (DIRS * R)]) sorted[offs[(ent[u] >> 20) - ts.slice0] + met[u]] = ent[u];
         __syncthreads();
         // write-out, one thread per entry; full bins fall back to red.or
         const uint64_t left = ts.n - ts.tile * TP;
         const uint32_t nu = (uint32_t)(left < TP ? left : TP) * DIRS * R;
         for (uint32_t q = threadIdx.x; q < nu; q += blockDim.x) {
             const uint32_t e = sorted[q];
-            const Slot sq = slot[e >> 20];
+            const Slot sq = slot[(e >> 20) - ts.slice0];
             if (q < sq.lim) {
                 sq.dst[q] = e;
             } else {
@@ -258,7 +261,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
                 red_or(ts.grid + w, 1u << (e & 31u));
             }
         }
-        for (uint32_t q = threadIdx.x; q < B.S; q += blockDim.x) hist[q] = 0;
+        for (uint32_t q = threadIdx.x; q < SL; q += blockDim.x) hist[q] = 0;
     }
 }
 
@@ -332,10 +335,11 @@ size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S) {
 template <int R, int DIRS, int PPT>
 static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                               const BinArgs &B, int num_sms, cudaStream_t s, const LinkDesc *links,
-                              uint32_t nlinks, uint64_t ntiles_all) {
+                              uint32_t nlinks, uint64_t ntiles_all, uint32_t slices_per_link) {
     auto kern = k_bin<R, DIRS, PPT>;
     const uint32_t threads = B.tile_pairs / PPT;
-    const size_t smem = bin_smem_bytes(B.tile_pairs, DIRS * R, B.S);
+    const uint32_t SL = links ? slices_per_link : B.S;
+    const size_t smem = bin_smem_bytes(B.tile_pairs, DIRS * R, SL);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -346,25 +350,25 @@ static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid,
     if (tiles < blocks) blocks = tiles ? tiles : 1;
     uint32_t lwpc = 0;
     while ((1u << lwpc) < G.wpc) lwpc++;
-    kern<<<(unsigned)blocks, threads, smem, s>>>(pairs, n, grid, G, B, lwpc, links, nlinks, ntiles_all);
+    kern<<<(unsigned)blocks, threads, smem, s>>>(pairs, n, grid, G, B, lwpc, links, nlinks, ntiles_all, SL);
     return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_bin_r(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                                 const BinArgs &B, int num_sms, cudaStream_t s, const LinkDesc *links,
-                                uint32_t nlinks, uint64_t ntiles_all) {
+                                uint32_t nlinks, uint64_t ntiles_all, uint32_t spl) {
     // 2 pairs per thread up to 1024-pair tiles (512 threads), else 4; the
     // API keeps tiles at 1024 pairs when dirs*r > 8 so registers suffice
     const bool two = B.tile_pairs <= 1024 || G.dirs * G.r > 8;
     if (G.dirs == 2) {
         if constexpr (2 * R <= 8) {
-            if (!two) return launch_bin<R, 2, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
+            if (!two) return launch_bin<R, 2, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, spl);
         }
-        return launch_bin<R, 2, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
+        return launch_bin<R, 2, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, spl);
     }
-    return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all)
-               : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all);
+    return two ? launch_bin<R, 1, 2>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, spl)
+               : launch_bin<R, 1, 4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, spl);
 }
 
 // One round: bin then apply (stream-ordered).  With `links` (a device table
@@ -375,12 +379,12 @@ static cudaError_t launch_rounds(const uint32_t *pairs, uint64_t n, uint32_t *gr
                                  uint32_t nlinks, uint64_t ntiles_all, uint32_t slices_per_link) {
     cudaError_t e;
     switch (G.r) {
-        case 3: e = launch_bin_r<3>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
-        case 4: e = launch_bin_r<4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
-        case 5: e = launch_bin_r<5>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
-        case 6: e = launch_bin_r<6>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
-        case 7: e = launch_bin_r<7>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
-        case 8: e = launch_bin_r<8>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all); break;
+        case 3: e = launch_bin_r<3>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
+        case 4: e = launch_bin_r<4>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
+        case 5: e = launch_bin_r<5>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
+        case 6: e = launch_bin_r<6>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
+        case 7: e = launch_bin_r<7>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
+        case 8: e = launch_bin_r<8>(pairs, n, grid, G, B, num_sms, s, links, nlinks, ntiles_all, slices_per_link); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
