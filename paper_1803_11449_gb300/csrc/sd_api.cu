@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -103,6 +104,16 @@ int szmax_of(uint32_t g, uint32_t r, double psi, double theta) {
     return (int)lo;
 }
 
+struct LaunchKey {
+    const void *fn;
+    int dev, threads;
+    size_t smem;
+    int per_sm;
+};
+std::mutex g_launch_mu;
+std::vector<LaunchKey> g_launch_cache;
+std::vector<std::pair<std::pair<const void *, int>, size_t>> g_smem_set;  // (fn, dev) -> opted-in bytes
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -158,10 +169,15 @@ struct sd_handle {
     uint64_t bin_mem_words = 0;
     BinArgs bin{};
 
-    // batched update (sd_update_many): link table and an event for stream joins
+    // batched update (sd_update_many): link tables in two halves used by
+    // alternate calls (a half is rewritten once the call two back has read
+    // it, so consecutive calls do not wait for each other), an event per
+    // half, and an event for stream joins
     LinkDesc *links_dev = nullptr;
     LinkDesc *links_h = nullptr;       // pinned
-    uint32_t links_cap = 0;
+    uint32_t links_cap = 0;            // descriptors per half
+    int links_half = 0;
+    cudaEvent_t ev_links[2] = {nullptr, nullptr};
     cudaEvent_t ev_batch = nullptr;
 
     uint64_t stage_pairs = 0;
@@ -190,6 +206,39 @@ struct sd_handle {
             return (h)->fail(e_ == cudaErrorMemoryAllocation ? SD_ERR_NOMEM : SD_ERR_CUDA,     \
                              "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
+
+namespace sd {
+
+cudaError_t prepare_launch(const void *kernel, int threads, size_t smem, int *per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_launch_mu);
+    for (const LaunchKey &k : g_launch_cache)
+        if (k.fn == kernel && k.dev == dev && k.threads == threads && k.smem == smem) {
+            *per_sm = k.per_sm;
+            return cudaSuccess;
+        }
+    if (smem > 48 * 1024) {
+        size_t *have = nullptr;
+        for (auto &p : g_smem_set)
+            if (p.first.first == kernel && p.first.second == dev) have = &p.second;
+        if (!have || *have < smem) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (have) *have = smem;
+            else g_smem_set.push_back({{kernel, dev}, smem});
+        }
+    }
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    *per_sm = n > 0 ? n : 1;
+    g_launch_cache.push_back({kernel, dev, threads, smem, *per_sm});
+    return cudaSuccess;
+}
+
+}  // namespace sd
 
 extern "C" {
 
@@ -266,6 +315,8 @@ static void release(sd_handle *h) {
     cudaFree(h->links_dev);
     cudaFreeHost(h->links_h);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
+    for (int b = 0; b < 2; b++)
+        if (h->ev_links[b]) cudaEventDestroy(h->ev_links[b]);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -308,6 +359,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         SD_CK(h, cudaEventCreateWithFlags(&h->ev_kern[b], cudaEventDisableTiming));
     }
     SD_CK(h, cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
+    for (int b = 0; b < 2; b++) SD_CK(h, cudaEventCreateWithFlags(&h->ev_links[b], cudaEventDisableTiming));
     const uint64_t words = (uint64_t)p->dirs * G.dir_words;
     const uint64_t nw = ((uint64_t)1 << p->k) >> 5;
     SD_CK(h, cudaMalloc(&h->grid, words * 4));
@@ -555,21 +607,27 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     uint64_t rounds_upper = 1;
     for (uint32_t q : batch) rounds_upper += (ns[q] + chunk - 1) / chunk;
     const uint64_t need = rounds_upper * per_group;
-    SD_CK(d, cudaStreamSynchronize(d->stream));  // an earlier batch may still read the table
+    const int half = d->links_half ^ 1;
     if (d->links_cap < need) {
+        SD_CK(d, cudaStreamSynchronize(d->stream));  // earlier batches may still read the tables
         cudaFree(d->links_dev);
         cudaFreeHost(d->links_h);
         d->links_dev = nullptr;
         d->links_h = nullptr;
         d->links_cap = 0;
-        SD_CK(d, cudaMalloc(&d->links_dev, need * sizeof(LinkDesc)));
-        SD_CK(d, cudaMallocHost(&d->links_h, need * sizeof(LinkDesc)));
+        SD_CK(d, cudaMalloc(&d->links_dev, 2 * need * sizeof(LinkDesc)));
+        SD_CK(d, cudaMallocHost(&d->links_h, 2 * need * sizeof(LinkDesc)));
         d->links_cap = (uint32_t)need;
+    } else {
+        SD_CK(d, cudaEventSynchronize(d->ev_links[half]));  // the call two back has read this half
     }
+    d->links_half = half;
+    LinkDesc *const tab_h = d->links_h + (size_t)half * d->links_cap;
+    LinkDesc *const tab_d = d->links_dev + (size_t)half * d->links_cap;
     // the members' earlier work comes first, on the driver's stream
     for (uint32_t q : batch) {
         sd_handle *h = hs[q];
-        if (h == d) continue;
+        if (h == d || h->stream == d->stream) continue;
         SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
         SD_CK(d, cudaStreamWaitEvent(d->stream, h->ev_batch, 0));
     }
@@ -587,7 +645,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         if (mem.empty()) break;
         cursor = (mem.back() + 1) % batch.size();
         const uint64_t budget = chunk;
-        LinkDesc *tab = d->links_h + tab_used;
+        LinkDesc *tab = tab_h + tab_used;
         uint64_t tiles = 0;
         for (uint32_t m = 0; m < mem.size(); m++) {
             const uint32_t i = batch[mem[m]];
@@ -608,7 +666,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
             done[mem[m]] += take;
         }
         if (tab_used + mem.size() > d->links_cap) return d->fail(SD_ERR_ARG, "sd_update_many: link table overflow");
-        SD_CK(d, cudaMemcpyAsync(d->links_dev + tab_used, tab, mem.size() * sizeof(LinkDesc), cudaMemcpyHostToDevice,
+        SD_CK(d, cudaMemcpyAsync(tab_d + tab_used, tab, mem.size() * sizeof(LinkDesc), cudaMemcpyHostToDevice,
                                  d->stream));
         BinArgs B;
         std::memset(&B, 0, sizeof B);
@@ -619,17 +677,18 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         B.total_words = (uint64_t)P.dirs * d->G.dir_words;  // words of one link's DHLA
         const int rc = ensure_bin_mem(d, B);
         if (rc != SD_OK) return rc;
-        SD_CK(d, launch_binned_links(d->links_dev + tab_used, (uint32_t)mem.size(), tiles, S_link, d->G, d->bin,
+        SD_CK(d, launch_binned_links(tab_d + tab_used, (uint32_t)mem.size(), tiles, S_link, d->G, d->bin,
                                      d->num_sms, d->stream));
         launched(2);
         tab_used += mem.size();
     }
+    SD_CK(d, cudaEventRecord(d->ev_links[half], d->stream));
     // later work on each member waits for the batch
     SD_CK(d, cudaEventRecord(d->ev_batch, d->stream));
     for (uint32_t q : batch) {
         sd_handle *h = hs[q];
         h->n_pairs += ns[q];
-        if (h == d) continue;
+        if (h == d || h->stream == d->stream) continue;
         SD_CK(h, cudaStreamWaitEvent(h->stream, d->ev_batch, 0));
     }
     return SD_OK;

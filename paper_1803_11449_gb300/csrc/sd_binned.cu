@@ -340,10 +340,8 @@ static cudaError_t launch_bin(const uint32_t *pairs, uint64_t n, uint32_t *grid,
     const uint32_t threads = B.tile_pairs / PPT;
     const uint32_t SL = links ? slices_per_link : B.S;
     const size_t smem = bin_smem_bytes(B.tile_pairs, DIRS * R, SL);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = links ? ntiles_all : (n + B.tile_pairs - 1) / B.tile_pairs;
     uint64_t blocks = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
@@ -389,10 +387,8 @@ static cudaError_t launch_rounds(const uint32_t *pairs, uint64_t n, uint32_t *gr
     }
     if (e != cudaSuccess) return e;
     const size_t smem_apply = (size_t)4 << B.slice_log2;
-    e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_apply);
-    if (e != cudaSuccess) return e;
     int per_sm_a = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_apply, 1024, smem_apply);
+    e = prepare_launch(reinterpret_cast<const void *>(k_apply), 1024, smem_apply, &per_sm_a);
     if (e != cudaSuccess) return e;
     uint64_t ablocks = (uint64_t)num_sms * (per_sm_a > 0 ? per_sm_a : 1);
     if (B.S < ablocks) ablocks = B.S;

@@ -450,10 +450,7 @@ cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaSt
     size_t smem = 16;
     A.smem_hot = hot_bytes <= (size_t)200 * 1024;
     if (A.smem_hot) smem = hot_bytes;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_restore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+
     uint64_t most = 0;
     for (uint32_t d = 0; d < G.dirs; d++) {
         if (!A.run[d]) continue;
@@ -463,9 +460,8 @@ cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaSt
     }
     if (most == 0) return cudaSuccess;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_restore, threads, smem);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_restore), (int)threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     uint64_t blocks = (uint64_t)num_sms * per_sm;
     if (most < blocks) blocks = most;
     dim3 grid((unsigned)blocks, G.dirs);
@@ -482,7 +478,8 @@ cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s) {
     const int smem = kSortSmall * (int)sizeof(unsigned long long);
-    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_sort_small), 1024, smem, &per_sm);
     if (e != cudaSuccess) return e;
     k_sort_small<<<dirs, 1024, smem, s>>>(hits, hits_cap, st, make_uint2(run[0], run[1]));
     return cudaGetLastError();
@@ -493,7 +490,8 @@ cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatB
 cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
                             cudaStream_t s, unsigned long long **out) {
     const int smem = kSortSmall * (int)sizeof(unsigned long long);
-    cudaError_t e = cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_sort_segments), 1024, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t segs = (n + kSortSmall - 1) / kSortSmall;
     k_sort_segments<<<(unsigned)segs, 1024, smem, s>>>(keys, n);

@@ -146,6 +146,12 @@ __device__ __forceinline__ uint32_t ld_weak(const uint32_t *p) {
     return v;
 }
 
+// Launch set-up shared by every launcher: opts the kernel in to `smem` bytes
+// of dynamic shared memory when above 48 KiB and returns its resident blocks
+// per SM for (threads, smem).  Both are looked up once per (kernel, device,
+// shape) and cached, so steady-state launches make no extra driver calls.
+cudaError_t prepare_launch(const void *kernel, int threads, size_t smem, int *per_sm);
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_update(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                           const Tuning &T, int num_sms, cudaStream_t s);

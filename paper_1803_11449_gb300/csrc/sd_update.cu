@@ -196,13 +196,8 @@ static cudaError_t launch3(const uint32_t *pairs, uint64_t n, uint32_t *grid, co
     auto kern = k_update<R, MODE, UNROLL>;
     const uint32_t flog = MODE >= 3 ? T.filter_log2 : 0u;
     const size_t smem = MODE >= 3 ? ((size_t)8 << flog) : 0;
-    cudaError_t e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)T.block_threads, smem);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)T.block_threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int want = T.blocks_per_sm ? (int)T.blocks_per_sm : per_sm;
