@@ -445,6 +445,153 @@ def run_batching(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def _serve_window(args):
+    """Traffic of serving link `link` (one window, cycled through its ring):
+    core-link traffic with 50-300 planted hosts; link 0 also carries a DDoS
+    victim (one dst, `ddos` distinct spoofed srcs) and link 1 a scanner (one
+    src, `scan` distinct dsts), written over random positions."""
+    link, n, planted, ddos, scan = args
+    w = T.WORKLOADS[WORKLOAD].with_(n=n, planted=planted)
+    win = T.make_window(w, T.window_seed(4, link=link))
+    pairs = win.pairs
+    rng = np.random.default_rng(T.window_seed(4, link=link) ^ 0xDD05)
+    special = None
+    if link == 0 and ddos:
+        victim = np.uint32(rng.integers(0, 2**32))
+        pos = rng.choice(n, size=ddos, replace=False)
+        pairs[pos, 0] = T.ip_of(0x7000_0000, np.arange(ddos), int(rng.integers(0, 2**32)))
+        pairs[pos, 1] = victim
+        special = (1, int(victim))
+    elif link == 1 and scan:
+        scanner = np.uint32(rng.integers(0, 2**32))
+        pos = rng.choice(n, size=scan, replace=False)
+        pairs[pos, 0] = scanner
+        pairs[pos, 1] = T.ip_of(0x7100_0000, np.arange(scan), int(rng.integers(0, 2**32)))
+        special = (0, int(scanner))
+    return pairs, special
+
+
+def run_serving(args, rank, world, local):
+    """The serving engine in real time: `serve_links` links, each with its
+    sketch resident under an HBM budget, take Poisson arrivals of batches of
+    uniform [64K, 4M] pairs (sharing `serve_load` Gpps offered) into a
+    device ring (the link's synthetic traffic, one window long, cycled);
+    the engine (continuous batching, a window closed every `window_pairs`
+    pairs of a link) runs for `serve_seconds`.  Reports the served rate,
+    pairs dropped at full rings, the close latency (end of the completing
+    update to the report on the host) and the latency from the arrival of a
+    window's last batch to its report."""
+    import multiprocessing as mp
+
+    W, nl = args.window_pairs, args.serve_links
+    rng = np.random.default_rng(0x5D5A0400 + rank)
+    planted = rng.integers(50, 301, size=nl)
+    jobs = [(rank * nl + i, W, int(p), args.serve_ddos, args.serve_scan) for i, p in enumerate(planted)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        gen = pool.map(_serve_window, jobs)
+    wins = [g[0] for g in gen]
+    special = {i: g[1] for i, g in enumerate(gen) if g[1] is not None}
+    rate = args.serve_load * 1e9 / nl                            # pairs/s per link
+    lo, hi = 1 << 16, 1 << 22
+    T_run = args.serve_seconds
+    arr_t, arr_n = [], []
+    for _ in range(nl):
+        m = int(T_run * rate / ((lo + hi) / 2) * 1.3) + 16
+        t = np.cumsum(rng.exponential((lo + hi) / 2 / rate, size=m))
+        k = int(np.searchsorted(t, T_run))
+        arr_t.append(t[:k])
+        arr_n.append(rng.integers(lo, hi + 1, size=k))
+
+    import torch
+
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import serving
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rings = [torch.from_numpy(wn.reshape(-1).view(np.int32)).cuda() for wn in wins]
+    del wins
+    srv = serving.Server(T.WORKLOADS[WORKLOAD], W, hbm_budget=int(args.serve_budget_gb * (1 << 30)),
+                         device=local, stream=stream, bin_chunk_log2=args.serve_chunk_log2)
+    admitted = 0
+    for i in range(nl):
+        admitted += srv.open_link(i, T.window_seed(4, link=rank * nl + i))
+        srv.attach_ring(i, rings[i])
+    # warm-up: one window on every admitted link
+    for i in srv.admitted:
+        srv.advance(i, W)
+    srv.drain()
+    torch.cuda.synchronize()
+    found = {i: any(int(ip) == sp[1] for ip, d in zip(r.report.hits["ip"], r.report.hits["dir"]) if d == sp[0])
+             for i, sp in special.items() for r in srv.reports if r.link == i}
+    srv.reports.clear()
+    base = {i: srv.links[i].tail for i in srv.admitted}
+    win0 = {i: srv.links[i].window for i in srv.admitted}
+    acc = {i: [] for i in srv.admitted}             # accepted batches: (pairs served after it, arrival)
+    nxt = {i: 0 for i in srv.admitted}
+    dropped = offered = 0
+    clock = ClockSampler(local)
+    t0 = time.perf_counter()
+    with clock:
+        while True:
+            now = time.perf_counter() - t0
+            if now >= T_run and srv.pending_pairs() == 0:
+                break
+            for i in srv.admitted:
+                L = srv.links[i]
+                while nxt[i] < len(arr_t[i]) and arr_t[i][nxt[i]] <= now:
+                    n = int(arr_n[i][nxt[i]])
+                    offered += n
+                    if L.head + n - L.tail <= W:
+                        srv.advance(i, n)
+                        acc[i].append((L.head - base[i], arr_t[i][nxt[i]]))
+                    else:
+                        dropped += n
+                    nxt[i] += 1
+            if srv.pending_pairs():
+                srv.step()
+            elif now < T_run:
+                time.sleep(20e-6)
+        torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    served = sum(srv.links[i].tail - base[i] for i in srv.admitted)
+    lat = []
+    for r in srv.reports:
+        end = (r.window - win0[r.link] + 1) * W
+        a = acc[r.link]
+        j = next((q for q, (cum, _) in enumerate(a) if cum >= end), None)
+        if j is not None:
+            lat.append(r.done_at - t0 - a[j][1])
+    close = [r.close_s for r in srv.reports]
+    n_win = len(srv.reports)
+    steps = srv.steps
+    srv.shutdown()
+    value = dist_max(elapsed, world)
+    if rank != 0:
+        return
+    pct = lambda a, q: 1e3 * float(np.percentile(a, q)) if len(a) else None
+    line = {
+        "metric": "packets/s (Gpps), served under Poisson arrivals", "value": world * served / value / 1e9,
+        "unit": "Gpps", "n_gpus": args.gpus, "steps": steps, "warmup": 1,
+        "ms_per_step": 1e3 * elapsed / max(1, steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"serving: {nl} links, Poisson batches of uniform [64K, 4M] pairs sharing "
+                               f"{args.serve_load} Gpps offered, a window closed every {W} pairs per link, "
+                               f"core-link sketch per link, HBM budget {args.serve_budget_gb} GiB, "
+                               f"DDoS victim ({args.serve_ddos} srcs) on link 0, scanner ({args.serve_scan} "
+                               f"dsts) on link 1, {T_run} s",
+                   "window_pairs": W, "offered_gpps": args.serve_load, "links": nl, "admitted": admitted},
+        "offered_pairs": int(offered), "served_pairs": int(served), "dropped_pairs": int(dropped),
+        "windows_closed": n_win, "attacks_reported_in_warmup_window": {str(k): v for k, v in found.items()},
+        "latency_ms_last_arrival_to_report": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n": len(lat)},
+        "close_ms": {"p50": pct(close, 50), "p99": pct(close, 99)},
+        "clocks": clock.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,6 +618,16 @@ def main():
                     help="many links of uneven size: batched versus one window at a time")
     ap.add_argument("--links", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--serving", action="store_true",
+                    help="the serving engine in real time under Poisson arrivals")
+    ap.add_argument("--serve-links", type=int, default=16)
+    ap.add_argument("--window-pairs", type=int, default=1 << 26)
+    ap.add_argument("--serve-load", type=float, default=10.0, help="offered Gpps, all links")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=2.0)
+    ap.add_argument("--serve-chunk-log2", type=int, default=20)
+    ap.add_argument("--serve-ddos", type=int, default=2_000_000)
+    ap.add_argument("--serve-scan", type=int, default=500_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -481,6 +638,8 @@ def main():
         run_reference(args, rank, world)
     elif args.batching:
         run_batching(args, rank, world, local)
+    elif args.serving:
+        run_serving(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -144,8 +144,11 @@ int sd_check_params(const sd_params *p);
  * *p is invalid. */
 uint64_t sd_grid_words(const sd_params *p);
 
-/* Device bytes a handle with *p allocates (DHLA, restore scratch, ingest
- * staging); 0 if *p is invalid. */
+/* Device bytes a handle with *p holds from sd_create on: the DHLA, the hot
+ * sets, the candidate and hit buffers; 0 if *p is invalid.  Not counted,
+ * because they are allocated on first use: the staging of host-pointer
+ * updates (2 * stage_pairs * 8 bytes) and the binned update's scratch
+ * (sd_scratch_bytes). */
 uint64_t sd_device_bytes(const sd_params *p);
 
 /* Create a handle: allocate a zeroed DHLA per direction and the scratch
@@ -190,6 +193,14 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
  * after it).  The other links take sd_update.  Returns
  * the first error, if any. */
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count);
+
+/* Device bytes of the binned update's scratch (bins and counters) that h
+ * allocates, with its current tuning, when it updates alone (links <= 1)
+ * or drives sd_update_many over `links` members; the scratch grows to the
+ * largest such need and is kept until sd_destroy.  0 when h does not bin
+ * (tuning mode other than 5, or a DHLA of more than 4096 slices) or h is
+ * NULL.  For memory budgets: a handle holds sd_device_bytes plus this. */
+uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links);
 
 /* Wait for all work queued on the handle's stream. */
 int sd_sync(sd_handle *h);

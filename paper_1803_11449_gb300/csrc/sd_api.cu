@@ -288,8 +288,9 @@ uint64_t sd_device_bytes(const sd_params *p) {
     uint64_t pc, cc, hc, rc, sp;
     resolve_caps(p, &pc, &cc, &hc, &rc, &sp);
     const uint64_t cells = (uint64_t)p->r << p->k;
+    (void)sp;  // the host-pointer staging is allocated on first use, not counted
     return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + 2 * hc * 8) +
-           sizeof(StatBlock) + 2 * sp * 8;
+           sizeof(StatBlock);
 }
 
 static void release(sd_handle *h) {
@@ -541,13 +542,43 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
 
 // Slices of one handle's DHLA for the binned update: (S, slice_log2), or
 // false when the DHLA is too large to bin.
-static bool link_slices(const sd_handle *h, uint32_t *S, uint32_t *sl_out) {
+// Layout of a batched update driven by h (sd_update_many): slices per
+// member DHLA, slice size, bin capacity per slice, members per round.  A
+// round gives every member a full binning round of pairs (each member's
+// apply sweeps its whole DHLA once per round, so smaller shares would
+// multiply that sweep); a round is bounded by 4096 slices and by
+// kBatchBinBytes of bins.  False when h does not bin.
+struct BatchLayout {
+    uint32_t S_link, sl, per_group;
+    uint64_t cap_link;
+};
+static bool batch_layout(const sd_handle *h, BatchLayout *L) {
+    constexpr uint64_t kBatchBinBytes = 8ull << 30;
     BinArgs B;
     uint64_t words = 0;
-    if (!bin_layout(h, &B, &words)) return false;
-    *S = B.S;
-    *sl_out = B.slice_log2;
+    if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return false;
+    L->S_link = B.S;
+    L->sl = B.slice_log2;
+    const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
+    const uint64_t upd = (uint64_t)h->p.dirs * h->p.r;
+    const uint64_t cap_mean = (chunk * upd + L->S_link - 1) / L->S_link;
+    L->cap_link = ((cap_mean + cap_mean * h->T.bin_slack_pct / 100 + 256) + 3) & ~3ull;
+    const uint64_t by_mem = kBatchBinBytes / std::max<uint64_t>(1, (uint64_t)L->S_link * L->cap_link * 4);
+    L->per_group = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4096u / L->S_link, by_mem));
     return true;
+}
+
+uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
+    if (!h) return 0;
+    BinArgs B;
+    uint64_t words = 0;
+    if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return 0;
+    if (links <= 1) return words * 4;
+    BatchLayout L;
+    batch_layout(h, &L);
+    const uint64_t m = std::min<uint64_t>(links, L.per_group);
+    const uint64_t S = m * L.S_link;
+    return std::max<uint64_t>(words, S * L.cap_link + S + 4) * 4;
 }
 
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count) {
@@ -558,22 +589,11 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     sd_handle *d = hs[0];
     DeviceGuard dg(d->p.device);
     const sd_params &P = d->p;
-    uint32_t S_link = 0, sl = 0;
-    const bool binnable = d->T.mode == 5 && link_slices(d, &S_link, &sl);
-    // a round gives every member a full binning round of pairs (each member's
-    // apply sweeps its whole DHLA once per round, so smaller shares would
-    // multiply that sweep); the group is bounded by 4096 slices and by
-    // kBatchBinBytes of bins
-    constexpr uint64_t kBatchBinBytes = 8ull << 30;
+    BatchLayout BL{0, 0, 1, 0};
+    const bool binnable = batch_layout(d, &BL);
+    const uint32_t S_link = BL.S_link, sl = BL.sl, per_group = BL.per_group;
+    const uint64_t cap_link = BL.cap_link;
     const uint64_t chunk = 1ull << d->T.bin_chunk_log2;
-    const uint64_t upd = (uint64_t)P.dirs * P.r;
-    const uint64_t cap_mean = binnable ? (chunk * upd + S_link - 1) / S_link : 0;
-    const uint64_t cap_link = (((cap_mean + cap_mean * d->T.bin_slack_pct / 100 + 256) + 3) & ~3ull);
-    uint32_t per_group = 1;
-    if (binnable) {
-        const uint64_t by_mem = kBatchBinBytes / std::max<uint64_t>(1, (uint64_t)S_link * cap_link * 4);
-        per_group = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4096u / S_link, by_mem));
-    }
 
     // which links join the batch: device-resident pairs on hs[0]'s device,
     // the same DHLA shape, each handle once; the others update on their own

@@ -37,7 +37,7 @@ SD_FLAG_REPORT_OVERFLOW = 8
 
 # every function the header declares, in declaration order
 EXPORTS = ["sd_default_params", "sd_check_params", "sd_grid_words", "sd_device_bytes", "sd_create",
-           "sd_update", "sd_close_window", "sd_close_many", "sd_update_many", "sd_sync", "sd_destroy",
+           "sd_update", "sd_close_window", "sd_close_many", "sd_update_many", "sd_scratch_bytes", "sd_sync", "sd_destroy",
            "sd_last_error", "sd_get_grid",
            "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_kernel_launches",
            "sd_get_tuning", "sd_set_tuning", "sd_update_noalloc"]
@@ -121,6 +121,7 @@ def lib():
                 "sd_get_candidates": (ctypes.c_int64, [_VP, ctypes.c_uint32, _VP, ctypes.c_uint64]),
                 "sd_merge": (ctypes.c_int, [_VP, _VP]),
                 "sd_kernel_launches": (ctypes.c_uint64, []),
+                "sd_scratch_bytes": (ctypes.c_uint64, [_VP, ctypes.c_uint32]),
                 "sd_get_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_set_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_update_noalloc": (ctypes.c_int, [_P(sd_params), _VP, _VP, ctypes.c_uint64, _VP]),
@@ -317,6 +318,11 @@ def sd_get_candidates(h: Handle, direction: int, cap: int | None = None):
 
 def sd_merge(dst: Handle, src: Handle) -> None:
     _check(lib().sd_merge(dst.ptr, src.ptr), dst.ptr)
+
+
+def sd_scratch_bytes(h: Handle, links: int = 1) -> int:
+    """Device bytes of the binned update's scratch of h (see sd.h)."""
+    return int(lib().sd_scratch_bytes(h.ptr, links))
 
 
 def sd_kernel_launches() -> int:
