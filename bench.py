@@ -34,6 +34,18 @@ WORKLOAD = "core"
 WORKLOAD_DESC = ("core-link window: 2^26 (src,dst) uint32 pairs, 2^24 Zipf(1.05) sources, 2^26 "
                  "destinations, 500 planted super points (1,024-200,000 peers); DHLA g=512 r=4 "
                  "k=16 alpha=8 (16 MiB per direction, L2-resident), theta=1024, both directions")
+DESCS = {
+    "core": WORKLOAD_DESC,
+    "paper": ("the paper's sketch parameters on core-link traffic: 2^26 (src,dst) uint32 pairs, 2^24 "
+              "Zipf(1.05) sources, 2^26 destinations, 500 planted super points (1,024-200,000 peers); "
+              "DHLA g=1024 r=5 k=14 alpha=6 (10 MiB per direction), theta=1024, both directions"),
+    "stress": ("stress window: 2^30 (src,dst) uint32 pairs in flows of 8 packets, 2^28 Zipf(1.0) sources, "
+               "2^30 destinations, 10^4 planted super points (1,024-10^7 peers); DHLA g=1024 r=4 k=18 "
+               "alpha=7 (128 MiB per direction, larger than L2), theta=1024, both directions"),
+    "tiny": ("small window: 2^20 (src,dst) uint32 pairs, 2^16 Zipf(1.1) sources, uniform destinations, "
+             "20 planted super points (1,500-4,000 peers); DHLA g=256 r=4 k=12 alpha=10, theta=1024, "
+             "outbound only"),
+}
 BYTES_PER_PAIR = 8
 GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
 CPU_SAMPLE_PAIRS = 1 << 23
@@ -325,7 +337,10 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "pairs_per_step_per_gpu": n,
-                   "l2": "inputs larger than L2 (512 MiB of pairs per step)",
+                   "l2": (f"inputs larger than L2 ({BYTES_PER_PAIR * n / 2**20:.0f} MiB of pairs per step)"
+                          if BYTES_PER_PAIR * n > 129e6 else
+                          f"inputs of {BYTES_PER_PAIR * n / 2**20:.0f} MiB fit L2 and are not flushed: "
+                          "a development number, not a bench value"),
                    "parallelism": f"{world} independent link(s), one per GPU",
                    "traffic": args.traffic,
                    "tuning": dict({f: getattr(tuning, f) for f, _ in tuning._fields_},
@@ -335,7 +350,8 @@ def run_ours(args, rank, world, local):
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
         "update_ms": 1e3 * t_upd,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(tuning.mode, n),
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(tuning.mode, n) if WORKLOAD == "core" else None,
                      "kernel": "k_bin+k_apply" if tuning.mode == 5 else "k_update",
                      "peak_source": f"hbm_gbs, {peak_kind}",
                      "algorithmic_bytes_per_pair": BYTES_PER_PAIR},
@@ -618,6 +634,8 @@ def main():
                     help="many links of uneven size: batched versus one window at a time")
     ap.add_argument("--links", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--workload", default="core", choices=sorted(DESCS),
+                    help="window and sketch configuration of the default mode")
     ap.add_argument("--serving", action="store_true",
                     help="the serving engine in real time under Poisson arrivals")
     ap.add_argument("--serve-links", type=int, default=16)
@@ -631,8 +649,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global TRAFFIC
+    global TRAFFIC, WORKLOAD, WORKLOAD_DESC
     TRAFFIC = args.traffic
+    if not (args.batching or args.serving):
+        WORKLOAD, WORKLOAD_DESC = args.workload, DESCS[args.workload]
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -129,6 +129,18 @@ typedef struct {
     uint32_t bin_chunk_log2; /* mode 5: pairs per bin-then-apply round, log2: 12..28 */
     uint32_t bin_slack_pct;  /* mode 5: bin capacity above the mean fill, percent
                                 (0xFFFFFFFF sets 0); a full bin falls back to atomics */
+    uint32_t restore;        /* how the close finds K (always set, like mode):
+                                0: HE(0) x HE(1) joined, the rest of each address
+                                   by inverting DH_0 (work |HE(0)||HE(1)| 2^max(0,32-2k));
+                                1: the paper's staged join (§4.2, Algorithms 3-4):
+                                   HE(0) x HE(1) x HE(2), then one row at a time
+                                   through two intermediate buffers of 4 cand_cap
+                                   entries per direction (allocated on first use);
+                                   work |HE(0)||HE(1)||HE(2)| + the survivors x |HE(i)|;
+                                   an intermediate list past its buffer flags the
+                                   direction SD_FLAG_OVERLOAD_CANDS, and a first
+                                   stage above pair_cap tuples SD_FLAG_OVERLOAD_PAIRS.
+                                Both give the same K and the same report. */
 } sd_tuning;
 
 /* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,

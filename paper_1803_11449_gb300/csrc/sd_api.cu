@@ -164,6 +164,12 @@ struct sd_handle {
     bool have_close = false;
     CloseState cs{};
 
+    // staged join (tuning restore = 1): all hot lists and the two
+    // intermediate buffers, allocated on first use
+    uint32_t *he_all = nullptr;
+    unsigned long long *jsub = nullptr;  // [2][dirs][join_cap]
+    uint64_t join_cap = 0;
+
     // binned update (mode 5): scratch sized for the current tuning
     uint32_t *bin_mem = nullptr;       // bins [S][cap], then count [S], then work [1]
     uint64_t bin_mem_words = 0;
@@ -304,6 +310,8 @@ static void release(sd_handle *h) {
     cudaFree(h->hits);
     cudaFree(h->hits_tmp);
     cudaFree(h->bin_mem);
+    cudaFree(h->he_all);
+    cudaFree(h->jsub);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     cudaFreeHost(h->big_h);
@@ -342,7 +350,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         G.h[d].A0inv = inverse_odd(G.h[d].A0);
     }
     // binned update, 128 KiB slices, 1024-pair tiles, 2^24-pair rounds (autotuned on GB300)
-    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100};
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0};
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -756,7 +764,7 @@ static int close_phase_a(sd_handle *h, sd_report *out) {
     h->report.clear();
     h->last_ncand[0] = h->last_ncand[1] = 0;
     SD_CK(h, launch_row_stats(h->grid, h->G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
-    SD_CK(h, launch_compact(h->hotmap, h->G, h->he, h->stream));
+    SD_CK(h, launch_compact(h->hotmap, h->G, h->he, 2, h->stream));
     launched(2);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
     return SD_OK;
@@ -780,7 +788,9 @@ static int close_phase_b(sd_handle *h, sd_report *out) {
         const int szmax = szmax_of(G.g, G.r, c.psi[d], h->p.theta);
         out->szmax[d] = szmax < 0 ? 0 : (uint32_t)szmax;
         const uint64_t n0 = h->st_h->nhot[d][0], n1 = h->st_h->nhot[d][1];
-        if (n0 * n1 > h->pair_cap) {
+        // the work bound: (c0, c1) pairs, or the staged join's first-stage tuples
+        const uint64_t n2 = h->T.restore == 1 ? h->st_h->nhot[d][2] : 1;
+        if (n0 * n1 > h->pair_cap || (n2 && n0 * n1 > h->pair_cap / n2)) {
             c.flags |= SD_FLAG_OVERLOAD_PAIRS << (8 * d);
             continue;
         }
@@ -798,10 +808,35 @@ static int close_phase_b(sd_handle *h, sd_report *out) {
     A.stats = h->st_d;
     A.cand_cap = h->cand_cap;
     A.hits_cap = h->hits_cap;
-    SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
+    if (h->T.restore == 1) {
+        if (!h->jsub) {
+            h->join_cap = 4 * h->cand_cap;
+            SD_CK(h, cudaMalloc(&h->he_all, ((uint64_t)G.dirs * G.r << G.k) * 4));
+            SD_CK(h, cudaMalloc(&h->jsub, 2 * G.dirs * h->join_cap * 8));
+        }
+        JoinArgs J;
+        std::memset(&J, 0, sizeof J);
+        J.he = h->he_all;
+        J.sub[0] = h->jsub;
+        J.sub[1] = h->jsub + G.dirs * h->join_cap;
+        J.cap = h->join_cap;
+        J.cand = h->cand;
+        J.cand_cap = h->cand_cap;
+        J.stats = h->st_d;
+        for (uint32_t d = 0; d < G.dirs; d++) {
+            J.run[d] = A.run[d];
+            for (uint32_t i = 0; i < G.r; i++) J.n[d][i] = h->st_h->nhot[d][i];
+        }
+        SD_CK(h, launch_compact(h->hotmap, G, h->he_all, G.r, h->stream));
+        SD_CK(h, launch_join(G, J, h->num_sms, h->stream));
+        launched(1 + (G.r - 2));
+    } else {
+        SD_CK(h, launch_restore(G, A, h->num_sms, h->stream));
+        launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 1 : 0);
+    }
     SD_CK(h, launch_estimate(G, A, h->num_sms, h->stream));
     SD_CK(h, launch_sort_small(h->hits, h->hits_cap, h->st_d, A.run, G.dirs, h->stream));
-    launched(((A.run[0] && A.n0[0] && A.n1[0]) || (A.run[1] && A.n0[1] && A.n1[1])) ? 3 : 2);
+    launched(2);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
     for (uint32_t d = 0; d < G.dirs; d++)
         if (A.run[d])
@@ -820,7 +855,10 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
         const uint64_t nk = h->st_h->ncand[d];
         out->n_cand[d] = nk;
         h->last_ncand[d] = nk;
-        if (nk > h->cand_cap) {
+        bool join_full = false;  // a staged-join list that overflowed its buffer: K is incomplete
+        if (h->T.restore == 1)
+            for (uint32_t i = 2; i + 1 < h->G.r; i++) join_full |= h->st_h->jcount[d][i] > h->join_cap;
+        if (nk > h->cand_cap || join_full) {
             c.flags |= SD_FLAG_OVERLOAD_CANDS << (8 * d);
             continue;
         }
@@ -1062,6 +1100,7 @@ int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     out->bin_tile_pairs = h->T.bin_tile_pairs;
     out->bin_chunk_log2 = h->T.bin_chunk_log2;
     out->bin_slack_pct = h->T.bin_slack_pct;
+    out->restore = h->T.restore;
     return SD_OK;
 }
 
@@ -1070,6 +1109,8 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
     Tuning T = h->T;
     if (t->mode > 5) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..5");
     T.mode = t->mode;
+    if (t->restore > 1) return h->fail(SD_ERR_ARG, "sd_set_tuning: restore must be 0 or 1");
+    T.restore = t->restore;
     if (t->block_threads) {
         if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
             return h->fail(SD_ERR_ARG, "sd_set_tuning: block_threads must be a multiple of 32 in [64, 1024]");

@@ -4,7 +4,8 @@
 //   k_row_stats   z_0 = g - popcount for every estimator, ZR(i) per row, the
 //                 hot bitmap of each row (z_0 <= zhot, i.e. z_0 < Zmin) and
 //                 |HE(i)|.
-//   k_compact     sorted lists HE(0) and HE(1) from their bitmaps.
+//   k_compact     sorted lists HE(0) and HE(1) (all HE(i) for the staged
+//                 join of sd_join.cu) from their bitmaps.
 //   k_restore     the candidate set K = {a : DH_i(a) in HE(i) for all i} and,
 //                 fused, SZ(a) from ULE(a) = AND of a's r estimators, keeping
 //                 (a, SZ) when SZ <= szmax.
@@ -89,11 +90,11 @@ k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *_
 // ---------------------------------------------------------------- compact
 // One block per (dir, row in {0, 1}): HE(row) in ascending order.
 __global__ void __launch_bounds__(1024)
-k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict__ he) {
-    const uint32_t dir = blockIdx.x >> 1, row = blockIdx.x & 1u;
+k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict__ he, uint32_t rows) {
+    const uint32_t dir = blockIdx.x / rows, row = blockIdx.x % rows;
     const uint32_t nw = (1u << G.k) >> 5;
     const uint32_t *bm = hotmap + ((uint64_t)dir * G.r + row) * nw;
-    uint32_t *out = he + ((uint64_t)dir * 2 + row) * (1ull << G.k);
+    uint32_t *out = he + ((uint64_t)dir * rows + row) * (1ull << G.k);
     const uint32_t per = (nw + blockDim.x - 1) / blockDim.x;
     const uint32_t w0 = threadIdx.x * per;
     const uint32_t w1 = min(w0 + per, nw);
@@ -428,8 +429,9 @@ cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, cudaStream_t s) {
-    k_compact<<<G.dirs * 2, 1024, 0, s>>>(hotmap, G, he);
+cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, uint32_t rows,
+                           cudaStream_t s) {
+    k_compact<<<G.dirs * rows, 1024, 0, s>>>(hotmap, G, he, rows);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct Tuning {
     uint32_t bin_tile_pairs; // mode 5: pairs per binning tile
     uint32_t bin_chunk_log2; // mode 5: pairs per bin/apply round = 2^bin_chunk_log2
     uint32_t bin_slack_pct;  // mode 5: bin capacity over the mean fill, in percent
+    uint32_t restore;        // 0 DH_0 inversion (k_restore), 1 staged join (sd_join.cu)
 };
 
 // One link of a batched binned update (device memory table).
@@ -74,6 +75,7 @@ struct StatBlock {
     unsigned int nhot[2][kMaxRows];
     unsigned int big_sort[2];  // 1: hits did not fit the one-block sort
     unsigned int pad[2];
+    unsigned long long jcount[2][kMaxRows];  // staged join: entries stage i produced
 };
 
 struct RestoreArgs {
@@ -91,6 +93,18 @@ struct RestoreArgs {
     uint32_t tile0;          // c0 values per block tile
     uint32_t jchunk;         // (c1, t) items per block tile
     int smem_hot;            // rows 2..r-1 of the hot bitmap staged in shared memory
+};
+
+// The staged join of sd_join.cu (the paper's Algorithms 3 and 4).
+struct JoinArgs {
+    const uint32_t *he;      // [dirs][r][2^k] hot lists
+    unsigned long long *sub[2];  // [dirs][cap] intermediate buffers: (partial << 32) | c0
+    uint64_t cap;
+    uint32_t *cand;          // [dirs][cand_cap]
+    uint64_t cand_cap;
+    StatBlock *stats;        // ncand, jcount
+    uint32_t n[2][kMaxRows]; // |HE(i)|
+    uint32_t run[2];
 };
 
 // ---------------------------------------------------------------- hashes
@@ -157,9 +171,12 @@ cudaError_t launch_update(const uint32_t *pairs, uint64_t n, uint32_t *grid, con
                           const Tuning &T, int num_sms, cudaStream_t s);
 cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, uint32_t *hotmap,
                              StatBlock *st, int num_sms, cudaStream_t s);
-cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, cudaStream_t s);
+// HE(i) for rows 0..rows-1 of every direction, ascending: he[dir][row][2^k]
+cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, uint32_t rows, cudaStream_t s);
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
 cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms, cudaStream_t s);
+// K by the staged join: r-2 launches (rows 2..r-1), both directions each
+cudaError_t launch_join(const Geometry &G, const JoinArgs &J, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s);
 cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
