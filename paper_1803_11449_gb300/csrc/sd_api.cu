@@ -964,6 +964,39 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
     if (!hs || !outs || !rcs) return count ? SD_ERR_ARG : SD_OK;
     for (uint32_t i = 0; i < count; i++)
         if (!hs[i]) return SD_ERR_ARG;
+    {
+        std::vector<sd_handle *> sorted(hs, hs + count);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return SD_ERR_ARG;
+    }
+    // Each handle's close runs on its side stream (ordered after everything
+    // queued on its stream so far, and its stream waits for the close), so
+    // the closes of handles that share one stream still overlap on the GPU.
+    const bool side = count > 1;
+    if (side) {
+        for (uint32_t i = 0; i < count; i++) {
+            sd_handle *h = hs[i];
+            DeviceGuard dg(h->p.device);
+            SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
+            SD_CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_batch, 0));
+        }
+        for (uint32_t i = 0; i < count; i++) std::swap(hs[i]->stream, hs[i]->copy_stream);
+    }
+    struct Unswap {
+        sd_handle *const *hs;
+        uint32_t count;
+        bool on;
+        ~Unswap() {
+            if (!on) return;
+            for (uint32_t i = 0; i < count; i++) {
+                sd_handle *h = hs[i];
+                std::swap(h->stream, h->copy_stream);
+                DeviceGuard dg(h->p.device);
+                cudaEventRecord(h->ev_batch, h->copy_stream);
+                cudaStreamWaitEvent(h->stream, h->ev_batch, 0);
+            }
+        }
+    } unswap{hs, count, side};
     std::vector<char> live(count, 1);
     auto step = [&](auto &&phase) {
         for (uint32_t i = 0; i < count; i++) {
