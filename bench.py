@@ -48,7 +48,7 @@ DESCS = {
 }
 BYTES_PER_PAIR = 8
 GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
-CPU_SAMPLE_PAIRS = 1 << 23
+CPU_SAMPLE_PAIRS = 1 << 26
 
 
 def profiled_traffic(mode: int, n: int):
@@ -203,6 +203,55 @@ def cpu_oracle_rate(pairs: np.ndarray, sample: int):
     return sample / dt, dt
 
 
+def _oracle_part(args):
+    """Worker of the parallel CPU baseline: the oracle's Algorithm 1 over one
+    contiguous part of the pairs (read from shared memory) into a new grid."""
+    import oracle as O
+    from multiprocessing import shared_memory
+    name, n, lo, hi, sketch, seed = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        pairs = np.ndarray((n, 2), dtype=np.uint32, buffer=shm.buf)
+        op = O.params_from(sketch, seed=seed)
+        grid = O.new_grid(op)
+        O.update(op, grid, pairs[lo:hi])
+        return grid
+    finally:
+        shm.close()
+
+
+def cpu_oracle_parallel(pairs: np.ndarray, workers: int):
+    """The oracle with the window split over `workers` processes: each
+    builds a grid from its part (Algorithm 1), the grids are OR-merged (the
+    grid of the union stream) and the oracle closes the window.  Returns
+    (pairs/s, seconds)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import oracle as O
+    O.build()
+    w = T.WORKLOADS[WORKLOAD]
+    seed = T.window_seed(2)
+    n = len(pairs)
+    shm = shared_memory.SharedMemory(create=True, size=pairs.nbytes)
+    try:
+        np.ndarray(pairs.shape, dtype=np.uint32, buffer=shm.buf)[:] = pairs
+        bounds = np.linspace(0, n, workers + 1).astype(np.int64)
+        jobs = [(shm.name, n, int(bounds[i]), int(bounds[i + 1]), w.sketch(), seed) for i in range(workers)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_oracle_part, [(shm.name, n, 0, 1, w.sketch(), seed)] * workers)  # start the workers
+            t0 = time.perf_counter()
+            grids = pool.map(_oracle_part, jobs)
+            grid = grids[0]
+            for g in grids[1:]:
+                grid |= g
+            O.close_window(O.params_from(w.sketch(), seed=seed), grid)
+            dt = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    return n / dt, dt
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -331,6 +380,11 @@ def run_ours(args, rank, world, local):
         cpu = {"value": r / 1e9, "unit": "Gpps", "cores": 1, "kind": "oracle",
                "sample": f"first {args.cpu_sample} pairs of the window: oracle update + close "
                          f"({dt:.1f} s, single thread)"}
+        workers = os.cpu_count() or 1
+        rp, dtp = cpu_oracle_parallel(win.pairs, workers)
+        cpu["parallel"] = {"value": rp / 1e9, "unit": "Gpps", "cores": workers,
+                           "sample": f"the whole window split over {workers} processes, one grid each, "
+                                     f"OR-merged, then the oracle's close ({dtp:.1f} s)"}
     line = {
         "metric": "packets/s (Gpps)", "value": value, "unit": "Gpps", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,

@@ -75,7 +75,7 @@ typedef struct {
     uint64_t cand_cap;    /* capacity for the candidate set K per direction;
                              default 2^20 */
     uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
-    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^24 */
+    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^22 */
     void *cuda_stream;    /* cudaStream_t for all device work, or NULL for a
                              handle-owned stream */
 } sd_params;
@@ -171,9 +171,14 @@ int sd_create(const sd_params *p, sd_handle **out);
  * interleaved (2n words), 4-byte aligned.  A device pointer is read in
  * place and the call returns once the work is queued: the buffer must stay
  * valid until the stream has executed it (sd_sync, or any later blocking
- * call on the handle).  A host pointer (pinned or pageable) is copied in
- * chunks of stage_pairs through the handle's staging buffers, and the call
- * returns once the caller's buffer may be reused.  n = 0 is a no-op. */
+ * call on the handle).  A pinned host pointer is copied in chunks of
+ * stage_pairs through the handle's device staging buffers, each chunk's
+ * kernels overlapping the next chunk's copy.  A pageable host pointer is
+ * read by the kernels in place when the device can access pageable memory
+ * (cudaDevAttrPageableMemoryAccess, e.g. over a coherent CPU-GPU link), else
+ * it is copied through pinned staging buffers as well.  For host pointers
+ * the call returns once the caller's buffer may be reused.  n = 0 is a
+ * no-op. */
 int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n);
 
 /* Close the window (Algorithm 2 with the §4.2 estimation step): per

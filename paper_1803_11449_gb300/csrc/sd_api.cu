@@ -142,6 +142,7 @@ struct sd_handle {
     Geometry G{};
     Tuning T{};
     int num_sms = 0;
+    int pageable_access = 0;  // kernels may read pageable host memory in place
     int zhot = -1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -286,7 +287,7 @@ static void resolve_caps(const sd_params *p, uint64_t *pair_cap, uint64_t *cand_
     *cand_cap = p->cand_cap ? p->cand_cap : (1ull << 20);
     *hits_cap = next_pow2(*cand_cap);
     *report_cap = p->report_cap ? p->report_cap : (uint64_t)p->dirs * *cand_cap;
-    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 24);
+    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 22);
 }
 
 uint64_t sd_device_bytes(const sd_params *p) {
@@ -356,6 +357,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
 
     SD_CK(h, cudaSetDevice(p->device));
     SD_CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    SD_CK(h, cudaDeviceGetAttribute(&h->pageable_access, cudaDevAttrPageableMemoryAccess, p->device));
     if (p->cuda_stream) {
         h->stream = (cudaStream_t)p->cuda_stream;
     } else {
@@ -520,8 +522,17 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
         h->n_pairs += n;
         return SD_OK;
     }
-    // host memory: chunked, double-buffered H2D overlapped with the kernel
     const bool pinned = attr.type == cudaMemoryTypeHost;
+    if (!pinned && h->pageable_access) {
+        // pageable memory the GPU reads in place (coherent link): no staging;
+        // the caller may reuse the buffer once the kernels are done
+        const int rc = update_device(h, pairs, n);
+        if (rc != SD_OK) return rc;
+        SD_CK(h, cudaStreamSynchronize(h->stream));
+        h->n_pairs += n;
+        return SD_OK;
+    }
+    // host memory: chunked, double-buffered H2D overlapped with the kernel
     const int rc = ensure_staging(h);
     if (rc != SD_OK) return rc;
     uint64_t c = 0;
@@ -571,6 +582,7 @@ static bool batch_layout(const sd_handle *h, BatchLayout *L) {
     const uint64_t upd = (uint64_t)h->p.dirs * h->p.r;
     const uint64_t cap_mean = (chunk * upd + L->S_link - 1) / L->S_link;
     L->cap_link = ((cap_mean + cap_mean * h->T.bin_slack_pct / 100 + 256) + 3) & ~3ull;
+    if (L->cap_link > 0xFFFFFFFFull) return false;  // BinArgs.cap is 32-bit
     const uint64_t by_mem = kBatchBinBytes / std::max<uint64_t>(1, (uint64_t)L->S_link * L->cap_link * 4);
     L->per_group = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4096u / L->S_link, by_mem));
     return true;
@@ -583,7 +595,7 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return 0;
     if (links <= 1) return words * 4;
     BatchLayout L;
-    batch_layout(h, &L);
+    if (!batch_layout(h, &L)) return words * 4;
     const uint64_t m = std::min<uint64_t>(links, L.per_group);
     const uint64_t S = m * L.S_link;
     return std::max<uint64_t>(words, S * L.cap_link + S + 4) * 4;
