@@ -141,6 +141,8 @@ typedef struct {
                                    direction SD_FLAG_OVERLOAD_CANDS, and a first
                                    stage above pair_cap tuples SD_FLAG_OVERLOAD_PAIRS.
                                 Both give the same K and the same report. */
+    uint32_t bin_batch_mib;  /* mode 5, sd_update_many: MiB of bins one batched round
+                                may use (bounds the links per round); default 8192 */
 } sd_tuning;
 
 /* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,

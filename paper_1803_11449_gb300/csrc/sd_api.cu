@@ -165,6 +165,13 @@ struct sd_handle {
     bool have_close = false;
     CloseState cs{};
 
+    // batched close (sd_close_many) driven by this handle: the jobs, and
+    // every job's StatBlock and first hit keys gathered for one copy back
+    CloseJob *cj_d = nullptr, *cj_h = nullptr;  // cj_h pinned
+    StatBlock *cb_st_d = nullptr, *cb_st_h = nullptr;
+    unsigned long long *cb_hits_d = nullptr, *cb_hits_h = nullptr;
+    uint32_t cj_cap = 0;
+
     // staged join (tuning restore = 1): all hot lists and the two
     // intermediate buffers, allocated on first use
     uint32_t *he_all = nullptr;
@@ -313,6 +320,12 @@ static void release(sd_handle *h) {
     cudaFree(h->bin_mem);
     cudaFree(h->he_all);
     cudaFree(h->jsub);
+    cudaFree(h->cj_d);
+    cudaFreeHost(h->cj_h);
+    cudaFree(h->cb_st_d);
+    cudaFreeHost(h->cb_st_h);
+    cudaFree(h->cb_hits_d);
+    cudaFreeHost(h->cb_hits_h);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     cudaFreeHost(h->big_h);
@@ -351,7 +364,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         G.h[d].A0inv = inverse_odd(G.h[d].A0);
     }
     // binned update, 128 KiB slices, 1024-pair tiles, 2^24-pair rounds (autotuned on GB300)
-    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0};
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192};
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -565,14 +578,14 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
 // member DHLA, slice size, bin capacity per slice, members per round.  A
 // round gives every member a full binning round of pairs (each member's
 // apply sweeps its whole DHLA once per round, so smaller shares would
-// multiply that sweep); a round is bounded by 4096 slices and by
-// kBatchBinBytes of bins.  False when h does not bin.
+// multiply that sweep); a round is bounded by 4096 slices and by the
+// tuning's bin_batch_mib of bins.  False when h does not bin.
 struct BatchLayout {
     uint32_t S_link, sl, per_group;
     uint64_t cap_link;
 };
 static bool batch_layout(const sd_handle *h, BatchLayout *L) {
-    constexpr uint64_t kBatchBinBytes = 8ull << 30;
+    const uint64_t kBatchBinBytes = (uint64_t)h->T.bin_batch_mib << 20;
     BinArgs B;
     uint64_t words = 0;
     if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return false;
@@ -753,9 +766,10 @@ struct CloseTrace {
         ph[i] += std::chrono::duration<double, std::micro>(now - last).count();
         last = now;
     }
+    const char *what = "sd_close_window";
     ~CloseTrace() {
         if (on)
-            std::fprintf(stderr, "sd_close_window us: stats %.1f restore %.1f bigsort %.1f report+reset %.1f total %.1f\n",
+            std::fprintf(stderr, "%s us: stats %.1f restore %.1f bigsort %.1f report+reset %.1f total %.1f\n", what,
                          ph[0], ph[1], ph[2], ph[3],
                          std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count());
     }
@@ -782,7 +796,9 @@ static int close_phase_a(sd_handle *h, sd_report *out) {
     return SD_OK;
 }
 
-static int close_phase_b(sd_handle *h, sd_report *out) {
+// Host part of phase B: psi, szmax and the work caps per direction, from the
+// row statistics in h->st_h; fills h->cs.A.  False when no direction runs.
+static bool close_decide(sd_handle *h, sd_report *out) {
     const Geometry &G = h->G;
     CloseState &c = h->cs;
     RestoreArgs &A = c.A;
@@ -811,7 +827,6 @@ static int close_phase_b(sd_handle *h, sd_report *out) {
         A.n1[d] = (uint32_t)n1;
         A.szmax[d] = szmax;
     }
-    if (!(A.run[0] || A.run[1])) return SD_OK;
     A.grid = h->grid;
     A.he = h->he;
     A.hotmap = h->hotmap;
@@ -820,6 +835,13 @@ static int close_phase_b(sd_handle *h, sd_report *out) {
     A.stats = h->st_d;
     A.cand_cap = h->cand_cap;
     A.hits_cap = h->hits_cap;
+    return A.run[0] || A.run[1];
+}
+
+static int close_phase_b(sd_handle *h, sd_report *out) {
+    if (!close_decide(h, out)) return SD_OK;
+    const Geometry &G = h->G;
+    RestoreArgs &A = h->cs.A;
     if (h->T.restore == 1) {
         if (!h->jsub) {
             h->join_cap = 4 * h->cand_cap;
@@ -892,7 +914,7 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
     return SD_OK;
 }
 
-static int close_phase_d(sd_handle *h, sd_report *out) {
+static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
     const Geometry &G = h->G;
     CloseState &c = h->cs;
     for (uint32_t d = 0; d < G.dirs; d++) {
@@ -921,9 +943,12 @@ static int close_phase_d(sd_handle *h, sd_report *out) {
         }
     }
     h->have_close = true;
-    // clear the DHLA and the counters for the next window (stream-ordered)
-    SD_CK(h, launch_reset(h->grid, (uint64_t)G.dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
-    launched(1);
+    // clear the DHLA and the counters for the next window (stream-ordered;
+    // a batched close clears all its handles in one launch instead)
+    if (reset) {
+        SD_CK(h, launch_reset(h->grid, (uint64_t)G.dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
+        launched(1);
+    }
 
     uint32_t flags = c.flags;
     out->n_hits_total = h->report.size();
@@ -972,6 +997,142 @@ int sd_close_window(sd_handle *h, sd_report *out) {
     return rc;
 }
 
+// sd_close_many for handles of one DHLA shape on one device that use the
+// default restore: every phase is one launch (or a few) over all the
+// handles, on hs[0]'s stream, with one host synchronisation per phase; the
+// host decisions per handle are the same functions as for one window.
+static bool batchable(sd_handle *const *hs, uint32_t count) {
+    if (count < 2) return false;
+    const sd_params &P = hs[0]->p;
+    for (uint32_t i = 0; i < count; i++) {
+        const sd_handle *h = hs[i];
+        if (h->p.device != P.device || h->p.g != P.g || h->p.r != P.r || h->p.k != P.k ||
+            h->p.alpha != P.alpha || h->p.dirs != P.dirs || h->T.restore != 0)
+            return false;
+    }
+    return true;
+}
+
+static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rcs) {
+    CloseTrace tr;
+    tr.what = "sd_close_many (batched)";
+    sd_handle *d = hs[0];
+    DeviceGuard dg(d->p.device);
+    const Geometry &G = d->G;
+    cudaStream_t s = d->stream;
+    if (d->cj_cap < count) {
+        SD_CK(d, cudaStreamSynchronize(s));
+        cudaFree(d->cj_d);
+        cudaFreeHost(d->cj_h);
+        cudaFree(d->cb_st_d);
+        cudaFreeHost(d->cb_st_h);
+        cudaFree(d->cb_hits_d);
+        cudaFreeHost(d->cb_hits_h);
+        d->cj_d = d->cj_h = nullptr;
+        d->cb_st_d = d->cb_st_h = nullptr;
+        d->cb_hits_d = d->cb_hits_h = nullptr;
+        d->cj_cap = 0;
+        SD_CK(d, cudaMalloc(&d->cj_d, count * sizeof(CloseJob)));
+        SD_CK(d, cudaMallocHost(&d->cj_h, count * sizeof(CloseJob)));
+        SD_CK(d, cudaMalloc(&d->cb_st_d, count * sizeof(StatBlock)));
+        SD_CK(d, cudaMallocHost(&d->cb_st_h, count * sizeof(StatBlock)));
+        SD_CK(d, cudaMalloc(&d->cb_hits_d, (uint64_t)count * 2 * kSortSmall * 8));
+        SD_CK(d, cudaMallocHost(&d->cb_hits_h, (uint64_t)count * 2 * kSortSmall * 8));
+        d->cj_cap = count;
+    }
+    // every member's queued work comes first, on the driver's stream
+    for (uint32_t i = 1; i < count; i++) {
+        sd_handle *h = hs[i];
+        if (h->stream == s) continue;
+        SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
+        SD_CK(d, cudaStreamWaitEvent(s, h->ev_batch, 0));
+    }
+    // phase A: row statistics and HE(0), HE(1) of every window
+    for (uint32_t i = 0; i < count; i++) {
+        sd_handle *h = hs[i];
+        std::memset(&outs[i], 0, sizeof outs[i]);
+        std::memset(&h->cs, 0, sizeof h->cs);
+        h->report.clear();
+        h->last_ncand[0] = h->last_ncand[1] = 0;
+        CloseJob &j = d->cj_h[i];
+        std::memset(&j, 0, sizeof j);
+        j.G = h->G;
+        j.A.grid = h->grid;
+        j.A.he = h->he;
+        j.A.hotmap = h->hotmap;
+        j.A.stats = h->st_d;
+        j.zhot = h->zhot;
+        rcs[i] = SD_OK;
+    }
+    SD_CK(d, cudaMemcpyAsync(d->cj_d, d->cj_h, count * sizeof(CloseJob), cudaMemcpyHostToDevice, s));
+    SD_CK(d, launch_stats_many(d->cj_d, count, G, d->num_sms, s));
+    SD_CK(d, launch_gather_many(d->cj_d, count, d->cb_st_d, d->cb_hits_d, s));
+    launched(3);
+    SD_CK(d, cudaMemcpyAsync(d->cb_st_h, d->cb_st_d, count * sizeof(StatBlock), cudaMemcpyDeviceToHost, s));
+    SD_CK(d, cudaStreamSynchronize(s));
+    tr.mark(0);
+    // phase B: host decisions per window, then restore, estimate and the
+    // small sorts of all of them
+    bool any = false;
+    for (uint32_t i = 0; i < count; i++) {
+        sd_handle *h = hs[i];
+        *h->st_h = d->cb_st_h[i];
+        const bool run = close_decide(h, &outs[i]);
+        CloseJob &j = d->cj_h[i];
+        j.A = h->cs.A;
+        if (run) prepare_restore(G, j.A, d->num_sms);
+        h->cs.A = j.A;
+        any = any || run;
+    }
+    if (any) {
+        SD_CK(d, cudaMemcpyAsync(d->cj_d, d->cj_h, count * sizeof(CloseJob), cudaMemcpyHostToDevice, s));
+        int nl = 0;
+        SD_CK(d, launch_restore_many(d->cj_d, d->cj_h, count, d->num_sms, s, &nl));
+        SD_CK(d, launch_gather_many(d->cj_d, count, d->cb_st_d, d->cb_hits_d, s));
+        launched(nl + 1);
+        SD_CK(d, cudaMemcpyAsync(d->cb_st_h, d->cb_st_d, count * sizeof(StatBlock), cudaMemcpyDeviceToHost, s));
+        SD_CK(d, cudaMemcpyAsync(d->cb_hits_h, d->cb_hits_d, (uint64_t)count * 2 * kSortSmall * 8,
+                                 cudaMemcpyDeviceToHost, s));
+        SD_CK(d, cudaStreamSynchronize(s));
+    }
+    tr.mark(1);
+    // phase C: caps, and the rare hit lists too long for one block's sort
+    std::vector<char> big(count, 0);
+    bool any_big = false;
+    for (uint32_t i = 0; i < count; i++) {
+        sd_handle *h = hs[i];
+        if (!any) continue;
+        *h->st_h = d->cb_st_h[i];
+        bool b = false;
+        rcs[i] = close_phase_c(h, &outs[i], &b);
+        for (uint32_t dd = 0; dd < G.dirs; dd++)
+            if (h->cs.keys[dd] == h->hits_h + (uint64_t)dd * kSortSmall)
+                h->cs.keys[dd] = d->cb_hits_h + ((uint64_t)i * 2 + dd) * kSortSmall;
+        big[i] = b;
+        any_big = any_big || b;
+    }
+    if (any_big)
+        for (uint32_t i = 0; i < count; i++)
+            if (big[i]) SD_CK(hs[i], cudaStreamSynchronize(hs[i]->stream));
+    tr.mark(2);
+    // phase D: the reports, then one reset of every DHLA
+    for (uint32_t i = 0; i < count; i++)
+        if (rcs[i] == SD_OK) rcs[i] = close_phase_d(hs[i], &outs[i], false);
+    SD_CK(d, launch_reset_many(d->cj_d, count, G, d->num_sms, s));
+    launched(1);
+    tr.mark(3);
+    // each member's later work waits for the batch
+    SD_CK(d, cudaEventRecord(d->ev_batch, s));
+    for (uint32_t i = 1; i < count; i++) {
+        sd_handle *h = hs[i];
+        if (h->stream == s) continue;
+        SD_CK(h, cudaStreamWaitEvent(h->stream, d->ev_batch, 0));
+    }
+    for (uint32_t i = 0; i < count; i++)
+        if (rc_is_error(rcs[i])) return rcs[i];
+    return SD_OK;
+}
+
 int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rcs) {
     if (!hs || !outs || !rcs) return count ? SD_ERR_ARG : SD_OK;
     for (uint32_t i = 0; i < count; i++)
@@ -981,6 +1142,7 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
         std::sort(sorted.begin(), sorted.end());
         if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return SD_ERR_ARG;
     }
+    if (batchable(hs, count)) return close_many_batched(hs, count, outs, rcs);
     // Each handle's close runs on its side stream (ordered after everything
     // queued on its stream so far, and its stream waits for the close), so
     // the closes of handles that share one stream still overlap on the GPU.
@@ -1146,6 +1308,7 @@ int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     out->bin_chunk_log2 = h->T.bin_chunk_log2;
     out->bin_slack_pct = h->T.bin_slack_pct;
     out->restore = h->T.restore;
+    out->bin_batch_mib = h->T.bin_batch_mib;
     return SD_OK;
 }
 
@@ -1190,6 +1353,11 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
         T.bin_chunk_log2 = t->bin_chunk_log2;
     }
     if (t->bin_slack_pct) T.bin_slack_pct = t->bin_slack_pct == 0xFFFFFFFFu ? 0u : t->bin_slack_pct;
+    if (t->bin_batch_mib) {
+        if (t->bin_batch_mib > (1u << 20))
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_batch_mib must be at most 2^20");
+        T.bin_batch_mib = t->bin_batch_mib;
+    }
     if (T.mode == 5) {
         // the binning tile must fit one block's shared memory
         const uint64_t total = (uint64_t)h->G.dirs * h->G.dir_words;

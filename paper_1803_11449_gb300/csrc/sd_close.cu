@@ -30,6 +30,8 @@
 // is kept when DH_i(a) is hot for i = 2..r-1: exactly K.  The work is
 // |HE(0)|*|HE(1)|*2^max(0,32-2k) cheap integer tests instead of a join whose
 // intermediate lists grow with |HE|^3.
+#include <algorithm>
+
 #include "sd_common.cuh"
 
 namespace sd {
@@ -43,9 +45,9 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 // ------------------------------------------------------------- row stats
 // One thread per estimator; a warp covers 32 consecutive estimators of one
 // row (2^k >= 32 because (r-1)k >= (r-2)alpha + k >= 32 with r <= 8).
-__global__ void __launch_bounds__(256)
-k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *__restrict__ hotmap,
-            StatBlock *__restrict__ st) {
+__device__ __forceinline__ void row_stats_body(const uint32_t *__restrict__ grid, const Geometry &G, int zhot,
+                                               uint32_t *__restrict__ hotmap, StatBlock *__restrict__ st,
+                                               uint32_t bx, uint32_t nbx) {
     __shared__ unsigned long long s_zr[2 * kMaxRows];
     __shared__ unsigned s_nhot[2 * kMaxRows];
     if (threadIdx.x < 2 * kMaxRows) {
@@ -54,9 +56,9 @@ k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *_
     }
     __syncthreads();
     const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = (uint64_t)nbx * blockDim.x;
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ncell; q += stride) {
+    for (uint64_t q = (uint64_t)bx * blockDim.x + threadIdx.x; q < ncell; q += stride) {
         const uint32_t *cell = grid + q * G.wpc;
         uint32_t pop = 0;
         if ((G.wpc & 3u) == 0) {
@@ -87,11 +89,17 @@ k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *_
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_row_stats(const uint32_t *__restrict__ grid, Geometry G, int zhot, uint32_t *__restrict__ hotmap,
+            StatBlock *__restrict__ st) {
+    row_stats_body(grid, G, zhot, hotmap, st, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------- compact
 // One block per (dir, row in {0, 1}): HE(row) in ascending order.
-__global__ void __launch_bounds__(1024)
-k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict__ he, uint32_t rows) {
-    const uint32_t dir = blockIdx.x / rows, row = blockIdx.x % rows;
+__device__ __forceinline__ void compact_body(const uint32_t *__restrict__ hotmap, const Geometry &G,
+                                             uint32_t *__restrict__ he, uint32_t rows, uint32_t bx) {
+    const uint32_t dir = bx / rows, row = bx % rows;
     const uint32_t nw = (1u << G.k) >> 5;
     const uint32_t *bm = hotmap + ((uint64_t)dir * G.r + row) * nw;
     uint32_t *out = he + ((uint64_t)dir * rows + row) * (1ull << G.k);
@@ -133,6 +141,11 @@ k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(1024)
+k_compact(const uint32_t *__restrict__ hotmap, Geometry G, uint32_t *__restrict__ he, uint32_t rows) {
+    compact_body(hotmap, G, he, rows, blockIdx.x);
+}
+
 // ---------------------------------------------------------------- restore
 __device__ __forceinline__ bool hot_at(const uint32_t *bm_row, uint32_t c) {
     return (bm_row[c >> 5] >> (c & 31u)) & 1u;
@@ -170,14 +183,13 @@ __device__ __forceinline__ void flush_hits(const RestoreArgs &A, uint32_t dir, u
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256)
-k_restore(Geometry G, RestoreArgs A) {
+__device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArgs &A, uint32_t bx, uint32_t nbx,
+                                             uint32_t dir) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_cbuf[8][kWarpBuf];
     __shared__ uint32_t s_c0[kRestoreTileMax];
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
-    const uint32_t dir = blockIdx.y;
     if (!(dir ? A.run[1] : A.run[0])) return;
     const uint32_t n0 = dir ? A.n0[1] : A.n0[0];
     const uint32_t n1 = dir ? A.n1[1] : A.n1[0];
@@ -213,7 +225,7 @@ k_restore(Geometry G, RestoreArgs A) {
     const uint32_t lowmask = (1u << lowbits) - 1u;
     const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
 
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (uint64_t t = bx; t < ntiles; t += nbx) {
         const uint32_t t0 = (uint32_t)(t / nchunk);
         const uint64_t jc = t % nchunk;
         const uint32_t c0_base = t0 * A.tile0;
@@ -258,14 +270,18 @@ k_restore(Geometry G, RestoreArgs A) {
     flush_cands(A, dir, cbuf, ccount, lane, overloaded);
 }
 
+__global__ void __launch_bounds__(256)
+k_restore(Geometry G, RestoreArgs A) {
+    restore_body(G, A, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
 // k_estimate: SZ(a) = zero bits of ULE(a), the AND of a's r estimators, for
 // every candidate in K (one warp per candidate, lanes over the estimator's
 // words); keeps (a, SZ) when SZ <= szmax.  A direction whose K overflowed its
 // capacity is skipped (it reports nothing).
-__global__ void __launch_bounds__(256)
-k_estimate(Geometry G, RestoreArgs A) {
+__device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreArgs &A, uint32_t bx, uint32_t nbx,
+                                              uint32_t dir) {
     __shared__ unsigned long long s_hbuf[8][kWarpBuf];
-    const uint32_t dir = blockIdx.y;
     if (!(dir ? A.run[1] : A.run[0])) return;
     const unsigned long long nk = A.stats->ncand[dir];
     if (nk > A.cand_cap) return;
@@ -276,8 +292,8 @@ k_estimate(Geometry G, RestoreArgs A) {
     uint32_t hcount = 0;
     const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
     const uint32_t *cand = A.cand + (uint64_t)dir * A.cand_cap;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nk; q += nwarps) {
+    const uint64_t nwarps = (uint64_t)nbx * (blockDim.x >> 5);
+    for (uint64_t q = (uint64_t)bx * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nk; q += nwarps) {
         const uint32_t x = cand[q];
         const uint32_t c0 = dh0(A0, G.k, x);
         uint32_t ones = 0;
@@ -300,6 +316,11 @@ k_estimate(Geometry G, RestoreArgs A) {
     }
     __syncwarp();
     flush_hits(A, dir, hbuf, hcount, lane);
+}
+
+__global__ void __launch_bounds__(256)
+k_estimate(Geometry G, RestoreArgs A) {
+    estimate_body(G, A, blockIdx.x, gridDim.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------- sort
@@ -327,11 +348,9 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *s, unsigned P) 
 
 // One block per direction: bitonic sort of up to kSortSmall hits in shared
 // memory (padding with all-ones keys, which sort last).
-__global__ void __launch_bounds__(1024)
-k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 run) {
+__device__ __forceinline__ void sort_small_body(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
+                                                uint32_t dir) {
     extern __shared__ unsigned long long s[];  // kSortSmall keys
-    const uint32_t dir = blockIdx.x;
-    if (!(dir ? run.y : run.x)) return;
     const unsigned long long n = st->nhits[dir];
     const unsigned long long nn = n < hits_cap ? n : hits_cap;
     if (nn > (unsigned long long)kSortSmall) {
@@ -346,6 +365,13 @@ k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 r
     __syncthreads();
     bitonic_smem(s, P);
     for (unsigned i = threadIdx.x; i < nn; i += blockDim.x) hd[i] = s[i];
+}
+
+__global__ void __launch_bounds__(1024)
+k_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st, uint2 run) {
+    const uint32_t dir = blockIdx.x;
+    if (!(dir ? run.y : run.x)) return;
+    sort_small_body(hits, hits_cap, st, dir);
 }
 
 // Sort every segment keys[j*kSortSmall, (j+1)*kSortSmall) of keys[0, n) in
@@ -396,15 +422,17 @@ __global__ void k_merge_rank(const unsigned long long *__restrict__ src, unsigne
 }
 
 // ------------------------------------------------------------ reset/merge
-__global__ void k_reset(uint4 *grid4, uint64_t n4, StatBlock *st) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+__device__ __forceinline__ void reset_body(uint4 *grid4, uint64_t n4, StatBlock *st, uint32_t bx, uint32_t nbx) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x;
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < n4; i += stride)
         grid4[i] = make_uint4(0, 0, 0, 0);
-    if (blockIdx.x == 0) {
+    if (bx == 0) {
         uint32_t *w = reinterpret_cast<uint32_t *>(st);
         for (uint32_t i = threadIdx.x; i < sizeof(StatBlock) / 4; i += blockDim.x) w[i] = 0;
     }
 }
+
+__global__ void k_reset(uint4 *grid4, uint64_t n4, StatBlock *st) { reset_body(grid4, n4, st, blockIdx.x, gridDim.x); }
 
 __global__ void k_merge_or(uint4 *dst, const uint4 *__restrict__ src, uint64_t n4) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -412,6 +440,59 @@ __global__ void k_merge_or(uint4 *dst, const uint4 *__restrict__ src, uint64_t n
         const uint4 a = dst[i], b = __ldg(src + i);
         dst[i] = make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
     }
+}
+
+// ------------------------------------------------------- batched closes
+// The same kernels over an array of jobs, one grid dimension per job.
+__global__ void __launch_bounds__(256) k_row_stats_many(const CloseJob *__restrict__ J) {
+    const CloseJob &j = J[blockIdx.y];
+    row_stats_body(j.A.grid, j.G, j.zhot, const_cast<uint32_t *>(j.A.hotmap), j.A.stats, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(1024) k_compact_many(const CloseJob *__restrict__ J) {
+    const CloseJob &j = J[blockIdx.y];
+    compact_body(j.A.hotmap, j.G, const_cast<uint32_t *>(j.A.he), 2, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_restore_many(const CloseJob *__restrict__ J) {
+    const CloseJob &j = J[blockIdx.z];
+    restore_body(j.G, j.A, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) k_estimate_many(const CloseJob *__restrict__ J) {
+    const CloseJob &j = J[blockIdx.z];
+    estimate_body(j.G, j.A, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_small_many(const CloseJob *__restrict__ J) {
+    const CloseJob &j = J[blockIdx.y];
+    const uint32_t dir = blockIdx.x;
+    if (!(dir ? j.A.run[1] : j.A.run[0])) return;
+    sort_small_body(j.A.hits, j.A.hits_cap, j.A.stats, dir);
+}
+
+// Every job's StatBlock, and the first min(hits, kSortSmall) hit keys of
+// each direction, into contiguous buffers (one copy to the host for all).
+__global__ void __launch_bounds__(256)
+k_gather_many(const CloseJob *__restrict__ J, StatBlock *__restrict__ st_out, unsigned long long *__restrict__ hits_out) {
+    const CloseJob &j = J[blockIdx.x];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(j.A.stats);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(st_out + blockIdx.x);
+    for (uint32_t i = threadIdx.x; i < sizeof(StatBlock) / 4; i += blockDim.x) dst[i] = src[i];
+    for (uint32_t d = 0; d < j.G.dirs; d++) {
+        if (!(d ? j.A.run[1] : j.A.run[0])) continue;
+        const unsigned long long n = j.A.stats->nhits[d];
+        uint64_t m = n < j.A.hits_cap ? n : j.A.hits_cap;
+        if (m > (uint64_t)kSortSmall) m = kSortSmall;
+        const unsigned long long *h = j.A.hits + (uint64_t)d * j.A.hits_cap;
+        unsigned long long *o = hits_out + ((uint64_t)blockIdx.x * 2 + d) * kSortSmall;
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) o[i] = h[i];
+    }
+}
+
+__global__ void k_reset_many(const CloseJob *__restrict__ J, uint64_t n4) {
+    const CloseJob &j = J[blockIdx.y];
+    reset_body(reinterpret_cast<uint4 *>(const_cast<uint32_t *>(j.A.grid)), n4, j.A.stats, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -435,24 +516,23 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
     return cudaGetLastError();
 }
 
-cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
+// Tile shape of k_restore for A's sizes: preimages per (c0, c1), (c1, t)
+// items per tile, and c0 values per tile -- enough work per tile to amortise
+// its set-up while still giving every resident block about one tile.
+void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms) {
     const unsigned threads = 256;
     A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
     A.jchunk = threads;
-    // c0 values per tile: enough work per tile to amortise its set-up, while
-    // still giving every resident block about one tile
-    {
-        uint64_t tests = 0;
-        for (uint32_t d = 0; d < G.dirs; d++)
-            if (A.run[d]) tests += (uint64_t)A.n0[d] * ((uint64_t)A.n1[d] << A.ulog);
-        const uint64_t per_block = tests / ((uint64_t)num_sms * 8 * threads) + 1;
-        A.tile0 = (uint32_t)(per_block < kRestoreTileMax ? per_block : kRestoreTileMax);
-    }
+    uint64_t tests = 0;
+    for (uint32_t d = 0; d < G.dirs; d++)
+        if (A.run[d]) tests += (uint64_t)A.n0[d] * ((uint64_t)A.n1[d] << A.ulog);
+    const uint64_t per_block = tests / ((uint64_t)num_sms * 8 * threads) + 1;
+    A.tile0 = (uint32_t)(per_block < kRestoreTileMax ? per_block : kRestoreTileMax);
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
-    size_t smem = 16;
     A.smem_hot = hot_bytes <= (size_t)200 * 1024;
-    if (A.smem_hot) smem = hot_bytes;
+}
 
+static uint64_t restore_tiles(const Geometry &G, const RestoreArgs &A) {
     uint64_t most = 0;
     for (uint32_t d = 0; d < G.dirs; d++) {
         if (!A.run[d]) continue;
@@ -460,6 +540,15 @@ cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaSt
         const uint64_t nc = (((uint64_t)A.n1[d] << A.ulog) + A.jchunk - 1) / A.jchunk;
         if (t0 * nc > most) most = t0 * nc;
     }
+    return most;
+}
+
+cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
+    const unsigned threads = 256;
+    prepare_restore(G, A, num_sms);
+    const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
+    const size_t smem = A.smem_hot ? hot_bytes : 16;
+    const uint64_t most = restore_tiles(G, A);
     if (most == 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_restore), (int)threads, smem, &per_sm);
@@ -511,6 +600,72 @@ cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, u
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s) {
     const uint64_t n4 = words / 4;
     k_reset<<<grid_for(n4, 256, num_sms, 8), 256, 0, s>>>(reinterpret_cast<uint4 *>(grid), n4, st);
+    return cudaGetLastError();
+}
+
+// Batched launchers: the grid's first dimension is shared by all jobs (each
+// job strides over its own work with it), the job index is the last one.
+cudaError_t launch_stats_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s) {
+    const uint64_t ncell = (uint64_t)G.dirs * G.r << G.k;
+    const unsigned per_job = std::max(1u, grid_for(ncell, 256, num_sms, 8) / std::max(1u, count / 4));
+    k_row_stats_many<<<dim3(per_job, count), 256, 0, s>>>(J);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_compact_many<<<dim3(G.dirs * 2, count), 1024, 0, s>>>(J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, int num_sms, cudaStream_t s,
+                                int *launches) {
+    *launches = 0;
+    const Geometry &G = Jh[0].G;
+    const unsigned threads = 256;
+    const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
+    const size_t smem = Jh[0].A.smem_hot ? hot_bytes : 16;
+    uint64_t most = 0, total = 0;
+    bool any = false;
+    for (uint32_t i = 0; i < count; i++) {
+        const uint64_t t = restore_tiles(G, Jh[i].A);
+        most = std::max(most, t);
+        total += t;
+        any = any || Jh[i].A.run[0] || Jh[i].A.run[1];
+    }
+    if (!any) return cudaSuccess;
+    cudaError_t e;
+    if (most > 0) {
+        int per_sm = 0;
+        e = prepare_launch(reinterpret_cast<const void *>(k_restore_many), (int)threads, smem, &per_sm);
+        if (e != cudaSuccess) return e;
+        // the jobs' tiles spread over the resident blocks in proportion
+        const uint64_t slots = (uint64_t)num_sms * per_sm;
+        uint64_t bx = total ? (most * slots + total - 1) / total : 1;
+        bx = std::max<uint64_t>(1, std::min<uint64_t>(bx, most));
+        k_restore_many<<<dim3((unsigned)bx, G.dirs, count), threads, smem, s>>>(J);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    }
+    const unsigned ebx = std::max(1u, (unsigned)num_sms * 4 / std::max(1u, count / 2));
+    k_estimate_many<<<dim3(ebx, G.dirs, count), 256, 0, s>>>(J);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int ssmem = kSortSmall * (int)sizeof(unsigned long long);
+    int per_sm = 0;
+    e = prepare_launch(reinterpret_cast<const void *>(k_sort_small_many), 1024, ssmem, &per_sm);
+    if (e != cudaSuccess) return e;
+    k_sort_small_many<<<dim3(G.dirs, count), 1024, ssmem, s>>>(J);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_many(const CloseJob *J, uint32_t count, StatBlock *st_out, unsigned long long *hits_out,
+                               cudaStream_t s) {
+    k_gather_many<<<count, 256, 0, s>>>(J, st_out, hits_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s) {
+    const uint64_t n4 = (uint64_t)G.dirs * G.dir_words / 4;
+    const unsigned per_job = std::max(1u, grid_for(n4, 256, num_sms, 8) / std::max(1u, count / 4));
+    k_reset_many<<<dim3(per_job, count), 256, 0, s>>>(J, n4);
     return cudaGetLastError();
 }
 

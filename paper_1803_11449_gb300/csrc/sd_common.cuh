@@ -40,6 +40,7 @@ struct Tuning {
     uint32_t bin_chunk_log2; // mode 5: pairs per bin/apply round = 2^bin_chunk_log2
     uint32_t bin_slack_pct;  // mode 5: bin capacity over the mean fill, in percent
     uint32_t restore;        // 0 DH_0 inversion (k_restore), 1 staged join (sd_join.cu)
+    uint32_t bin_batch_mib;  // mode 5, batched update: MiB of bins per round
 };
 
 // One link of a batched binned update (device memory table).
@@ -93,6 +94,18 @@ struct RestoreArgs {
     uint32_t tile0;          // c0 values per block tile
     uint32_t jchunk;         // (c1, t) items per block tile
     int smem_hot;            // rows 2..r-1 of the hot bitmap staged in shared memory
+};
+
+// One window close of a batch (sd_close_many over handles of one DHLA
+// shape): the handle's geometry (its hash constants), its restore arguments
+// (all its device buffers: A.grid, A.he, A.hotmap, A.cand, A.hits, A.stats)
+// and its hot threshold.  The batched close kernels take an array of these
+// in device memory and pick the link from a grid dimension.
+struct CloseJob {
+    Geometry G;
+    RestoreArgs A;
+    int zhot;
+    int pad;
 };
 
 // The staged join of sd_join.cu (the paper's Algorithms 3 and 4).
@@ -175,6 +188,18 @@ cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, 
 cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, uint32_t rows, cudaStream_t s);
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
 cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms, cudaStream_t s);
+// Batched close over `count` jobs (device array J; Jh is the host copy,
+// used for grid sizing): row stats + HE(0), HE(1) of every job; restore,
+// estimate and small sorts; a gather of every job's StatBlock and first
+// kSortSmall hits per direction into st_out[count] / hits_out[count][2]
+// [kSortSmall]; the reset of every job's DHLA and counters.
+cudaError_t launch_stats_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s);
+void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms);
+cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, int num_sms, cudaStream_t s,
+                                int *launches);
+cudaError_t launch_gather_many(const CloseJob *J, uint32_t count, StatBlock *st_out, unsigned long long *hits_out,
+                               cudaStream_t s);
+cudaError_t launch_reset_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s);
 // K by the staged join: r-2 launches (rows 2..r-1), both directions each
 cudaError_t launch_join(const Geometry &G, const JoinArgs &J, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,

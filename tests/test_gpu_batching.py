@@ -95,3 +95,33 @@ def test_close_many_equals_close_window_on_core_links(sd, O):
         assert np.array_equal(a.hits, b.hits)
         _, ref = _oracle(O, w, win.pairs, s)
         _same_report(b, ref, 2)
+
+
+def test_close_many_mixed_shapes_and_restores(sd, O):
+    """Handles of different shapes, or with the staged-join restore, close
+    one by one inside sd_close_many; handles of one shape close in batched
+    launches.  Every report equals the oracle's."""
+    import torch
+    w1 = T.WORKLOADS["tiny"].with_(dirs=1)
+    w2 = T.WORKLOADS["tiny"].with_(dirs=2)
+    cases = [(w1, 31, 0), (w2, 32, 0), (w2, 33, 1), (w2, 34, 0)]
+    wins = [T.make_window(w.with_(n=1 << 18, planted=6), s) for w, s, _ in cases]
+    for group in (cases, [c for c in cases if c[0] is w2 and c[2] == 0]):
+        hs = [sd.sd_create(sd.params_for(w, s)) for w, s, _ in group]
+        try:
+            for h, (_, _, restore) in zip(hs, group):
+                sd.sd_set_tuning(h, mode=5, restore=restore)
+            for h, (w, s, _) in zip(hs, group):
+                win = wins[[c[1] for c in cases].index(s)]
+                sd.sd_update(h, _dev(win.pairs))
+            torch.cuda.synchronize()
+            reps = sd.sd_close_many(hs)
+            again = sd.sd_close_many(hs)  # empty windows after the close
+        finally:
+            for h in hs:
+                sd.sd_destroy(h)
+        for rep, r2, (w, s, _) in zip(reps, again, group):
+            win = wins[[c[1] for c in cases].index(s)]
+            _, ref = _oracle(O, w, win.pairs, s)
+            _same_report(rep, ref, w.dirs)
+            assert r2.n_pairs == 0 and len(r2.hits) == 0
