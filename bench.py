@@ -459,6 +459,10 @@ def run_batching(args, rank, world, local):
     hs = [sd.sd_create(sd.params_for(w, seed=seed, device=local, cuda_stream=stream.cuda_stream))
           for _ in wins]
     one = hs[0]
+    tuned = None
+    if args.autotune:
+        from paper_1803_11449_gb300.tune import autotune_many
+        tuned = autotune_many(hs, devs, stream, verbose=args.verbose)
 
     def one_at_a_time():
         lat = []
@@ -491,6 +495,7 @@ def run_batching(args, rank, world, local):
         lat_bat.append(batched())
         torch.cuda.synchronize()
         t_bat.append(time.perf_counter() - t0)
+    tuning = {f: getattr(sd.sd_get_tuning(one), f) for f, _ in sd.sd_tuning._fields_}
     for h in hs:
         sd.sd_destroy(h)
     one_v = dist_max(min(t_one), world)
@@ -504,7 +509,8 @@ def run_batching(args, rank, world, local):
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"batching: {args.links} links, window sizes lognormal (median 4M pairs, "
                                "clipped to [256K, 64M]), 50-300 planted each, core-link sketch per link",
-                   "pairs_per_step_per_gpu": total},
+                   "pairs_per_step_per_gpu": total,
+                   "tuning": tuning, "autotuned": tuned is not None},
         "one_window_at_a_time": {"value": world * total / one_v / 1e9, "unit": "Gpps",
                                  "ms_per_step": 1e3 * one_v,
                                  "close_ms_per_window": {"p50": 1e3 * float(np.percentile(lat_one, 50)),
@@ -697,7 +703,7 @@ def main():
     ap.add_argument("--serve-load", type=float, default=10.0, help="offered Gpps, all links")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-budget-gb", type=float, default=2.0)
-    ap.add_argument("--serve-chunk-log2", type=int, default=20)
+    ap.add_argument("--serve-chunk-log2", type=int, default=22)
     ap.add_argument("--serve-ddos", type=int, default=2_000_000)
     ap.add_argument("--serve-scan", type=int, default=500_000)
     args = ap.parse_args()

@@ -204,10 +204,11 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
  * handle i gets the ns[i] pairs at pairs[i], exactly as sd_update would give
  * it.  When hs[0] uses the binned update (tuning mode 5), every link whose
  * pairs are device-resident on hs[0]'s device and whose DHLA has hs[0]'s
- * shape (g, r, k, alpha, dirs) is binned with the others: in each round up
- * to 4096/(slices per DHLA) links (fewer when their bins would pass 8 GiB)
- * contribute up to 2^bin_chunk_log2 pairs each, with one bin launch and one
- * apply launch per round, on hs[0]'s stream and with hs[0]'s scratch
+ * shape (g, r, k, alpha, dirs) is binned with the others: each round takes
+ * links round-robin, each contributing up to 2^bin_chunk_log2 pairs, as
+ * many as hs[0]'s bin_batch_mib of bins holds at the round's largest share
+ * (and at most 4096 slices in all), with one bin launch and one apply
+ * launch per round, on hs[0]'s stream and with hs[0]'s scratch
  * (ordered after each member's earlier work, and each member's later work
  * after it).  The other links take sd_update.  Returns
  * the first error, if any. */
@@ -215,8 +216,9 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
 
 /* Device bytes of the binned update's scratch (bins and counters) that h
  * allocates, with its current tuning, when it updates alone (links <= 1)
- * or drives sd_update_many over `links` members; the scratch grows to the
- * largest such need and is kept until sd_destroy.  0 when h does not bin
+ * or drives sd_update_many over `links` members (at most about
+ * bin_batch_mib MiB then); the scratch grows to the largest such need and
+ * is kept until sd_destroy.  0 when h does not bin
  * (tuning mode other than 5, or a DHLA of more than 4096 slices) or h is
  * NULL.  For memory budgets: a handle holds sd_device_bytes plus this. */
 uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links);

@@ -170,6 +170,7 @@ struct sd_handle {
     CloseJob *cj_d = nullptr, *cj_h = nullptr;  // cj_h pinned
     StatBlock *cb_st_d = nullptr, *cb_st_h = nullptr;
     unsigned long long *cb_hits_d = nullptr, *cb_hits_h = nullptr;
+    unsigned long long *cb_base_d = nullptr, *cb_base_h = nullptr;  // tile and candidate offsets
     uint32_t cj_cap = 0;
 
     // staged join (tuning restore = 1): all hot lists and the two
@@ -326,6 +327,8 @@ static void release(sd_handle *h) {
     cudaFreeHost(h->cb_st_h);
     cudaFree(h->cb_hits_d);
     cudaFreeHost(h->cb_hits_h);
+    cudaFree(h->cb_base_d);
+    cudaFreeHost(h->cb_base_h);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     cudaFreeHost(h->big_h);
@@ -581,22 +584,28 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
 // multiply that sweep); a round is bounded by 4096 slices and by the
 // tuning's bin_batch_mib of bins.  False when h does not bin.
 struct BatchLayout {
-    uint32_t S_link, sl, per_group;
-    uint64_t cap_link;
+    uint32_t S_link, sl, per_group;  // per_group: members of a round of full chunks
+    uint64_t cap_link;               // bin capacity per slice for a full chunk
+    uint64_t bin_bytes;              // bins one round may use
+    uint64_t upd, slack;
+    // bin capacity per slice when the largest member share of a round is `take` pairs
+    uint64_t cap_for(uint64_t take) const {
+        const uint64_t mean = (take * upd + S_link - 1) / S_link;
+        return ((mean + mean * slack / 100 + 256) + 3) & ~3ull;
+    }
 };
 static bool batch_layout(const sd_handle *h, BatchLayout *L) {
-    const uint64_t kBatchBinBytes = (uint64_t)h->T.bin_batch_mib << 20;
     BinArgs B;
     uint64_t words = 0;
     if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return false;
     L->S_link = B.S;
     L->sl = B.slice_log2;
-    const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
-    const uint64_t upd = (uint64_t)h->p.dirs * h->p.r;
-    const uint64_t cap_mean = (chunk * upd + L->S_link - 1) / L->S_link;
-    L->cap_link = ((cap_mean + cap_mean * h->T.bin_slack_pct / 100 + 256) + 3) & ~3ull;
+    L->upd = (uint64_t)h->p.dirs * h->p.r;
+    L->slack = h->T.bin_slack_pct;
+    L->bin_bytes = (uint64_t)h->T.bin_batch_mib << 20;
+    L->cap_link = L->cap_for(1ull << h->T.bin_chunk_log2);
     if (L->cap_link > 0xFFFFFFFFull) return false;  // BinArgs.cap is 32-bit
-    const uint64_t by_mem = kBatchBinBytes / std::max<uint64_t>(1, (uint64_t)L->S_link * L->cap_link * 4);
+    const uint64_t by_mem = L->bin_bytes / std::max<uint64_t>(1, (uint64_t)L->S_link * L->cap_link * 4);
     L->per_group = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4096u / L->S_link, by_mem));
     return true;
 }
@@ -609,9 +618,12 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     if (links <= 1) return words * 4;
     BatchLayout L;
     if (!batch_layout(h, &L)) return words * 4;
-    const uint64_t m = std::min<uint64_t>(links, L.per_group);
+    // a round holds as many members as its bins allow at their actual
+    // shares, so the bins reach the byte bound whenever that bound binds
+    const uint64_t m = std::min<uint64_t>(links, 4096u / L.S_link);
     const uint64_t S = m * L.S_link;
-    return std::max<uint64_t>(words, S * L.cap_link + S + 4) * 4;
+    const uint64_t full = S * L.cap_link * 4;
+    return std::max<uint64_t>(words * 4, std::min<uint64_t>(full, std::max<uint64_t>(L.bin_bytes, (uint64_t)L.S_link * L.cap_link * 4)) + (S + 4) * 4);
 }
 
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count) {
@@ -622,10 +634,10 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     sd_handle *d = hs[0];
     DeviceGuard dg(d->p.device);
     const sd_params &P = d->p;
-    BatchLayout BL{0, 0, 1, 0};
+    BatchLayout BL{};
     const bool binnable = batch_layout(d, &BL);
-    const uint32_t S_link = BL.S_link, sl = BL.sl, per_group = BL.per_group;
-    const uint64_t cap_link = BL.cap_link;
+    const uint32_t S_link = BL.S_link, sl = BL.sl;
+    const uint32_t max_members = S_link ? 4096u / S_link : 1u;
     const uint64_t chunk = 1ull << d->T.bin_chunk_log2;
 
     // which links join the batch: device-resident pairs on hs[0]'s device,
@@ -659,7 +671,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     // the rounds' link tables live side by side in one buffer
     uint64_t rounds_upper = 1;
     for (uint32_t q : batch) rounds_upper += (ns[q] + chunk - 1) / chunk;
-    const uint64_t need = rounds_upper * per_group;
+    const uint64_t need = rounds_upper * std::min<uint64_t>(batch.size(), max_members);
     const int half = d->links_half ^ 1;
     if (d->links_cap < need) {
         SD_CK(d, cudaStreamSynchronize(d->stream));  // earlier batches may still read the tables
@@ -689,11 +701,20 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     std::vector<uint64_t> done(batch.size(), 0);
     size_t cursor = 0, tab_used = 0;
     for (;;) {
-        // up to per_group links with pairs left, round-robin
+        // the round's members, round-robin among links with pairs left: as
+        // many as the bins allow at the largest member share of the round
+        // (a share is up to one chunk), at most 4096 slices in all
         std::vector<uint32_t> mem;
-        for (size_t t = 0; t < batch.size() && mem.size() < per_group; t++) {
+        uint64_t max_take = 0;
+        for (size_t t = 0; t < batch.size() && mem.size() < max_members; t++) {
             const size_t q = (cursor + t) % batch.size();
-            if (done[q] < ns[batch[q]]) mem.push_back((uint32_t)q);
+            if (done[q] >= ns[batch[q]]) continue;
+            const uint64_t take = std::min(chunk, ns[batch[q]] - done[q]);
+            const uint64_t mt = std::max(max_take, take);
+            const uint64_t bytes = (uint64_t)(mem.size() + 1) * S_link * BL.cap_for(mt) * 4;
+            if (!mem.empty() && bytes > BL.bin_bytes) break;
+            mem.push_back((uint32_t)q);
+            max_take = mt;
         }
         if (mem.empty()) break;
         cursor = (mem.back() + 1) % batch.size();
@@ -725,7 +746,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         std::memset(&B, 0, sizeof B);
         B.S = (uint32_t)mem.size() * S_link;
         B.slice_log2 = sl;
-        B.cap = (uint32_t)cap_link;
+        B.cap = (uint32_t)BL.cap_for(max_take);
         B.tile_pairs = TP;
         B.total_words = (uint64_t)P.dirs * d->G.dir_words;  // words of one link's DHLA
         const int rc = ensure_bin_mem(d, B);
@@ -1028,9 +1049,12 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         cudaFreeHost(d->cb_st_h);
         cudaFree(d->cb_hits_d);
         cudaFreeHost(d->cb_hits_h);
+        cudaFree(d->cb_base_d);
+        cudaFreeHost(d->cb_base_h);
         d->cj_d = d->cj_h = nullptr;
         d->cb_st_d = d->cb_st_h = nullptr;
         d->cb_hits_d = d->cb_hits_h = nullptr;
+        d->cb_base_d = d->cb_base_h = nullptr;
         d->cj_cap = 0;
         SD_CK(d, cudaMalloc(&d->cj_d, count * sizeof(CloseJob)));
         SD_CK(d, cudaMallocHost(&d->cj_h, count * sizeof(CloseJob)));
@@ -1038,6 +1062,9 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         SD_CK(d, cudaMallocHost(&d->cb_st_h, count * sizeof(StatBlock)));
         SD_CK(d, cudaMalloc(&d->cb_hits_d, (uint64_t)count * 2 * kSortSmall * 8));
         SD_CK(d, cudaMallocHost(&d->cb_hits_h, (uint64_t)count * 2 * kSortSmall * 8));
+        // tile offsets (device + host) and candidate offsets (device), 2 count + 1 each
+        SD_CK(d, cudaMalloc(&d->cb_base_d, (uint64_t)2 * (2 * count + 1) * 8));
+        SD_CK(d, cudaMallocHost(&d->cb_base_h, (uint64_t)(2 * count + 1) * 8));
         d->cj_cap = count;
     }
     // every member's queued work comes first, on the driver's stream
@@ -1087,7 +1114,8 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
     if (any) {
         SD_CK(d, cudaMemcpyAsync(d->cj_d, d->cj_h, count * sizeof(CloseJob), cudaMemcpyHostToDevice, s));
         int nl = 0;
-        SD_CK(d, launch_restore_many(d->cj_d, d->cj_h, count, d->num_sms, s, &nl));
+        SD_CK(d, launch_restore_many(d->cj_d, d->cj_h, count, d->cb_base_d, d->cb_base_h,
+                                     d->cb_base_d + (2 * count + 1), d->num_sms, s, &nl));
         SD_CK(d, launch_gather_many(d->cj_d, count, d->cb_st_d, d->cb_hits_d, s));
         launched(nl + 1);
         SD_CK(d, cudaMemcpyAsync(d->cb_st_h, d->cb_st_d, count * sizeof(StatBlock), cudaMemcpyDeviceToHost, s));

@@ -183,11 +183,13 @@ __device__ __forceinline__ void flush_hits(const RestoreArgs &A, uint32_t dir, u
     __syncwarp();
 }
 
-__device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArgs &A, uint32_t bx, uint32_t nbx,
-                                             uint32_t dir) {
+// Tiles t_begin, t_begin + t_step, ... below t_end of direction `dir`.
+__device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArgs &A, uint32_t dir, uint64_t t_begin,
+                                             uint64_t t_end, uint64_t t_step) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_cbuf[8][kWarpBuf];
     __shared__ uint32_t s_c0[kRestoreTileMax];
+    __syncthreads();  // shared memory may still be in use by a previous call
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
     if (!(dir ? A.run[1] : A.run[0])) return;
@@ -225,7 +227,8 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     const uint32_t lowmask = (1u << lowbits) - 1u;
     const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
 
-    for (uint64_t t = bx; t < ntiles; t += nbx) {
+    const uint64_t t_stop = t_end < ntiles ? t_end : ntiles;
+    for (uint64_t t = t_begin; t < t_stop; t += t_step) {
         const uint32_t t0 = (uint32_t)(t / nchunk);
         const uint64_t jc = t % nchunk;
         const uint32_t c0_base = t0 * A.tile0;
@@ -272,15 +275,17 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
 
 __global__ void __launch_bounds__(256)
 k_restore(Geometry G, RestoreArgs A) {
-    restore_body(G, A, blockIdx.x, gridDim.x, blockIdx.y);
+    restore_body(G, A, blockIdx.y, blockIdx.x, ~0ull, gridDim.x);
 }
 
 // k_estimate: SZ(a) = zero bits of ULE(a), the AND of a's r estimators, for
 // every candidate in K (one warp per candidate, lanes over the estimator's
 // words); keeps (a, SZ) when SZ <= szmax.  A direction whose K overflowed its
 // capacity is skipped (it reports nothing).
-__device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreArgs &A, uint32_t bx, uint32_t nbx,
-                                              uint32_t dir) {
+// Candidates q_begin, q_begin + q_step, ... below q_end of direction `dir`,
+// one warp each.
+__device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreArgs &A, uint32_t dir, uint64_t q_begin,
+                                              uint64_t q_end, uint64_t q_step) {
     __shared__ unsigned long long s_hbuf[8][kWarpBuf];
     if (!(dir ? A.run[1] : A.run[0])) return;
     const unsigned long long nk = A.stats->ncand[dir];
@@ -292,8 +297,8 @@ __device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreAr
     uint32_t hcount = 0;
     const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
     const uint32_t *cand = A.cand + (uint64_t)dir * A.cand_cap;
-    const uint64_t nwarps = (uint64_t)nbx * (blockDim.x >> 5);
-    for (uint64_t q = (uint64_t)bx * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nk; q += nwarps) {
+    const uint64_t q_stop = q_end < nk ? q_end : nk;
+    for (uint64_t q = q_begin; q < q_stop; q += q_step) {
         const uint32_t x = cand[q];
         const uint32_t c0 = dh0(A0, G.k, x);
         uint32_t ones = 0;
@@ -320,7 +325,8 @@ __device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreAr
 
 __global__ void __launch_bounds__(256)
 k_estimate(Geometry G, RestoreArgs A) {
-    estimate_body(G, A, blockIdx.x, gridDim.x, blockIdx.y);
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    estimate_body(G, A, blockIdx.y, (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), ~0ull, nwarps);
 }
 
 // ------------------------------------------------------------------- sort
@@ -454,14 +460,69 @@ __global__ void __launch_bounds__(1024) k_compact_many(const CloseJob *__restric
     compact_body(j.A.hotmap, j.G, const_cast<uint32_t *>(j.A.he), 2, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) k_restore_many(const CloseJob *__restrict__ J) {
-    const CloseJob &j = J[blockIdx.z];
-    restore_body(j.G, j.A, blockIdx.x, gridDim.x, blockIdx.y);
+// Work of all (job, direction) segments laid end to end: segment s = 2 job +
+// dir starts at base[s] (non-decreasing, base[2 count] = total).  The last
+// segment whose start is at or below x holds item x.
+__device__ __forceinline__ uint32_t segment_of(const unsigned long long *base, uint32_t nseg, uint64_t x) {
+    uint32_t lo = 0, hi = nseg;  // base[lo] <= x < base[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (base[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(256) k_estimate_many(const CloseJob *__restrict__ J) {
-    const CloseJob &j = J[blockIdx.z];
-    estimate_body(j.G, j.A, blockIdx.x, gridDim.x, blockIdx.y);
+// Every block takes a contiguous run of the jobs' restore tiles (tile_base:
+// host-computed tile offsets per segment), so that blocks share the work of
+// the jobs in proportion to their tiles.
+__global__ void __launch_bounds__(256)
+k_restore_many(const CloseJob *__restrict__ J, const unsigned long long *__restrict__ tile_base, uint32_t count) {
+    const uint64_t total = tile_base[2 * count];
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    uint64_t a = (uint64_t)blockIdx.x * per;
+    const uint64_t b = a + per < total ? a + per : total;
+    while (a < b) {
+        const uint32_t sg = segment_of(tile_base, 2 * count, a);
+        const uint64_t end = tile_base[sg + 1] < b ? tile_base[sg + 1] : b;
+        const CloseJob &j = J[sg >> 1];
+        restore_body(j.G, j.A, sg & 1u, a - tile_base[sg], end - tile_base[sg], 1);
+        a = end;
+    }
+}
+
+// Candidate offsets per segment (0 for a direction that did not run or
+// whose K overflowed its capacity), for the flat estimate below.
+__global__ void k_cand_base(const CloseJob *__restrict__ J, uint32_t count, unsigned long long *__restrict__ base) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (uint32_t s = 0; s < 2 * count; s++) {
+        base[s] = acc;
+        const CloseJob &j = J[s >> 1];
+        const uint32_t d = s & 1u;
+        if (d < j.G.dirs && (d ? j.A.run[1] : j.A.run[0])) {
+            const unsigned long long nk = j.A.stats->ncand[d];
+            if (nk <= j.A.cand_cap) acc += nk;
+        }
+    }
+    base[2 * count] = acc;
+}
+
+// Every warp takes a contiguous run of the jobs' candidates.
+__global__ void __launch_bounds__(256)
+k_estimate_many(const CloseJob *__restrict__ J, const unsigned long long *__restrict__ cand_base, uint32_t count) {
+    const uint64_t total = cand_base[2 * count];
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t per = (total + nwarps - 1) / nwarps;
+    uint64_t a = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per;
+    const uint64_t b = a + per < total ? a + per : total;
+    while (a < b) {
+        const uint32_t sg = segment_of(cand_base, 2 * count, a);
+        const uint64_t end = cand_base[sg + 1] < b ? cand_base[sg + 1] : b;
+        const CloseJob &j = J[sg >> 1];
+        estimate_body(j.G, j.A, sg & 1u, a - cand_base[sg], end - cand_base[sg], 1);
+        a = end;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_sort_small_many(const CloseJob *__restrict__ J) {
@@ -532,14 +593,17 @@ void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms) {
     A.smem_hot = hot_bytes <= (size_t)200 * 1024;
 }
 
+// k_restore tiles of direction d (the same count the kernel derives)
+static uint64_t restore_tiles_dir(const Geometry &G, const RestoreArgs &A, uint32_t d) {
+    if (d >= G.dirs || !A.run[d] || A.n0[d] == 0 || A.n1[d] == 0) return 0;
+    const uint64_t t0 = (A.n0[d] + A.tile0 - 1) / A.tile0;
+    const uint64_t nc = (((uint64_t)A.n1[d] << A.ulog) + A.jchunk - 1) / A.jchunk;
+    return t0 * nc;
+}
+
 static uint64_t restore_tiles(const Geometry &G, const RestoreArgs &A) {
     uint64_t most = 0;
-    for (uint32_t d = 0; d < G.dirs; d++) {
-        if (!A.run[d]) continue;
-        const uint64_t t0 = (A.n0[d] + A.tile0 - 1) / A.tile0;
-        const uint64_t nc = (((uint64_t)A.n1[d] << A.ulog) + A.jchunk - 1) / A.jchunk;
-        if (t0 * nc > most) most = t0 * nc;
-    }
+    for (uint32_t d = 0; d < G.dirs; d++) most = std::max(most, restore_tiles_dir(G, A, d));
     return most;
 }
 
@@ -615,44 +679,46 @@ cudaError_t launch_stats_many(const CloseJob *J, uint32_t count, const Geometry 
     return cudaGetLastError();
 }
 
-cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, int num_sms, cudaStream_t s,
-                                int *launches) {
+cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, unsigned long long *tile_base_d,
+                                unsigned long long *tile_base_h, unsigned long long *cand_base_d, int num_sms,
+                                cudaStream_t s, int *launches) {
     *launches = 0;
     const Geometry &G = Jh[0].G;
     const unsigned threads = 256;
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
     const size_t smem = Jh[0].A.smem_hot ? hot_bytes : 16;
-    uint64_t most = 0, total = 0;
+    unsigned long long acc = 0;
     bool any = false;
     for (uint32_t i = 0; i < count; i++) {
-        const uint64_t t = restore_tiles(G, Jh[i].A);
-        most = std::max(most, t);
-        total += t;
         any = any || Jh[i].A.run[0] || Jh[i].A.run[1];
+        for (uint32_t d = 0; d < 2; d++) {
+            tile_base_h[2 * i + d] = acc;
+            if (d < G.dirs) acc += restore_tiles_dir(G, Jh[i].A, d);
+        }
     }
+    tile_base_h[2 * count] = acc;
     if (!any) return cudaSuccess;
-    cudaError_t e;
-    if (most > 0) {
+    cudaError_t e = cudaMemcpyAsync(tile_base_d, tile_base_h, (2 * count + 1) * sizeof(unsigned long long),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (acc > 0) {
         int per_sm = 0;
         e = prepare_launch(reinterpret_cast<const void *>(k_restore_many), (int)threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
-        // the jobs' tiles spread over the resident blocks in proportion
-        const uint64_t slots = (uint64_t)num_sms * per_sm;
-        uint64_t bx = total ? (most * slots + total - 1) / total : 1;
-        bx = std::max<uint64_t>(1, std::min<uint64_t>(bx, most));
-        k_restore_many<<<dim3((unsigned)bx, G.dirs, count), threads, smem, s>>>(J);
+        const uint64_t blocks = std::min<uint64_t>((uint64_t)num_sms * per_sm, acc);
+        k_restore_many<<<(unsigned)blocks, threads, smem, s>>>(J, tile_base_d, count);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*launches;
     }
-    const unsigned ebx = std::max(1u, (unsigned)num_sms * 4 / std::max(1u, count / 2));
-    k_estimate_many<<<dim3(ebx, G.dirs, count), 256, 0, s>>>(J);
+    k_cand_base<<<1, 32, 0, s>>>(J, count, cand_base_d);
+    k_estimate_many<<<(unsigned)num_sms * 8, 256, 0, s>>>(J, cand_base_d, count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ssmem = kSortSmall * (int)sizeof(unsigned long long);
     int per_sm = 0;
     e = prepare_launch(reinterpret_cast<const void *>(k_sort_small_many), 1024, ssmem, &per_sm);
     if (e != cudaSuccess) return e;
     k_sort_small_many<<<dim3(G.dirs, count), 1024, ssmem, s>>>(J);
-    *launches += 2;
+    *launches += 3;
     return cudaGetLastError();
 }
 

@@ -195,8 +195,11 @@ cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms
 // [kSortSmall]; the reset of every job's DHLA and counters.
 cudaError_t launch_stats_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s);
 void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms);
-cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, int num_sms, cudaStream_t s,
-                                int *launches);
+// (restore and estimate spread all jobs' tiles / candidates over the whole
+// grid: tile_base_* and cand_base_d hold 2 count + 1 offsets)
+cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, unsigned long long *tile_base_d,
+                                unsigned long long *tile_base_h, unsigned long long *cand_base_d, int num_sms,
+                                cudaStream_t s, int *launches);
 cudaError_t launch_gather_many(const CloseJob *J, uint32_t count, StatBlock *st_out, unsigned long long *hits_out,
                                cudaStream_t s);
 cudaError_t launch_reset_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s);

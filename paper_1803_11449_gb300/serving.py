@@ -62,10 +62,13 @@ class _Link:
 class Server:
     """Serve links with per-link sketches of one shape (`workload`, a
     traffic.Workload or a dict of its sketch parameters).  hbm_budget is in
-    bytes; bin_chunk_log2 sets the pairs per link in one binned round."""
+    bytes; bin_chunk_log2 sets the most pairs a link gives one binned round,
+    bin_bytes the bins of a round (default: half the budget): a round takes
+    as many links as its bins hold at their actual shares."""
 
     def __init__(self, workload, window_pairs: int, hbm_budget: int, device: int = 0,
-                 bin_chunk_log2: int = 21, cand_cap: int = 1 << 18, stream=None):
+                 bin_chunk_log2: int = 22, bin_bytes: int | None = None, cand_cap: int = 1 << 18,
+                 stream=None):
         import torch
         self.torch = torch
         self.workload = workload
@@ -83,8 +86,10 @@ class Server:
         self.pairs_done = 0
         self.steps = 0
         self._bytes = None
+        self.bin_bytes = int(bin_bytes) if bin_bytes is not None else self.budget // 2
         self.driver = sd.sd_create(self._params(0, cand_cap=1024))
-        sd.sd_set_tuning(self.driver, mode=5, bin_chunk_log2=bin_chunk_log2)
+        sd.sd_set_tuning(self.driver, mode=5, bin_chunk_log2=bin_chunk_log2,
+                         bin_batch_mib=max(1, self.bin_bytes >> 20))
         self.fixed = (sd.sd_device_bytes(self._params(0, cand_cap=1024)) +
                       sd.sd_scratch_bytes(self.driver, 1 << 20))
         if self.fixed > self.budget:

@@ -61,3 +61,41 @@ def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, 
     best = min(table, key=lambda r: r["ms"])
     sd.sd_set_tuning(h, **{k: v for k, v in best.items() if k != "ms"})
     return dict(best, table=table)
+
+
+BATCHED = [dict(bin_chunk_log2=ch, bin_batch_mib=mib, bin_tile_pairs=tp)
+           for ch in (20, 21, 22, 23, 24) for mib in (1024, 4096, 8192) for tp in (1024, 2048)]
+
+
+def autotune_many(hs, pairs_list, stream, reps: int = 2, space=None, verbose: bool = False) -> dict:
+    """Time sd_update_many over the caller's links for every batched-update
+    setting (the driver hs[0]'s chunk, bins per round and tile), each trial
+    from empty DHLAs (sd_close_many clears them); apply the best to every
+    handle and return it as a dict with "ms" and "table"."""
+    import torch
+
+    table = []
+    for knobs in (space or BATCHED):
+        try:
+            for h in hs:
+                sd.sd_set_tuning(h, mode=5, **knobs)
+        except sd.SdError:
+            continue
+        times = []
+        for _ in range(reps):
+            sd.sd_close_many(hs)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sd.sd_update_many(hs, pairs_list)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        table.append(dict(knobs, ms=min(times)))
+        if verbose:
+            print(table[-1], flush=True)
+    sd.sd_close_many(hs)
+    best = min(table, key=lambda r: r["ms"])
+    for h in hs:
+        sd.sd_set_tuning(h, mode=5, **{k: v for k, v in best.items() if k != "ms"})
+    return dict(best, table=table)

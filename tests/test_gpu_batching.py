@@ -41,7 +41,8 @@ def _same_report(rep, ref, dirs):
     assert np.array_equal(rep.hits["est"], ref["est"])
 
 
-@pytest.mark.parametrize("tuning", [dict(mode=5), dict(mode=5, bin_chunk_log2=17), dict(mode=1)])
+@pytest.mark.parametrize("tuning", [dict(mode=5), dict(mode=5, bin_chunk_log2=17), dict(mode=1),
+                                    dict(mode=5, bin_batch_mib=1), dict(mode=5, bin_chunk_log2=14, bin_batch_mib=4)])
 def test_batched_links_equal_each_link_alone(sd, O, tuning):
     """Seven links of uneven sizes (one of them much larger than a round's
     share), each with its own traffic and its own hash seed."""

@@ -126,17 +126,19 @@ def test_served_windows_equal_oracle_and_alone(mods, O):
 def test_admission_respects_budget(mods):
     sd, serving = mods
     w = _workload()
-    probe = serving.Server(w, WINDOW, hbm_budget=1 << 40)
+    bins = 64 << 20
+    probe = serving.Server(w, WINDOW, hbm_budget=1 << 40, bin_bytes=bins)
     fixed, lb = probe.fixed, probe.link_bytes()
+    assert fixed >= sd.sd_scratch_bytes(probe.driver, 1 << 20) >= bins
     probe.shutdown()
     assert fixed > 0 and lb > 2 * 4 * sd.sd_grid_words(sd.params_for(w, 1))
     with pytest.raises(ValueError):
-        serving.Server(w, WINDOW, hbm_budget=fixed - 1)  # not even the engine fits
-    srv = serving.Server(w, WINDOW, hbm_budget=fixed + lb - 1)
+        serving.Server(w, WINDOW, hbm_budget=fixed - 1, bin_bytes=bins)  # not even the engine fits
+    srv = serving.Server(w, WINDOW, hbm_budget=fixed + lb - 1, bin_bytes=bins)
     with pytest.raises(ValueError):
         srv.open_link("a", 1)  # one link does not fit
     srv.shutdown()
-    srv = serving.Server(w, WINDOW, hbm_budget=fixed + 2 * lb)
+    srv = serving.Server(w, WINDOW, hbm_budget=fixed + 2 * lb, bin_bytes=bins)
     assert srv.open_link("a", 1) and srv.open_link("b", 2)
     assert not srv.open_link("c", 3)
     assert list(srv.waiting) == ["c"] and srv.used == fixed + 2 * lb
