@@ -492,20 +492,52 @@ k_restore_many(const CloseJob *__restrict__ J, const unsigned long long *__restr
 }
 
 // Candidate offsets per segment (0 for a direction that did not run or
-// whose K overflowed its capacity), for the flat estimate below.
-__global__ void k_cand_base(const CloseJob *__restrict__ J, uint32_t count, unsigned long long *__restrict__ base) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long acc = 0;
-    for (uint32_t s = 0; s < 2 * count; s++) {
-        base[s] = acc;
-        const CloseJob &j = J[s >> 1];
-        const uint32_t d = s & 1u;
-        if (d < j.G.dirs && (d ? j.A.run[1] : j.A.run[0])) {
-            const unsigned long long nk = j.A.stats->ncand[d];
-            if (nk <= j.A.cand_cap) acc += nk;
+// whose K overflowed its capacity), for the flat estimate below: one block,
+// 1024 segments at a time, a block scan per batch of segments.
+__global__ void __launch_bounds__(1024)
+k_cand_base(const CloseJob *__restrict__ J, uint32_t count, unsigned long long *__restrict__ base) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t s0 = 0; s0 < 2 * count; s0 += blockDim.x) {
+        const uint32_t sg = s0 + threadIdx.x;
+        unsigned long long c = 0;
+        if (sg < 2 * count) {
+            const CloseJob &j = J[sg >> 1];
+            const uint32_t d = sg & 1u;
+            if (d < j.G.dirs && (d ? j.A.run[1] : j.A.run[0])) {
+                const unsigned long long nk = j.A.stats->ncand[d];
+                if (nk <= j.A.cand_cap) c = nk;
+            }
         }
+        unsigned long long incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long x = lane < (blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if ((int)lane >= o) x += v;
+            }
+            s_warp[lane] = x;  // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        const unsigned long long excl = carry + incl - c + (wid ? s_warp[wid - 1] : 0);
+        if (sg < 2 * count) base[sg] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = carry + s_warp[(blockDim.x >> 5) - 1];
+        __syncthreads();
     }
-    base[2 * count] = acc;
+    if (threadIdx.x == 0) base[2 * count] = s_carry;
 }
 
 // Every warp takes a contiguous run of the jobs' candidates.
@@ -710,7 +742,7 @@ cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*launches;
     }
-    k_cand_base<<<1, 32, 0, s>>>(J, count, cand_base_d);
+    k_cand_base<<<1, 1024, 0, s>>>(J, count, cand_base_d);
     k_estimate_many<<<(unsigned)num_sms * 8, 256, 0, s>>>(J, cand_base_d, count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ssmem = kSortSmall * (int)sizeof(unsigned long long);
