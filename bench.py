@@ -187,9 +187,10 @@ def window_for(rank: int, n: int | None = None):
 
 
 
-def cpu_oracle_rate(pairs: np.ndarray, sample: int):
+def cpu_oracle_rate(pairs: np.ndarray, sample: int, parts: dict | None = None):
     """The oracle, as it stands, on the first `sample` pairs of the window:
-    update then close, single-threaded.  Returns (pairs/s, seconds)."""
+    update then close, single-threaded.  Returns (pairs/s, seconds); the
+    update and close seconds go to `parts` when given."""
     import oracle as O
     O.build()
     w = T.WORKLOADS[WORKLOAD]
@@ -198,8 +199,11 @@ def cpu_oracle_rate(pairs: np.ndarray, sample: int):
     sub = np.ascontiguousarray(pairs[:sample])
     t0 = time.perf_counter()
     O.update(op, grid, sub)
+    t1 = time.perf_counter()
     O.close_window(op, grid)
     dt = time.perf_counter() - t0
+    if parts is not None:
+        parts.update(update_s=t1 - t0, close_s=dt - (t1 - t0))
     return sample / dt, dt
 
 
@@ -376,10 +380,13 @@ def run_ours(args, rank, world, local):
         return
     cpu = None
     if not args.no_cpu_baseline:
-        r, dt = cpu_oracle_rate(win.pairs, args.cpu_sample)
+        parts = {}
+        r, dt = cpu_oracle_rate(win.pairs, args.cpu_sample, parts)
         cpu = {"value": r / 1e9, "unit": "Gpps", "cores": 1, "kind": "oracle",
                "sample": f"first {args.cpu_sample} pairs of the window: oracle update + close "
-                         f"({dt:.1f} s, single thread)"}
+                         f"({dt:.1f} s, single thread: update {parts['update_s']:.2f} s, "
+                         f"close {parts['close_s']:.2f} s)",
+               "update_gpps": args.cpu_sample / parts["update_s"] / 1e9, "close_s": parts["close_s"]}
         workers = os.cpu_count() or 1
         rp, dtp = cpu_oracle_parallel(win.pairs, workers)
         cpu["parallel"] = {"value": rp / 1e9, "unit": "Gpps", "cores": workers,
