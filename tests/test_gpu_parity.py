@@ -241,6 +241,17 @@ def test_core_link_window_full_size(sd, O, torch_mod, mode):
     assert rep.n_hits_total > 500
 
 
+def test_stress_sketch_beyond_l2(sd, O, torch_mod):
+    """The stress sketch (g=1024, r=4, k=18, alpha=7: 2 x 128 MiB, larger than
+    L2; 2048 binning slices) on 2^25 pairs of stress-shaped traffic (flows of
+    8 packets), in the benchmark's launch configuration (binned, 2^24-pair
+    rounds) and with a round that ends mid-window."""
+    w = T.WORKLOADS["stress"]
+    win = T.make_window(w, T.window_seed(5), n=(1 << 25) + 12345)
+    rep, ref = _full_check(sd, O, torch_mod, w, win)
+    assert rep.n_hits_total > 100 and ref["flags"] == [0, 0]
+
+
 _CORE = {}
 
 
