@@ -126,3 +126,41 @@ def test_close_many_mixed_shapes_and_restores(sd, O):
             _, ref = _oracle(O, w, win.pairs, s)
             _same_report(rep, ref, w.dirs)
             assert r2.n_pairs == 0 and len(r2.hits) == 0
+
+
+def _batch_window(args):
+    link, n, planted = args
+    w = T.WORKLOADS["core"].with_(n=n, planted=planted)
+    return T.make_window(w, T.window_seed(3, link=link)).pairs
+
+
+def test_batching_workload_full_size_sampled(sd, O):
+    """The batching benchmark's workload at full size (64 links, lognormal
+    window sizes clipped to [256K, 64M], 50-300 planted each, core-link
+    sketches) in the benchmark's launch configuration; the smallest, the
+    median and the largest link are checked against the oracle in full, and
+    every link's pair count and flags are checked."""
+    import multiprocessing as mp
+
+    rng = np.random.default_rng(0x5D5A0300)
+    sizes = np.clip(np.exp(rng.normal(np.log(4 << 20), 1.0, size=64)), 256 << 10, 64 << 20)
+    sizes = (sizes.astype(np.int64) // 2) * 2
+    planted = rng.integers(50, 301, size=64)
+    jobs = [(i, int(n), int(p)) for i, (n, p) in enumerate(zip(sizes, planted))]
+    with mp.get_context("spawn").Pool(8) as pool:
+        wins = pool.map(_batch_window, jobs)
+    w = T.WORKLOADS["core"]
+    seed = T.window_seed(2)
+    hs = [sd.sd_create(sd.params_for(w, seed)) for _ in wins]
+    try:
+        sd.sd_update_many(hs, [_dev(p) for p in wins])
+        reps = sd.sd_close_many(hs)
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    order = np.argsort(sizes)
+    for i in range(64):
+        assert reps[i].n_pairs == len(wins[i]) and reps[i].flags == 0
+    for i in (order[0], order[32], order[-1]):
+        _, ref = _oracle(O, w, wins[i], seed)
+        _same_report(reps[i], ref, 2)

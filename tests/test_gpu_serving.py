@@ -198,3 +198,49 @@ def test_ring_fed_links_equal_oracle(mods, O):
         srv2.open_link("x", 1)
         srv2.attach_ring("x", rings[0])
         srv2.advance("x", R + 1)
+
+
+def test_serving_full_size_windows_sampled(mods, O):
+    """Serving at the benchmark's sizes: core-link sketches, 2^26-pair
+    windows, batches uniform in [64K, 4M] pairs, a 2 GiB budget with half for
+    bins and 2^22-pair shares; a link carrying a DDoS victim (2M spoofed
+    sources) and a plain link are served together and each link's first
+    window equals the oracle's report for those pairs alone."""
+    import torch
+    sd, serving = mods
+    W = 1 << 26
+    w = T.WORKLOADS["core"].with_(n=W, planted=100)
+    wins = [T.make_window(w, T.window_seed(4, link=i)).pairs for i in range(2)]
+    rng = np.random.default_rng(9)
+    victim = np.uint32(0xC0A80001)
+    pos = rng.choice(W, size=2_000_000, replace=False)
+    wins[0][pos, 0] = T.ip_of(0x7000_0000, np.arange(2_000_000), 12345)
+    wins[0][pos, 1] = victim
+    srv = serving.Server(w, W, hbm_budget=2 << 30)
+    seeds = [T.window_seed(4, link=i) for i in range(2)]
+    for i in range(2):
+        srv.open_link(i, seeds[i])
+    dev = [_dev(p) for p in wins]
+    at = [0, 0]
+    while min(at) < W:
+        for i in range(2):
+            m = int(min(W - at[i], rng.integers(1 << 16, (1 << 22) + 1)))
+            if m:
+                srv.submit(i, dev[i][2 * at[i]:2 * (at[i] + m)])
+                at[i] += m
+        srv.step()
+    srv.drain()
+    srv.shutdown()
+    got = {r.link: r.report for r in srv.reports if r.window == 0}
+    for i in range(2):
+        _, ref = O_close(O, w, wins[i], seeds[i])
+        _same(got[i], ref)
+    hits0 = got[0].hits
+    assert ((hits0["ip"] == victim) & (hits0["dir"] == 1)).any()
+
+
+def O_close(O, w, pairs, seed):
+    op = O.params_from(w.sketch(), seed=seed)
+    og = O.new_grid(op)
+    O.update(op, og, pairs)
+    return og, O.close_window(op, og)
