@@ -255,6 +255,31 @@ cudaError_t prepare_launch(const void *kernel, int threads, size_t smem, int *pe
 
 }  // namespace sd
 
+// Layout and hash constants of a DHLA with parameters *p (§3.1-3.2): per
+// direction, A0, A1, B1 are the first three splitmix64 outputs for the state
+// seed ^ (0x9E3779B97F4A7C15 (dir + 1)), with A0 and A1 made odd.
+void sd::geometry_of(const sd_params *p, Geometry *out) {
+    Geometry G;
+    std::memset(&G, 0, sizeof G);
+    G.g = p->g;
+    G.r = p->r;
+    G.k = p->k;
+    G.alpha = p->alpha;
+    G.dirs = p->dirs;
+    G.lg = ilog2(p->g);
+    G.wpc = p->g / 32;
+    G.row_words = ((uint64_t)1 << p->k) * G.wpc;
+    G.dir_words = (uint64_t)p->r * G.row_words;
+    for (uint32_t d = 0; d < 2; d++) {
+        uint64_t st = p->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(d + 1));
+        G.h[d].A0 = (uint32_t)splitmix64(&st) | 1u;
+        G.h[d].A1 = splitmix64(&st) | 1ull;
+        G.h[d].B1 = splitmix64(&st);
+        G.h[d].A0inv = inverse_odd(G.h[d].A0);
+    }
+    *out = G;
+}
+
 extern "C" {
 
 int sd_default_params(sd_params *p) {
@@ -349,23 +374,8 @@ static void release(sd_handle *h) {
 
 static int create_impl(const sd_params *p, sd_handle *h) {
     h->p = *p;
-    Geometry &G = h->G;
-    G.g = p->g;
-    G.r = p->r;
-    G.k = p->k;
-    G.alpha = p->alpha;
-    G.dirs = p->dirs;
-    G.lg = ilog2(p->g);
-    G.wpc = p->g / 32;
-    G.row_words = ((uint64_t)1 << p->k) * G.wpc;
-    G.dir_words = (uint64_t)p->r * G.row_words;
-    for (uint32_t d = 0; d < 2; d++) {
-        uint64_t st = p->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(d + 1));
-        G.h[d].A0 = (uint32_t)splitmix64(&st) | 1u;
-        G.h[d].A1 = splitmix64(&st) | 1ull;
-        G.h[d].B1 = splitmix64(&st);
-        G.h[d].A0inv = inverse_odd(G.h[d].A0);
-    }
+    geometry_of(p, &h->G);
+    const Geometry &G = h->G;
     // binned update, 128 KiB slices, 1024-pair tiles, 2^24-pair rounds (autotuned on GB300)
     h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192};
     h->zhot = zhot_of(p->g, p->theta);

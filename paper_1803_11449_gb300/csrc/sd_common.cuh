@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sd.h"
+
 namespace sd {
 
 constexpr int kMaxRows = 8;
@@ -188,6 +190,9 @@ cudaError_t launch_row_stats(const uint32_t *grid, const Geometry &G, int zhot, 
 cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *he, uint32_t rows, cudaStream_t s);
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s);
 cudaError_t launch_estimate(const Geometry &G, const RestoreArgs &A, int num_sms, cudaStream_t s);
+// Host: DHLA layout and hash constants for a valid *p (as sd_create sets them).
+void geometry_of(const sd_params *p, Geometry *out);
+
 // Batched close over `count` jobs (device array J; Jh is the host copy,
 // used for grid sizing): row stats + HE(0), HE(1) of every job; restore,
 // estimate and small sorts; a gather of every job's StatBlock and first

@@ -32,13 +32,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t *g_addr[kMaxDevices] = {nullptr};
 
-uint64_t splitmix64_next(uint64_t *state) {  // Steele, Lea, Flood 2014
-    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 __global__ void k_clear_counts(uint32_t *p, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
 }
@@ -69,25 +62,7 @@ extern "C" int sd_update_noalloc(const sd_params *p, uint32_t *grid, const uint3
 
     // geometry and hash constants, as for a handle with the same parameters
     Geometry G;
-    std::memset(&G, 0, sizeof G);
-    G.g = p->g;
-    G.r = p->r;
-    G.k = p->k;
-    G.alpha = p->alpha;
-    G.dirs = p->dirs;
-    while ((1u << G.lg) < p->g) G.lg++;
-    G.wpc = p->g / 32;
-    G.row_words = ((uint64_t)1 << p->k) * G.wpc;
-    G.dir_words = (uint64_t)p->r * G.row_words;
-    for (uint32_t d = 0; d < 2; d++) {
-        uint64_t st = p->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(d + 1));
-        G.h[d].A0 = (uint32_t)splitmix64_next(&st) | 1u;
-        G.h[d].A1 = splitmix64_next(&st) | 1ull;
-        G.h[d].B1 = splitmix64_next(&st);
-        uint32_t x = G.h[d].A0;
-        for (int i = 0; i < 5; i++) x *= 2u - G.h[d].A0 * x;
-        G.h[d].A0inv = x;
-    }
+    geometry_of(p, &G);
 
     // slices of 2^15 words (at most 4096: a DHLA of up to 512 MiB); bins sized
     // to the scratch, rounds sized to the bins with 100% slack for skew
