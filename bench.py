@@ -311,38 +311,65 @@ def run_ours(args, rank, world, local):
     elif args.autotune:
         from paper_1803_11449_gb300.tune import autotune
         tuned = autotune(h, pairs_dev, stream, verbose=args.verbose)
+    # a second sketch of the same link on its own stream: window w+1 is
+    # ingested while window w closes (two DHLAs in turn, as a monitor that
+    # keeps counting during a close would run)
+    stream2 = torch.cuda.Stream()
+    h2 = sd.sd_create(sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream2.cuda_stream))
+    t1 = sd.sd_get_tuning(h)
+    sd.sd_set_tuning(h2, **{f: getattr(t1, f) for f, _ in sd.sd_tuning._fields_})
+    hs, streams = (h, h2), (stream, stream2)
 
-    def step():
-        sd.sd_update(h, pairs_dev)
-        return sd.sd_close_window(h)
+    def timed(steps, pipelined):
+        """`steps` windows, each sd_update then sd_close_window; pipelined:
+        the two sketches alternate and window w's close overlaps window
+        w+1's update.  Returns (elapsed s, per-update s, last report)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_mid = torch.cuda.Event()
+        t_start.record(stream)
+        stream2.wait_event(t_start)
+        rep = None
+        for i in range(steps):
+            k = (i & 1) if pipelined else 0
+            ev[i][0].record(streams[k])
+            sd.sd_update(hs[k], pairs_dev)
+            ev[i][1].record(streams[k])
+            if not pipelined:
+                rep = sd.sd_close_window(hs[0])
+            elif i > 0:
+                rep = sd.sd_close_window(hs[1 - k])
+        if pipelined:
+            rep = sd.sd_close_window(hs[(steps - 1) & 1])
+        t_mid.record(stream2)
+        stream.wait_event(t_mid)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        return t_start.elapsed_time(t_end) / 1e3, [a.elapsed_time(b_) / 1e3 for a, b_ in ev], rep
 
-    for _ in range(args.warmup):
-        rep = step()
+    for _ in range(max(1, args.warmup // 2)):
+        timed(2, True)
+        timed(2, False)
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     close_ms = []
     dist_barrier(world)
     torch.cuda.synchronize()
     launches0 = sd.sd_kernel_launches()
     with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            sd.sd_update(h, pairs_dev)
-            ev[i][1].record(stream)
-            rep = sd.sd_close_window(h)
-        t_end.record(stream)
-        torch.cuda.synchronize()
+        elapsed, upd, rep = timed(args.steps, not args.sequential)
     launches = sd.sd_kernel_launches() - launches0
     dist_barrier(world)
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    upd = [a.elapsed_time(b_) / 1e3 for a, b_ in ev]
     elapsed_max = dist_max(elapsed, world)
     value = world * args.steps * n / elapsed_max / 1e9
+    # the other schedule, for reference
+    el2, upd2, _ = timed(args.steps, args.sequential)
+    el2_max = dist_max(el2, world)
+    # the roofline takes the update kernels alone (the sequential schedule);
+    # in the pipelined one a close overlaps them
+    upd_alone, upd_piped = (upd, upd2) if args.sequential else (upd2, upd)
+    other = world * args.steps * n / el2_max / 1e9
 
     # window-close latency on its own: the update has finished when the
     # clock starts; the report is on the host when it stops
@@ -371,9 +398,10 @@ def run_ours(args, rank, world, local):
     e2e = world * args.e2e_steps * n / e_el / 1e9
     tuning = sd.sd_get_tuning(h)
     sd.sd_destroy(h)
+    sd.sd_destroy(h2)
 
     peak, peak_kind = measured_peaks()
-    t_upd = statistics.mean(upd)
+    t_upd = statistics.mean(upd_alone)
     achieved = BYTES_PER_PAIR * n / t_upd / 1e9
     clocks = clk.summary()
     if rank != 0:
@@ -406,14 +434,21 @@ def run_ours(args, rank, world, local):
                    "traffic": args.traffic,
                    "tuning": dict({f: getattr(tuning, f) for f, _ in tuning._fields_},
                                   autotuned=tuned is not None)},
+        "schedule": ("sequential: one sketch, each window's close before the next update" if args.sequential else
+                     "pipelined: two sketches of the link in turn, window w closes while w+1 is ingested"),
+        ("pipelined" if args.sequential else "sequential"): {"value": other, "unit": "Gpps",
+                                                             "ms_per_step": 1e3 * el2_max / args.steps},
         "gbps_at_800B": value * 1e9 * GBITS_PER_PACKET,
         "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
         "update_ms": 1e3 * t_upd,
+        "update_ms_in_pipeline": 1e3 * statistics.mean(upd_piped),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": profiled_traffic(tuning.mode, n) if WORKLOAD == "core" else None,
                      "kernel": "k_bin+k_apply" if tuning.mode == 5 else "k_update",
+                     "timed": "CUDA events around each sd_update of the sequential schedule "
+                              "(the update kernels alone on the library's stream)",
                      "peak_source": f"hbm_gbs, {peak_kind}",
                      "algorithmic_bytes_per_pair": BYTES_PER_PAIR},
         "l2_random_op_roofline": {"ops_per_pair": p.r * p.dirs,
@@ -697,6 +732,8 @@ def main():
     ap.add_argument("--traffic", default="core", choices=["core", "uniform"],
                     help="uniform: every pair random (no Zipf, no planted hosts)")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="one sketch: each window closes before the next is ingested")
     ap.add_argument("--batching", action="store_true",
                     help="many links of uneven size: batched versus one window at a time")
     ap.add_argument("--links", type=int, default=64)
