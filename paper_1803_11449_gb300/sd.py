@@ -177,6 +177,13 @@ class Handle:
     def _as_parameter_(self):
         return ctypes.c_void_p(self.ptr)
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        sd_destroy(self)
+        return False
+
 
 def sd_create(p: sd_params) -> Handle:
     out = _VP()
