@@ -381,21 +381,45 @@ def run_ours(args, rank, world, local):
         close_ms.append(1e3 * (time.perf_counter() - c0))
 
     # end to end: pinned host pairs through sd_update (H2D in the timed
-    # region), report back to the host in sd_close_window
-    for _ in range(2):
-        sd.sd_update(h, pairs_host)
-        sd.sd_close_window(h)
+    # region), report back to the host in sd_close_window.  In the pipelined
+    # schedule a second host thread closes window w (its own sketch) while
+    # the main thread ingests window w+1 into the other sketch, so the
+    # host-to-device link does not wait for the close.
+    from concurrent.futures import ThreadPoolExecutor
+
+    def e2e_run(steps, pipelined):
+        d2h = 0
+        if not pipelined:
+            for _ in range(steps):
+                sd.sd_update(h, pairs_host)
+                d2h += 296 + 8 * sd.sd_close_window(h).n_hits_total
+            return d2h
+        with ThreadPoolExecutor(1) as ex:
+            fut = None
+            for i in range(steps):
+                sd.sd_update(hs[i & 1], pairs_host)
+                if fut is not None:
+                    d2h += 296 + 8 * fut.result().n_hits_total
+                fut = ex.submit(sd.sd_close_window, hs[i & 1])
+            d2h += 296 + 8 * fut.result().n_hits_total
+        return d2h
+
+    e2e_run(2, not args.sequential)
     torch.cuda.synchronize()
     dist_barrier(world)
     e0 = time.perf_counter()
-    d2h = 0
-    for _ in range(args.e2e_steps):
-        sd.sd_update(h, pairs_host)
-        r2 = sd.sd_close_window(h)
-        d2h += 296 + 8 * r2.n_hits_total
+    d2h = e2e_run(args.e2e_steps, not args.sequential)
     torch.cuda.synchronize()
     e_el = dist_max(time.perf_counter() - e0, world)
     e2e = world * args.e2e_steps * n / e_el / 1e9
+    # the other schedule, for reference
+    e2e_run(2, args.sequential)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    e0 = time.perf_counter()
+    e2e_run(args.e2e_steps, args.sequential)
+    torch.cuda.synchronize()
+    e2e_other = world * args.e2e_steps * n / dist_max(time.perf_counter() - e0, world) / 1e9
     tuning = sd.sd_get_tuning(h)
     sd.sd_destroy(h)
     sd.sd_destroy(h2)
@@ -437,7 +461,8 @@ def run_ours(args, rank, world, local):
         "schedule": ("sequential: one sketch, each window's close before the next update" if args.sequential else
                      "pipelined: two sketches of the link in turn, window w closes while w+1 is ingested"),
         ("pipelined" if args.sequential else "sequential"): {"value": other, "unit": "Gpps",
-                                                             "ms_per_step": 1e3 * el2_max / args.steps},
+                                                             "ms_per_step": 1e3 * el2_max / args.steps,
+                                                             "e2e": e2e_other},
         "gbps_at_800B": value * 1e9 * GBITS_PER_PACKET,
         "close_latency_ms": {"p50": float(np.percentile(close_ms, 50)),
                              "p99": float(np.percentile(close_ms, 99)), "samples": len(close_ms)},
@@ -716,7 +741,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--ref-sample", type=int, default=1 << 22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
