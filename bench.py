@@ -699,6 +699,7 @@ def run_serving(args, rank, world, local):
                 time.sleep(20e-6)
         torch.cuda.synchronize()
     elapsed = time.perf_counter() - t0
+    srv.drain()  # the reports of closes still in flight
     served = sum(srv.links[i].tail - base[i] for i in srv.admitted)
     lat = []
     for r in srv.reports:

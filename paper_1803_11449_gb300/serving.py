@@ -3,16 +3,19 @@ link's DHLA resident on the device, a window closed every `window_pairs`
 pairs of a link.
 
 The engine does continuous batching: every step takes all batches that
-have arrived for every admitted link, cuts them at window boundaries, and
-runs them in one batched update (sd_update_many); every window that
-filled during the step is closed together with the others that filled
-(sd_close_many).  The batched update runs on a driver handle of the same
-shape that holds no link (its bins serve every step); the budget covers
-the driver, its bins for the largest round, and the admitted links'
-sketches.  A link is admitted when its sketch fits the budget; the others
-keep their batches queued, in arrival order, until a slot frees (a link
-leaves).  All GPU work goes through the C ABI;
-this module only schedules.
+have arrived for every admitted link that is not closing, cuts them at
+window boundaries, and runs them in one batched update (sd_update_many);
+the windows that filled during the step are closed together
+(sd_close_many) by a closing thread while the next steps update the other
+links.  Each link's handle has its own CUDA stream, so a close waits only
+for the update that filled its window; the link itself rejoins the steps
+once its report is on the host.  The batched update runs on a driver
+handle of the same shape that holds no link (its bins serve every step);
+the budget covers the driver, its bins for the largest round, and the
+admitted links' sketches.  A link is admitted when its sketch fits the
+budget; the others keep their batches queued, in arrival order, until a
+slot frees (a link leaves).  All GPU work goes through the C ABI; this
+module only schedules.
 
 A link takes its pairs either as submitted batches (device tensors, queued
 in order) or from a ring of pairs in device memory that a producer fills
@@ -29,6 +32,7 @@ from __future__ import annotations
 import collections
 import dataclasses
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 from . import sd
 
@@ -47,8 +51,10 @@ class _Link:
     def __init__(self, seed):
         self.seed = seed
         self.h = None                        # handle while admitted
+        self.stream = None                   # the handle's CUDA stream
         self.filled = 0                      # pairs in the open window
         self.window = 0                      # index of the open window
+        self.closing = False                 # its full window is being closed
         self.pending = collections.deque()   # [pairs tensor (2n words), arrival stamp]
         self.last_arrival = 0.0
         self.ring = None                     # device ring of pairs (2R words)
@@ -86,33 +92,37 @@ class Server:
         self.pairs_done = 0
         self.steps = 0
         self._bytes = None
+        self._closer = ThreadPoolExecutor(1)
+        self._closing = collections.deque()    # (future, link ids) in submission order
         self.bin_bytes = int(bin_bytes) if bin_bytes is not None else self.budget // 2
-        self.driver = sd.sd_create(self._params(0, cand_cap=1024))
+        self.driver = sd.sd_create(self._params(0, self.stream, cand_cap=1024))
         sd.sd_set_tuning(self.driver, mode=5, bin_chunk_log2=bin_chunk_log2,
                          bin_batch_mib=max(1, self.bin_bytes >> 20))
-        self.fixed = (sd.sd_device_bytes(self._params(0, cand_cap=1024)) +
+        self.fixed = (sd.sd_device_bytes(self._params(0, self.stream, cand_cap=1024)) +
                       sd.sd_scratch_bytes(self.driver, 1 << 20))
         if self.fixed > self.budget:
             sd.sd_destroy(self.driver)
             self.driver = None
+            self._closer.shutdown()
             raise ValueError(f"the engine's own memory ({self.fixed} bytes) is above the budget {self.budget}")
         self.used = self.fixed
         self._empty = torch.zeros(0, dtype=torch.int32, device=f"cuda:{device}")
 
     # ---------------------------------------------------------- admission
-    def _params(self, seed, cand_cap=None):
+    def _params(self, seed, stream, cand_cap=None):
         return sd.params_for(self.workload, seed, device=self.device, cand_cap=cand_cap or self.cand_cap,
-                             cuda_stream=self.stream.cuda_stream)
+                             cuda_stream=stream.cuda_stream)
 
     def link_bytes(self) -> int:
         """Device bytes of one link's handle (its DHLA and close buffers)."""
         if self._bytes is None:
-            self._bytes = sd.sd_device_bytes(self._params(0))
+            self._bytes = sd.sd_device_bytes(self._params(0, self.stream))
         return self._bytes
 
     def _admit(self, lid) -> None:
         L = self.links[lid]
-        L.h = sd.sd_create(self._params(L.seed))
+        L.stream = self.torch.cuda.Stream(device=self.device)
+        L.h = sd.sd_create(self._params(L.seed, L.stream))
         sd.sd_set_tuning(L.h, mode=5, bin_chunk_log2=self.bin_chunk_log2)
         self.admitted[lid] = L
         self.used += self.link_bytes()
@@ -142,14 +152,13 @@ class Server:
         L = self.links[link_id]
         out = None
         if L.h is not None:
+            while L.closing:
+                self._collect(block=True)
             while L.has_work():
                 self._feed([link_id], flush=True)
             if L.filled:
-                self.stream.synchronize()
-                t0 = time.perf_counter()
-                rep = sd.sd_close_window(L.h)
-                t1 = time.perf_counter()
-                out = WindowReport(link_id, L.window, rep, t1 - t0, t1, L.last_arrival)
+                reps, close_s, done_at = self._close_now([L.h])
+                out = WindowReport(link_id, L.window, reps[0], close_s, done_at, L.last_arrival)
                 self.reports.append(out)
             sd.sd_destroy(L.h)
             L.h = None
@@ -197,7 +206,7 @@ class Server:
         """Take each link's queued pairs up to the end of its open window
         (a batch that crosses the boundary is split, its rest waits) and
         apply them in one batched update.  Returns the links whose window
-        is full."""
+        is full; with flush, closes them here (the caller's thread)."""
         hs, bufs, full = [self.driver], [self._empty], []
         for lid in lids:
             L = self.links[lid]
@@ -234,34 +243,66 @@ class Server:
         if len(hs) > 1:
             sd.sd_update_many(hs, bufs)
         if flush and full:
-            self._close(full)
+            self._finish(full, *self._close_now([self.links[lid].h for lid in full]))
         return full
 
-    def _close(self, lids) -> list[WindowReport]:
-        self.stream.synchronize()
+    @staticmethod
+    def _close_now(handles):
+        """Close the windows of `handles` (each handle's stream already
+        waits for the update that filled it).  Returns (reports, close
+        seconds, completion time)."""
+        for h in handles:
+            sd.sd_sync(h)  # the completing update is done: the close latency starts here
         t0 = time.perf_counter()
-        reps = sd.sd_close_many([self.links[lid].h for lid in lids])
+        reps = sd.sd_close_many(handles)
         t1 = time.perf_counter()
+        return reps, t1 - t0, t1
+
+    def _finish(self, lids, reps, close_s, done_at) -> list[WindowReport]:
         out = []
         for lid, rep in zip(lids, reps):
             L = self.links[lid]
-            out.append(WindowReport(lid, L.window, rep, t1 - t0, t1, L.last_arrival))
+            out.append(WindowReport(lid, L.window, rep, close_s, done_at, L.last_arrival))
             L.window += 1
             L.filled = 0
+            L.closing = False
         self.reports += out
         return out
 
+    def _collect(self, block=False) -> list[WindowReport]:
+        """Reports of the closes that have finished (block: wait for the
+        oldest one when none has)."""
+        out = []
+        while self._closing and (self._closing[0][0].done() or (block and not out)):
+            fut, lids = self._closing.popleft()
+            out += self._finish(lids, *fut.result())
+        return out
+
     def step(self) -> list[WindowReport]:
-        """One engine step: one batched update over every admitted link's
-        arrived pairs, then one batched close of the windows it filled."""
+        """One engine step: collect finished closes, run one batched update
+        over every ready link's arrived pairs, and hand the windows it
+        filled to the closing thread.  With nothing to update, wait for the
+        oldest close in flight instead."""
         self.steps += 1
-        full = self._feed(list(self.admitted))
-        return self._close(full) if full else []
+        out = self._collect()
+        ready = [lid for lid, L in self.admitted.items() if not L.closing and L.has_work()]
+        if not ready:
+            if self._closing:
+                out += self._collect(block=True)
+            return out
+        full = self._feed(ready)
+        if full:
+            for lid in full:
+                self.links[lid].closing = True
+            fut = self._closer.submit(self._close_now, [self.links[lid].h for lid in full])
+            self._closing.append((fut, full))
+        return out
 
     def drain(self) -> list[WindowReport]:
-        """Steps until no admitted link has queued pairs."""
+        """Steps until no admitted link has queued pairs and no close is
+        in flight."""
         out = []
-        while any(L.has_work() for L in self.admitted.values()):
+        while self._closing or any(L.has_work() for L in self.admitted.values()):
             out += self.step()
         return out
 
@@ -269,6 +310,8 @@ class Server:
         """Close every link (admitted links first, then those that get
         admitted as slots free)."""
         out = []
+        while self._closing:
+            out += self._collect(block=True)
         while self.links:
             lid = next(iter(self.admitted), None)
             if lid is None:
@@ -281,4 +324,5 @@ class Server:
             sd.sd_destroy(self.driver)
             self.driver = None
             self.used -= self.fixed
+            self._closer.shutdown()
         return out
