@@ -75,7 +75,8 @@ typedef struct {
     uint64_t cand_cap;    /* capacity for the candidate set K per direction;
                              default 2^20 */
     uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
-    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^22 */
+    uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^22, or 2^24 when the
+                             DHLA has more than 64 MiB */
     void *cuda_stream;    /* cudaStream_t for all device work, or NULL for a
                              handle-owned stream */
 } sd_params;

@@ -320,7 +320,11 @@ static void resolve_caps(const sd_params *p, uint64_t *pair_cap, uint64_t *cand_
     *cand_cap = p->cand_cap ? p->cand_cap : (1ull << 20);
     *hits_cap = next_pow2(*cand_cap);
     *report_cap = p->report_cap ? p->report_cap : (uint64_t)p->dirs * *cand_cap;
-    *stage = p->stage_pairs ? p->stage_pairs : (1ull << 22);
+    // host-ingest chunks: 2^22 pairs keep the last chunk's kernels short; a
+    // DHLA larger than L2 takes 2^24 (each chunk is one binning round, and
+    // every round reads and writes such a DHLA in DRAM once)
+    const uint64_t dhla_bytes = (uint64_t)p->dirs * p->r * ((uint64_t)1 << p->k) * (p->g / 8);
+    *stage = p->stage_pairs ? p->stage_pairs : (dhla_bytes > (64ull << 20) ? (1ull << 24) : (1ull << 22));
 }
 
 uint64_t sd_device_bytes(const sd_params *p) {
