@@ -259,9 +259,9 @@ def _report_of(h: Handle, rc: int, rep: sd_report) -> Report:
     p = h.params
     n = int(rep.n_hits)
     if n:
-        raw = np.ctypeslib.as_array(ctypes.cast(rep.hits, ctypes.POINTER(ctypes.c_uint8)),
-                                    shape=(n * HIT_DTYPE.itemsize,))
-        hits = raw.view(HIT_DTYPE).copy()
+        addr = ctypes.cast(rep.hits, ctypes.c_void_p).value
+        raw = (ctypes.c_char * (n * HIT_DTYPE.itemsize)).from_address(addr)
+        hits = np.frombuffer(raw, dtype=HIT_DTYPE, count=n).copy()  # the handle reuses its buffer
     else:
         hits = np.zeros(0, dtype=HIT_DTYPE)
     zr = np.frombuffer(rep.zr, dtype=np.uint64).reshape(2, 8)[: p.dirs, : p.r].copy()
