@@ -164,3 +164,30 @@ def test_batching_workload_full_size_sampled(sd, O):
     for i in (order[0], order[32], order[-1]):
         _, ref = _oracle(O, w, wins[i], seed)
         _same_report(reps[i], ref, 2)
+
+
+def test_update_many_mixed_members_and_close_many_arguments(sd, O):
+    """sd_update_many members that cannot join the binned batch (host-memory
+    pairs, another DHLA shape, no pairs) take the single-handle path; the
+    results still equal the oracle's.  sd_close_many rejects a handle given
+    twice and accepts an empty list."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    w1 = T.WORKLOADS["tiny"].with_(dirs=1)
+    wins = [T.make_window(w.with_(n=100_000, planted=4), s) for s in (51, 52, 53)]
+    hs = [sd.sd_create(sd.params_for(w, 51)), sd.sd_create(sd.params_for(w, 52)),
+          sd.sd_create(sd.params_for(w1, 53)), sd.sd_create(sd.params_for(w, 54))]
+    try:
+        pairs = [_dev(wins[0].pairs), np.ascontiguousarray(wins[1].pairs), _dev(wins[2].pairs),
+                 np.zeros((0, 2), np.uint32)]
+        sd.sd_update_many(hs, pairs)
+        reps = sd.sd_close_many(hs)
+        with pytest.raises(sd.SdError):
+            sd.sd_close_many([hs[0], hs[1], hs[0]])
+        assert sd.sd_close_many([]) == []
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    for rep, win, ww, s in zip(reps[:3], wins, (w, w, w1), (51, 52, 53)):
+        _, ref = _oracle(O, ww, win.pairs, s)
+        _same_report(rep, ref, ww.dirs)
+    assert reps[3].n_pairs == 0 and len(reps[3].hits) == 0
