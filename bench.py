@@ -47,6 +47,7 @@ DESCS = {
              "outbound only"),
 }
 BYTES_PER_PAIR = 8
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e specification, for context beside the measured copy rate
 GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
 CPU_SAMPLE_PAIRS = 1 << 26
 
@@ -471,6 +472,7 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": profiled_traffic(tuning.mode, n) if WORKLOAD == "core" else None,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal": NOMINAL_HBM_GBS,
                      "kernel": "k_bin+k_apply" if tuning.mode == 5 else "k_update",
                      "timed": "CUDA events around each sd_update of the sequential schedule "
                               "(the update kernels alone on the library's stream)",
