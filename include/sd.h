@@ -52,8 +52,9 @@ extern "C" {
 
 /* Per-direction flags, in sd_report.flags at bit offset 8*dir. */
 #define SD_FLAG_SATURATED 1u
-#define SD_FLAG_OVERLOAD_PAIRS 2u  /* |HE(0)| * |HE(1)| > pair_cap: restore skipped */
-#define SD_FLAG_OVERLOAD_CANDS 4u  /* |K| > cand_cap: candidates not kept */
+#define SD_FLAG_OVERLOAD_PAIRS 2u  /* restore work over pair_cap: restore skipped */
+#define SD_FLAG_OVERLOAD_CANDS 4u  /* |K| > cand_cap (or a staged-join list over its
+                                      buffer): candidates not kept */
 #define SD_FLAG_REPORT_OVERFLOW 8u /* hits beyond report_cap were dropped */
 
 typedef struct sd_handle sd_handle;
@@ -70,8 +71,9 @@ typedef struct {
     uint64_t seed;        /* seed of the hash constants */
     uint32_t dirs;        /* 1: outbound (src keyed) only; 2: outbound and inbound */
     int32_t device;       /* CUDA device ordinal */
-    uint64_t pair_cap;    /* restore is skipped (OVERLOAD) when |HE(0)|*|HE(1)| exceeds
-                             this; default 2^32 */
+    uint64_t pair_cap;    /* restore is skipped (OVERLOAD) when its work bound exceeds
+                             this: |HE(0)|*|HE(1)| (c0, c1) pairs, or |HE(0)||HE(1)||HE(2)|
+                             tuples for the staged join (tuning restore = 1); default 2^32 */
     uint64_t cand_cap;    /* capacity for the candidate set K per direction;
                              default 2^20 */
     uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
