@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -137,6 +138,33 @@ struct CloseState {
     const unsigned long long *keys[2];     // their sorted keys in pinned host memory
 };
 
+// The report's hits: a plain growable array that is not zero-filled when it
+// grows (every slot is written by the close before it is read).
+class HitBuf {
+  public:
+    void clear() { n_ = 0; }
+    size_t size() const { return n_; }
+    bool empty() const { return n_ == 0; }
+    sd_hit *data() { return buf_.get(); }
+    sd_hit &operator[](size_t i) { return buf_[i]; }
+    void truncate(size_t n) { n_ = n < n_ ? n : n_; }
+    void grow_to(size_t n) {
+        if (n > cap_) {
+            size_t c = cap_ ? cap_ : 1024;
+            while (c < n) c *= 2;
+            std::unique_ptr<sd_hit[]> b(new sd_hit[c]);
+            if (n_) std::memcpy(b.get(), buf_.get(), n_ * sizeof(sd_hit));
+            buf_ = std::move(b);
+            cap_ = c;
+        }
+        n_ = n;
+    }
+
+  private:
+    std::unique_ptr<sd_hit[]> buf_;
+    size_t n_ = 0, cap_ = 0;
+};
+
 struct sd_handle {
     sd_params p{};
     Geometry G{};
@@ -159,7 +187,7 @@ struct sd_handle {
     unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
     uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
     unsigned long long *big_h = nullptr;  // pinned [2][hits_cap]: large sorted hit lists
-    std::vector<sd_hit> report;
+    HitBuf report;
     std::vector<double> est_tbl;
     uint64_t last_ncand[2] = {0, 0};
     bool have_close = false;
@@ -967,7 +995,7 @@ static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
         const uint64_t nh = c.nh[d];
         const unsigned long long *keys = c.keys[d];
         const size_t at = h->report.size();
-        h->report.resize(at + nh);
+        h->report.grow_to(at + nh);
         sd_hit *out_h = h->report.data() + at;
         const double *t = tbl.data();
         const size_t tn = tbl.size();
@@ -994,7 +1022,7 @@ static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
     if (h->report.size() > h->report_cap) {
         for (uint64_t q = h->report_cap; q < h->report.size(); q++)
             flags |= SD_FLAG_REPORT_OVERFLOW << (8 * h->report[q].dir);
-        h->report.resize(h->report_cap);
+        h->report.truncate(h->report_cap);
     }
     out->n_pairs = h->n_pairs;
     h->n_pairs = 0;
