@@ -252,6 +252,25 @@ def test_stress_sketch_beyond_l2(sd, O, torch_mod):
     assert rep.n_hits_total > 100 and ref["flags"] == [0, 0]
 
 
+@pytest.mark.parametrize("g,r,k,alpha,theta,n,pool,planted,c", [
+    (32, 8, 8, 4, 40, 6000, 1 << 10, 2, (120, 200)),       # one word per estimator, the most rows,
+                                                           # 256 estimators, 2^16 preimages per (c0, c1)
+    (64, 6, 10, 6, 80, 40_000, 1 << 12, 3, (250, 400)),
+    (4096, 3, 16, 16, 1024, 1 << 18, 1 << 15, 6, (3072, 6144)),  # 128 words per estimator, blocks
+                                                                 # that do not overlap
+    (32, 3, 24, 8, 40, 1 << 18, 1 << 16, 6, (120, 240)),   # 2^24 estimators: 3 x 64 MiB per direction,
+                                                           # hot row 2 too large for shared memory
+])
+def test_edge_sketch_shapes(sd, O, torch_mod, g, r, k, alpha, theta, n, pool, planted, c):
+    """The extremes of the parameter space (g = 32 and 4096, r = 3 and 8,
+    k = 8 and 24) on both directions, in the default launch configuration."""
+    w = T.WORKLOADS["tiny"].with_(g=g, r=r, k=k, alpha=alpha, theta=theta, dirs=2, n=n, src_pool=pool,
+                                  dst_pool=pool, planted=planted, planted_c=("uniform",) + c)
+    win = T.make_window(w, 61)
+    rep, ref = _full_check(sd, O, torch_mod, w, win)
+    assert ref["flags"] == [0, 0] and rep.n_hits_total > 0
+
+
 _CORE = {}
 
 
