@@ -271,6 +271,28 @@ def test_edge_sketch_shapes(sd, O, torch_mod, g, r, k, alpha, theta, n, pool, pl
     assert ref["flags"] == [0, 0] and rep.n_hits_total > 0
 
 
+def _window_of(w, pairs):
+    return T.Window(pairs=np.ascontiguousarray(pairs, dtype=np.uint32), planted_ip=np.zeros(0, np.uint32),
+                    planted_dir=np.zeros(0, np.uint8), planted_c=np.zeros(0, np.int64), workload=w, seed=0)
+
+
+def test_degenerate_windows(sd, O, torch_mod):
+    """One pair repeated 2^20 times (every bit-set of the window lands in the
+    same 8 words: the bins overflow into the atomic fallback), and one source
+    with 2^20 distinct destinations (its estimators fill completely: SZ = 0,
+    an infinite Eq. 4 estimate, reported by both sides)."""
+    w = T.WORKLOADS["core"].with_(n=1 << 20)
+    same = np.tile(np.array([[0x0A000001, 0xC0A80001]], np.uint32), (1 << 20, 1))
+    rep, ref = _full_check(sd, O, torch_mod, w, _window_of(w, same))
+    assert rep.n_hits_total == 0
+    one = np.empty((1 << 20, 2), np.uint32)
+    one[:, 0] = 0x0A000002
+    one[:, 1] = T.mix32(np.arange(1 << 20, dtype=np.uint32))
+    rep, ref = _full_check(sd, O, torch_mod, w, _window_of(w, one))
+    hit = rep.hits[(rep.hits["ip"] == 0x0A000002) & (rep.hits["dir"] == 0)]
+    assert len(hit) == 1 and hit["sz"][0] == 0 and np.isinf(hit["est"][0])
+
+
 _CORE = {}
 
 
