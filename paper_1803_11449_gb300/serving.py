@@ -108,6 +108,13 @@ class Server:
         self.used = self.fixed
         self._empty = torch.zeros(0, dtype=torch.int32, device=f"cuda:{device}")
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.shutdown()
+        return False
+
     # ---------------------------------------------------------- admission
     def _params(self, seed, stream, cand_cap=None):
         return sd.params_for(self.workload, seed, device=self.device, cand_cap=cand_cap or self.cand_cap,

@@ -152,3 +152,12 @@ def test_admission_order_and_budget(fake):
     assert len(_windows(srv, "c")[0]) == 50 and fake.live == 0
     with pytest.raises(ValueError):
         serving.Server({}, 100, hbm_budget=999)
+
+
+def test_server_as_context_manager_releases_everything(fake):
+    with serving.Server({}, 10, hbm_budget=10_000) as srv:
+        srv.open_link("a", 1)
+        srv.submit("a", torch.from_numpy(_stream(25, 1).reshape(-1)))
+        srv.step()
+    assert fake.live == 0 and srv.used == 0 and not srv.links
+    assert [len(w) for w in _windows(srv, "a")] == [10, 10, 5]
