@@ -621,14 +621,12 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
     return SD_OK;
 }
 
-// Slices of one handle's DHLA for the binned update: (S, slice_log2), or
-// false when the DHLA is too large to bin.
 // Layout of a batched update driven by h (sd_update_many): slices per
-// member DHLA, slice size, bin capacity per slice, members per round.  A
-// round gives every member a full binning round of pairs (each member's
-// apply sweeps its whole DHLA once per round, so smaller shares would
-// multiply that sweep); a round is bounded by 4096 slices and by the
-// tuning's bin_batch_mib of bins.  False when h does not bin.
+// member DHLA, slice size, bin capacity per slice for a given member share,
+// and the members a round of full shares (one chunk each) holds.  A round is
+// bounded by 4096 slices and by the tuning's bin_batch_mib of bins; each
+// member's apply sweeps its whole DHLA once per round, so shares are as long
+// as the bins allow.  False when h does not bin.
 struct BatchLayout {
     uint32_t S_link, sl, per_group;  // per_group: members of a round of full chunks
     uint64_t cap_link;               // bin capacity per slice for a full chunk
