@@ -6,13 +6,16 @@
 //                 |HE(i)|.
 //   k_compact     sorted lists HE(0) and HE(1) (all HE(i) for the staged
 //                 join of sd_join.cu) from their bitmaps.
-//   k_restore     the candidate set K = {a : DH_i(a) in HE(i) for all i} and,
-//                 fused, SZ(a) from ULE(a) = AND of a's r estimators, keeping
-//                 (a, SZ) when SZ <= szmax.
+//   k_restore     the candidate set K = {a : DH_i(a) in HE(i) for all i}.
+//   k_estimate    SZ(a) from ULE(a) = AND of a's r estimators, one warp per
+//                 candidate, keeping (a, SZ) when SZ <= szmax.
 //   k_sort_small  orders each direction's hits by address (bitonic, smem).
-//   k_bitonic_*   the same for hit lists too large for one block.
+//   k_sort_segments + k_merge_rank  the same for hit lists too large for one
+//                 block: sorted 2048-key segments, then pairwise merges.
 //   k_reset       clears the DHLA and the per-window counters.
 //   k_merge_or    dst |= src over whole DHLAs (multi-monitor merge).
+//   k_*_many      the same kernels over an array of windows of one shape
+//                 (sd_close_many): one launch per phase for all of them.
 //
 // Restore.  The paper's GPU restore (Algorithms 3 and 4) joins HE(0) x HE(1)
 // x HE(2) and extends the surviving partial addresses row by row.  Here the
