@@ -965,11 +965,10 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
         c.keys[d] = h->hits_h + (uint64_t)d * kSortSmall;
         if (!h->st_h->big_sort[d]) continue;
         unsigned long long *sorted = nullptr;
+        int nl = 0;
         SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp + (uint64_t)d * h->hits_cap,
-                                 c.nh[d], h->num_sms, h->stream, &sorted));
-        uint64_t rounds = 0;
-        for (uint64_t L = kSortSmall; L < c.nh[d]; L <<= 1) rounds++;
-        launched(1 + rounds);
+                                 c.nh[d], h->num_sms, h->stream, &sorted, &nl));
+        launched(nl);
         if (!h->big_h) SD_CK(h, cudaMallocHost(&h->big_h, (uint64_t)2 * h->hits_cap * 8));
         unsigned long long *dst = h->big_h + (uint64_t)d * h->hits_cap;
         SD_CK(h, cudaMemcpyAsync(dst, sorted, c.nh[d] * 8, cudaMemcpyDeviceToHost, h->stream));

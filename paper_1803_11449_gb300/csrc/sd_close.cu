@@ -430,6 +430,36 @@ __global__ void k_merge_rank(const unsigned long long *__restrict__ src, unsigne
     }
 }
 
+// Merge all sorted segments of 2048 keys at once: a key's place in the
+// output is its index in its own segment plus, for every other segment, the
+// number of keys below it there (keys are distinct).  One launch instead of
+// log2(segments) pairwise passes, for a few dozen segments at most.
+constexpr uint32_t kMergeAllMaxSegs = 32;
+
+__global__ void k_merge_all(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst,
+                            uint64_t n) {
+    const uint32_t nseg = (uint32_t)((n + kSortSmall - 1) / kSortSmall);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long key = src[i];
+        const uint32_t own = (uint32_t)(i / kSortSmall);
+        uint64_t pos = i - (uint64_t)own * kSortSmall;
+        for (uint32_t t = 0; t < nseg; t++) {
+            if (t == own) continue;
+            uint64_t lo = (uint64_t)t * kSortSmall;
+            uint64_t hi = lo + kSortSmall < n ? lo + kSortSmall : n;
+            const uint64_t base = lo;
+            while (lo < hi) {
+                const uint64_t mid = lo + (hi - lo) / 2;
+                if (src[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            pos += lo - base;
+        }
+        dst[pos] = key;
+    }
+}
+
 // ------------------------------------------------------------ reset/merge
 __device__ __forceinline__ void reset_body(uint4 *grid4, uint64_t n4, StatBlock *st, uint32_t bx, uint32_t nbx) {
     const uint64_t stride = (uint64_t)nbx * blockDim.x;
@@ -678,16 +708,24 @@ cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatB
 // Sort keys[0, n) ascending (distinct keys) with `tmp` as scratch of the
 // same size; *out points at whichever of the two holds the result.
 cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
-                            cudaStream_t s, unsigned long long **out) {
+                            cudaStream_t s, unsigned long long **out, int *launches) {
     const int smem = kSortSmall * (int)sizeof(unsigned long long);
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_sort_segments), 1024, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t segs = (n + kSortSmall - 1) / kSortSmall;
     k_sort_segments<<<(unsigned)segs, 1024, smem, s>>>(keys, n);
+    *launches = 1;
+    if (segs <= kMergeAllMaxSegs) {
+        k_merge_all<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(keys, tmp, n);
+        *launches = 2;
+        *out = tmp;
+        return cudaGetLastError();
+    }
     unsigned long long *a = keys, *b = tmp;
     for (uint64_t L = kSortSmall; L < n; L <<= 1) {
         k_merge_rank<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(a, b, n, L);
+        ++*launches;
         unsigned long long *t = a;
         a = b;
         b = t;

@@ -213,7 +213,7 @@ cudaError_t launch_join(const Geometry &G, const JoinArgs &J, int num_sms, cudaS
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s);
 cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
-                            cudaStream_t s, unsigned long long **out);
+                            cudaStream_t s, unsigned long long **out, int *launches);
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);

@@ -353,12 +353,13 @@ def test_report_cap_truncates_in_order(sd, O, torch_mod):
     assert np.array_equal(rep.hits["est"], ref["est"][:17])
 
 
-def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod):
-    """A DHLA where ~4.7% of the estimators of each row are full: |K| is about
-    p^4 2^32 (tens of thousands), every candidate has SZ = 0 and is reported,
-    more than one block sorts."""
+@pytest.mark.parametrize("p_full,least", [(0.0465, 8192), (0.066, 65536)])
+def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod, p_full, least):
+    """A DHLA where a fraction p of the estimators of each row are full: |K|
+    is about p^4 2^32, every candidate has SZ = 0 and is reported, and more
+    than one block sorts: up to 32 sorted segments merge in one pass, more
+    in pairwise passes."""
     w = T.WORKLOADS["core"].with_(dirs=1, g=256)
-    p_full = 0.0465
     rng = np.random.default_rng(12)
     cells = rng.random((w.r, 1 << w.k)) < p_full
     grid = np.zeros((w.r, 1 << w.k, w.g // 32), dtype=np.uint32)
@@ -375,7 +376,7 @@ def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod):
         sd.sd_destroy(h)
     op = O.params_from(w.sketch(), seed=SEED, cand_cap=1 << 17)
     ref = O.close_window(op, grid)
-    assert ref["n_hits"] > 8192
+    assert ref["n_hits"] > least
     _assert_report_equal(O, rep, ref, p)
 
 
