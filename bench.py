@@ -746,7 +746,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
-    ap.add_argument("--ref-sample", type=int, default=1 << 22)
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="pairs per reference step (default: 2^22, fewer for long runs so that the "
+                         "reference arm stays within a few minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairs", type=int, default=None,
                     help="pairs per window (default: the workload's 2^26); profiling only")
@@ -781,6 +783,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if not args.ref_sample:
+        # about a second of oracle work per step up to 50 steps, then shorter steps
+        args.ref_sample = 1 << 22
+        while args.ref_sample > (1 << 18) and args.ref_sample * (args.steps + args.warmup) > 55 * (1 << 22):
+            args.ref_sample >>= 1
     global TRAFFIC, WORKLOAD, WORKLOAD_DESC
     TRAFFIC = args.traffic
     if not (args.batching or args.serving):
