@@ -19,8 +19,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "sd_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# SD_ORACLE_SRC builds the oracle from another copy of the C source instead:
+# the mutation tests plant one mistake in a copy and run the pins against it.
+_SRC = os.environ.get("SD_ORACLE_SRC") or os.path.join(_HERE, "sd_oracle.c")
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(_SRC)), "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -53,7 +53,9 @@
  * single-key linear-counting closed form; order/duplicate/split invariance of
  * Algorithm 1; psi in closed form for constructed grids; Eq. 4 special cases;
  * the three restore routines agree; the restored set equals an exhaustive
- * sweep of the key space; planted keys with cardinality >= 2 theta are found.
+ * sweep of the key space; planted keys with cardinality >= 2 theta are found;
+ * SZ of hand-built estimators (Definition 1).  Copies of this file with one
+ * planted mistake each must fail at least one pin (the mutation tests).
  * The estimate's value beyond Eq. 4's special cases is "parity unpinned":
  * the paper prints no worked example.
  */

@@ -19,6 +19,7 @@ CONFIGS = [  # (g, r, k, alpha)
     (1024, 4, 18, 7),   # stress
     (64, 3, 16, 16),    # alpha = k: no overlap between blocks
     (128, 6, 10, 6),    # (r-2)alpha + k > 32: last block runs past bit 31
+    (64, 8, 8, 6),      # the last block starts at bit 36: Eq. 2's shift leaves nothing
 ]
 
 
@@ -111,14 +112,20 @@ def test_dh_rows_are_uniform(O, g, r, k, alpha):
 
 
 def test_h1_is_uniform_over_g_bits(O):
+    """§3.2: H1 spreads a host's peers uniformly over the g bits of an
+    estimator, also when the peers are structured the way addresses are:
+    one subnet (only the low bits differ) or one host number in many
+    networks (only the high bits differ)."""
     for g in (256, 512, 1024):
         p = O.make_params(g, 4, 16, 8, 1024.0, seed=3)
         rng = np.random.default_rng(g)
-        ys = rng.integers(0, 2**32, size=60000, dtype=np.uint64)
-        bits = np.array([O.h1(p, 0, int(y)) for y in ys])
-        assert bits.min() >= 0 and bits.max() < g
-        counts = np.bincount(bits * 16 // g, minlength=16)
-        assert stats.chisquare(counts).pvalue > 1e-6
+        for ys in (rng.integers(0, 2**32, size=60000, dtype=np.uint64),
+                   0x0A000000 + np.arange(60000, dtype=np.uint64),
+                   (np.arange(60000, dtype=np.uint64) << np.uint64(16)) | np.uint64(0x0101)):
+            bits = np.array([O.h1(p, 0, int(y)) for y in ys])
+            assert bits.min() >= 0 and bits.max() < g
+            counts = np.bincount(bits * 16 // g, minlength=16)
+            assert stats.chisquare(counts).pvalue > 1e-6
 
 
 def test_parameter_restrictions(O):

@@ -109,3 +109,28 @@ def test_directions_key_on_src_and_dst(O):
     # inbound: every peer is a distinct dst host with a single src -> 1 bit each
     in_pop = np.unpackbits(cells[1].view(np.uint8)).reshape(p.r, -1).sum(axis=1)
     assert in_pop.max() <= 3000 and in_pop.min() > 2800
+
+
+def test_sz_counts_zeros_of_the_and(O):
+    """§3.2, Definition 1: ULE(a0) is the bitwise AND of a0's r estimators
+    and SZ(a0) its number of zero bits.  Estimators built here by hand: a
+    common set of 100 bits in all r, plus bits of their own in each row (and
+    a neighbour estimator full), so the AND keeps exactly the common 100."""
+    p = O.make_params(512, 4, 16, 8, 1024.0, seed=31)
+    a0 = 0x0A0B0C0D
+    bits = np.zeros((p.r, 1 << p.k, p.g), dtype=np.uint8)
+    common = np.arange(3, 503, 5)  # 100 bits
+    for i in range(p.r):
+        j = O.dh(p, 0, i, a0)
+        bits[i, j, common] = 1
+        bits[i, j, (common + 1 + i) % p.g] = 1   # row-specific bits
+        bits[i, (j + 1) % (1 << p.k), :] = 1     # a full neighbour estimator
+    grid = np.packbits(bits, axis=2, bitorder="little").view(np.uint32).reshape(-1).copy()
+    assert O.sz(p, grid, 0, a0) == p.g - 100
+    # a host none of whose estimators share a bit with a0's: SZ = g unless
+    # it lands on a0's or a neighbour's estimator in every row
+    b0 = 0x01020304
+    cells = [O.dh(p, 0, i, b0) for i in range(p.r)]
+    if all(bits[i, c].sum() == 0 for i, c in enumerate(cells)):
+        assert O.sz(p, grid, 0, b0) == p.g
+
