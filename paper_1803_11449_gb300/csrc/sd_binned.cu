@@ -107,18 +107,32 @@ struct TileSrc {
     DirHash H;
 };
 
+// Where a tile's sorted entries of one slice go: sorted entry q is written
+// to dst + q while q < lim (the rest of the slice's run did not fit its bin).
+struct Slot {
+    uint32_t *dst;
+    uint32_t lim;
+    uint32_t pad;
+};
+
+// Slice qg (q within the tile's link) got bin positions b0, b0+1, ... for
+// its sorted entries run, run+1, ...: entry run + i goes to bins[qg][b0 + i]
+// while b0 + i < cap.
+__device__ __forceinline__ void set_slot(Slot *slot, const BinArgs &B, uint32_t qg, uint32_t q, uint32_t b0,
+                                         uint32_t run) {
+    Slot sq;
+    sq.dst = B.bins + (uint64_t)qg * B.cap + b0 - run;
+    sq.lim = b0 < B.cap ? run + (B.cap - b0) : run;
+    sq.pad = 0;
+    slot[q] = sq;
+}
+
 template <int R, int DIRS, int PPT>
 __global__ void __launch_bounds__(512)
 k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ grid, Geometry G, BinArgs B,
       uint32_t lwpc, const LinkDesc *__restrict__ links, uint32_t nlinks, uint64_t ntiles_all, uint32_t SL) {
     constexpr int UPT = PPT * DIRS * R;  // bit-sets per thread per tile
     extern __shared__ uint32_t sm[];
-    // per slice: destination of sorted entry q is dst + q while q < lim
-    struct Slot {
-        uint32_t *dst;
-        uint32_t lim;
-        uint32_t pad;
-    };
     // indexed by the slice within the tile's link: a tile only touches the
     // SL slices of its own link
     Slot *slot = reinterpret_cast<Slot *>(sm);           // [SL], 16-byte aligned
@@ -201,12 +215,28 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             bin_hash<R, DIRS, PPT, false>(G, ts.H, base5, cshift, kmask, sl5, ts.slice0, src, dst, ok, hist, ent,
                                           met);
         __syncthreads();
-        // exclusive scan of hist into offs; reserve each slice's run in its bin
+        // reserve each slice's run in its bin and scan hist into offs.  With
+        // at most two slices per thread the reservations are issued first and
+        // their results used only after the scatter, so the atomics' round
+        // trip to L2 overlaps the scatter.
+        uint32_t rb0[2], rrun[2], ds0 = 0, ds1 = 0;
+        bool early = false;
         {
             const uint32_t per = (SL + blockDim.x - 1) / blockDim.x;
             const uint32_t s0 = min(threadIdx.x * per, SL), s1 = min(s0 + per, SL);
+            early = per <= 2;
+            ds0 = s0;
+            ds1 = s1;
             uint32_t cnt = 0;
-            for (uint32_t q = s0; q < s1; q++) cnt += hist[q];
+            if (early) {
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const uint32_t q = s0 + j;
+                    if (q < s1) cnt += hist[q];
+                }
+            } else {
+                for (uint32_t q = s0; q < s1; q++) cnt += hist[q];
+            }
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -226,20 +256,26 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             }
             __syncthreads();
             uint32_t run = incl - cnt + (wid ? warp_tot[wid - 1] : 0);
-            for (uint32_t q = s0; q < s1; q++) {
-                const uint32_t hq = hist[q];
-                offs[q] = run;
-                if (hq) {
-                    const uint32_t qg = ts.slice0 + q;  // slice in this launch
-                    const uint32_t b0 = atomicAdd(&B.count[qg], hq);
-                    // entries q' = run + k go to bins[qg][b0 + k] while b0 + k < cap
-                    Slot sq;
-                    sq.dst = B.bins + (uint64_t)qg * B.cap + b0 - run;
-                    sq.lim = b0 < B.cap ? run + (B.cap - b0) : run;
-                    sq.pad = 0;
-                    slot[q] = sq;
+            if (early) {
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const uint32_t q = s0 + j;
+                    rrun[j] = run;
+                    rb0[j] = 0;
+                    if (q < s1) {
+                        const uint32_t hq = hist[q];
+                        offs[q] = run;
+                        if (hq) rb0[j] = atomicAdd(&B.count[ts.slice0 + q], hq);
+                        run += hq;
+                    }
                 }
-                run += hq;
+            } else {
+                for (uint32_t q = s0; q < s1; q++) {
+                    const uint32_t hq = hist[q];
+                    offs[q] = run;
+                    if (hq) set_slot(slot, B, ts.slice0 + q, q, atomicAdd(&B.count[ts.slice0 + q], hq), run);
+                    run += hq;
+                }
             }
         }
         __syncthreads();
@@ -247,6 +283,13 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
 #pragma unroll
         for (int u = 0; u < UPT; u++)
             if (full || ok[u / (DIRS * R)]) sorted[offs[(ent[u] >> 20) - ts.slice0] + met[u]] = ent[u];
+        if (early) {
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const uint32_t q = ds0 + j;
+                if (q < ds1 && hist[q]) set_slot(slot, B, ts.slice0 + q, q, rb0[j], rrun[j]);
+            }
+        }
         __syncthreads();
         // write-out, one thread per entry; full bins fall back to red.or
         const uint64_t left = ts.n - ts.tile * TP;
@@ -255,7 +298,7 @@ k_bin(const uint32_t *__restrict__ pairs, uint64_t n, uint32_t *__restrict__ gri
             const uint32_t e = sorted[q];
             const Slot sq = slot[(e >> 20) - ts.slice0];
             if (q < sq.lim) {
-                sq.dst[q] = e;
+                __stcs(sq.dst + q, e);  // evict-first: keeps the bin counters and the DHLA in L2
             } else {
                 const uint32_t w = (((e >> 20) - ts.slice0) << sl) | ((e & 0xFFFFFu) >> 5);
                 red_or(ts.grid + w, 1u << (e & 31u));

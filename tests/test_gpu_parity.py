@@ -256,6 +256,7 @@ def test_stress_sketch_beyond_l2(sd, O, torch_mod):
     (32, 8, 8, 4, 40, 6000, 1 << 10, 2, (120, 200)),       # one word per estimator, the most rows,
                                                            # 256 estimators, 2^16 preimages per (c0, c1)
     (64, 6, 10, 6, 80, 40_000, 1 << 12, 3, (250, 400)),
+    (32, 8, 8, 6, 40, 6000, 1 << 10, 2, (120, 200)),       # the last block starts at bit 36 (empty)
     (4096, 3, 16, 16, 1024, 1 << 18, 1 << 15, 6, (3072, 6144)),  # 128 words per estimator, blocks
                                                                  # that do not overlap
     (32, 3, 24, 8, 40, 1 << 18, 1 << 16, 6, (120, 240)),   # 2^24 estimators: 3 x 64 MiB per direction,
