@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sd.h"
 #include "sd_common.cuh"
 
@@ -33,6 +35,16 @@ thread_local std::string g_create_error;
 std::atomic<uint64_t> g_launches{0};  // kernels launched by this library, all handles
 
 void launched(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// An NVTX range over one entry point, so that profilers can attribute and
+// filter the kernels of an update, a close or a merge (a no-op when no tool
+// is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // splitmix64 (Steele, Lea, Flood 2014): the published generator.
 uint64_t splitmix64(uint64_t *state) {
@@ -565,6 +577,7 @@ static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
 }
 
 int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+    NvtxRange nvtx("sd_update");
     if (!h) return SD_ERR_ARG;
     if (n == 0) return SD_OK;
     if (!pairs) return h->fail(SD_ERR_ARG, "sd_update: pairs is NULL");
@@ -671,6 +684,7 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
 }
 
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count) {
+    NvtxRange nvtx("sd_update_many");
     if (!count) return SD_OK;
     if (!hs || !pairs || !ns) return SD_ERR_ARG;
     for (uint32_t i = 0; i < count; i++)
@@ -1040,6 +1054,7 @@ static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
 static bool rc_is_error(int rc) { return rc == SD_ERR_ARG || rc == SD_ERR_NOMEM || rc == SD_ERR_CUDA; }
 
 int sd_close_window(sd_handle *h, sd_report *out) {
+    NvtxRange nvtx("sd_close_window");
     if (!h || !out) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
     CloseTrace trace;
@@ -1205,6 +1220,7 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
 }
 
 int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rcs) {
+    NvtxRange nvtx("sd_close_many");
     if (!hs || !outs || !rcs) return count ? SD_ERR_ARG : SD_OK;
     for (uint32_t i = 0; i < count; i++)
         if (!hs[i]) return SD_ERR_ARG;
@@ -1343,6 +1359,7 @@ int64_t sd_get_candidates(sd_handle *h, uint32_t dir, uint32_t *host_dst, uint64
 }
 
 int sd_merge(sd_handle *dst, sd_handle *src) {
+    NvtxRange nvtx("sd_merge");
     if (!dst || !src || dst == src) return SD_ERR_ARG;
     const sd_params &a = dst->p, &b = src->p;
     if (a.g != b.g || a.r != b.r || a.k != b.k || a.alpha != b.alpha || a.seed != b.seed || a.dirs != b.dirs ||
