@@ -80,6 +80,16 @@ def profiled_traffic(mode: int, n: int):
     return float(fields["dram_bytes_per_pair"]) * n
 
 
+def ref_sample_for(steps: int, warmup: int) -> int:
+    """Pairs per step of the reference arm: 2^22 (about a second of oracle
+    work) while the whole run stays near 55 such samples, then halved down to
+    2^18, so that long runs still end within a few minutes."""
+    sample = 1 << 22
+    while sample > (1 << 18) and sample * (steps + warmup) > 55 * (1 << 22):
+        sample >>= 1
+    return sample
+
+
 def l2_reduction_ceiling():
     """Random L2 reductions per second measured on this GPU (the in-place
     update's bound), from the committed ncu summary of k_update mode 0 on
@@ -812,10 +822,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if not args.ref_sample:
-        # about a second of oracle work per step up to 50 steps, then shorter steps
-        args.ref_sample = 1 << 22
-        while args.ref_sample > (1 << 18) and args.ref_sample * (args.steps + args.warmup) > 55 * (1 << 22):
-            args.ref_sample >>= 1
+        args.ref_sample = ref_sample_for(args.steps, args.warmup)
     global TRAFFIC, WORKLOAD, WORKLOAD_DESC
     TRAFFIC = args.traffic
     if not (args.batching or args.serving):

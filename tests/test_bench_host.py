@@ -49,3 +49,17 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "Gpps" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_sample_bounds_the_run():
+    """The reference arm's default sample keeps a run of --steps K near 55
+    samples of 2^22 pairs (a few minutes of oracle work), never below 2^18."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.ref_sample_for(5, 5) == 1 << 22
+    assert bench.ref_sample_for(50, 5) == 1 << 22
+    for steps in (100, 200, 1000, 10_000):
+        s = bench.ref_sample_for(steps, 5)
+        assert (1 << 18) <= s < (1 << 22)
+        assert s * (steps + 5) <= 55 * (1 << 22) or s == 1 << 18
+
