@@ -96,8 +96,6 @@ def lib():
                                                       _u32p, ctypes.c_uint64]),
                 "or_restore_preimage": (ctypes.c_uint64, [_P(Params), ctypes.c_uint32, _u32p,
                                                           _u32p, _u32p, ctypes.c_uint64]),
-                "or_restore_brute": (ctypes.c_uint64, [_P(Params), ctypes.c_uint32, _u32p, _u32p,
-                                                       _u32p, ctypes.c_uint64]),
                 "or_close_window": (ctypes.c_uint64, [_P(Params), _u32p, _P(Summary), _u32p,
                                                       _u32p, _u32p, _f64p, ctypes.c_uint64,
                                                       _u32p]),
@@ -226,10 +224,6 @@ def restore_join(p, direction, he, nhe, cap=1 << 22):
 
 def restore_preimage(p, direction, he, nhe, cap=1 << 22):
     return _restore(lib().or_restore_preimage, p, direction, he, nhe, cap)
-
-
-def restore_brute(p, direction, he, nhe, cap=1 << 22):
-    return _restore(lib().or_restore_brute, p, direction, he, nhe, cap)
 
 
 def close_window(p: Params, grid: np.ndarray, hit_cap: int = 1 << 20, want_cands: bool = False):

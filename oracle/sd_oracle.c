@@ -22,8 +22,9 @@
  *   or_restore_join .................... the tuple join of Algorithm 2, in the
  *                                        staged form of Algorithms 3 and 4
  *   or_restore_preimage ................ same set, by enumerating DH_0 preimages
- *   or_restore_brute ................... same set, by sweeping all 2^32 keys
  *   or_close_window .................... Algorithm 2 end to end + §4.2 report
+ *   or_report_brute .................... K and the report by definition, sweeping
+ *                                        all 2^32 keys
  *
  * Readings of points the paper leaves open (each also recorded in the
  * project's design notes):
@@ -420,27 +421,6 @@ uint64_t or_restore_preimage(const or_params *p, uint32_t dir, const uint32_t *h
     free(hot);
     if (count <= cap) qsort(out, count, sizeof(uint32_t), cmp_u32);
     return count;
-}
-
-/* Same set K by definition: every a in [0, 2^32) with DH_i(a) in HE(i) for
- * all i. */
-uint64_t or_restore_brute(const or_params *p, uint32_t dir, const uint32_t *he, const uint32_t *nhe,
-                          uint32_t *out, uint64_t cap)
-{
-    uint32_t ncell = 1u << p->k;
-    uint64_t count = 0;
-    or_hash h;
-    uint8_t *hot = hot_bitmap(p, he, nhe);
-    if (!hot) return UINT64_MAX;
-    make_hash(p, &h);
-    for (uint64_t a = 0; a < ((uint64_t)1 << 32); a++) {
-        int all = 1;
-        for (uint32_t i = 0; i < p->r && all; i++)
-            all = hot[(uint64_t)i * ncell + dh(h.A0[dir], p->k, p->alpha, i, (uint32_t)a)];
-        if (all) emit(out, cap, &count, (uint32_t)a);
-    }
-    free(hot);
-    return count; /* ascending by construction */
 }
 
 /* ----------------------------------------------------------- close window */

@@ -144,6 +144,29 @@ def test_every_host_restores_to_itself(O, g, r, k, alpha):
         assert all(O.dh(p, 0, i, int(a)) in hot[i] for i in range(p.r))
 
 
+def test_join_stops_at_bit_31(O):
+    """Algorithm 3 joins BL(1) and the new bits of BL(2) into bits [0, k +
+    alpha) of a0.  With k + alpha > 32, a tuple whose BL(2) sets a bit at or
+    above 32 names no IPv4 address and restores nothing; cut to 32 bits it
+    would name a host whose row-2 estimator is not hot.  Hand-built hot sets
+    around one host a: its own CL_0 and CL_1, and in row 2 such a tuple's
+    estimator, a's own, or both."""
+    p = O.make_params(64, 3, 20, 16, 1024.0, seed=77)
+    assert O.check_params(p)
+    a = 0xC0A81234
+    c0, c1, c2 = (O.dh(p, 0, i, a) for i in range(3))
+    past_31 = c0 ^ (((a >> 16) & 0xFFFF) | (0x5 << 16))  # BL(2) with bits 32-35 set
+    assert past_31 != c2
+    he = np.zeros((p.r, 1 << p.k), dtype=np.uint32)
+    he[0, 0], he[1, 0] = c0, c1
+    for row2, expect in (([past_31], []), ([c2], [a]), (sorted([past_31, c2]), [a])):
+        he[2, :len(row2)] = row2
+        nhe = np.array([1, 1, len(row2)], dtype=np.uint32)
+        _, kj = O.restore_join(p, 0, he, nhe)
+        _, kp = O.restore_preimage(p, 0, he, nhe)
+        assert kj.tolist() == kp.tolist() == expect
+
+
 @pytest.mark.slow
 def test_restore_and_report_equal_exhaustive_sweep(O):
     """The restored set K equals {a in [0, 2^32) : DH_i(a) in HE(i) for all i}

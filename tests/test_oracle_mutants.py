@@ -92,6 +92,49 @@ MUTANTS = {
         ("if (zr[i] == 0) return -1.0;", "if (zr[i] == 0) continue;")]),
     "overload-cap-off-by-one": ("pair_cap bounds |HE(0)| |HE(1)|", [
         ("(uint64_t)sum->n_hot[dir][1] > p->pair_cap)", "(uint64_t)sum->n_hot[dir][1] > p->pair_cap + 1u)")]),
+    "cand-cap-off-by-one": ("cand_cap bounds |K|", [
+        ("if (nk > kcap) { sum->flags[dir] |= OR_FLAG_OVERLOAD_CANDS; continue; }",
+         "if (nk >= kcap) { sum->flags[dir] |= OR_FLAG_OVERLOAD_CANDS; continue; }")]),
+    "update-break-not-continue": ("Algorithm 1: a bit already set skips only its own row", [
+        ("if ((LEp[BITidx >> 5] >> (BITidx & 31u)) & 1u) continue;",
+         "if ((LEp[BITidx >> 5] >> (BITidx & 31u)) & 1u) break;")]),
+    "h1-hashes-the-key": ("Algorithm 1: the bit comes from the peer", [
+        ("uint32_t BITidx = or_h1(h.A1[dir], h.B1[dir], p->g, b0);",
+         "uint32_t BITidx = or_h1(h.A1[dir], h.B1[dir], p->g, a0);")]),
+    "inbound-hashes-dst": ("direction 1 counts a destination's sources", [
+        ("uint32_t b0 = dir == 0 ? dst : src;", "uint32_t b0 = dst;")]),
+    "row-stats-reads-row-0": ("z_0 of every row's own estimators", [
+        ("uint32_t z = p->g - weight(cell_ptr(p, (uint32_t *)grid, dir, i, j), p->g);",
+         "uint32_t z = p->g - weight(cell_ptr(p, (uint32_t *)grid, dir, 0, j), p->g);")]),
+    "zr-keeps-last-estimator": ("ZR(i) sums z_0 over the row", [("            zr[i] += z;", "            zr[i] = z;")]),
+    "hot-sets-read-row-0": ("HE(i) from row i's z_0", [
+        ("if ((double)z0[(uint64_t)i * ncell + j] < Zmin) he[(uint64_t)i * ncell + nhe[i]++] = j;",
+         "if ((double)z0[j] < Zmin) he[(uint64_t)i * ncell + nhe[i]++] = j;")]),
+    "zmin-theta-over-2g": ("Zmin = g e^(-theta/g)", [
+        ("return (double)g * exp(-theta / (double)g);", "return (double)g * exp(-theta / (2.0 * (double)g));")]),
+    "psi-log-inverted": ("w(i)' = -g 2^k ln(ZR(i) / (g 2^k))", [
+        ("wi = -G * log((double)zr[i] / G);", "wi = -G * log(G / (double)zr[i]);")]),
+    "psi-first-row-only": ("w' averages all r rows", [
+        ("        wsum += wi;", "        wsum += (i == 0) ? wi * p->r : 0.0;")]),
+    "eq4-sz-off-by-one": ("Eq. 4 takes SZ itself", [
+        ("return -gd * log((double)sz / (", "return -gd * log((double)(sz + 1u) / (")]),
+    "sz-half-the-words": ("SZ over all g bits of ULE", [
+        ("    for (uint32_t q = 0; q < p->g / 32u; q++) {\n        uint32_t ule",
+         "    for (uint32_t q = 0; q < p->g / 64u; q++) {\n        uint32_t ule")]),
+    "join-mask-one-bit-wide": ("Algorithm 3: overlaps of k - alpha bits", [
+        ("uint32_t ovmask = (ov == 32u) ? 0xFFFFFFFFu : ((1u << ov) - 1u);",
+         "uint32_t ovmask = (ov == 32u) ? 0xFFFFFFFFu : ((2u << ov) - 1u);")]),
+    "join-stage-overlap-index": ("Algorithm 4: BL(i) overlaps the partial from bit (i-1) alpha", [
+        ("uint32_t top = (i - 1u) * al;", "uint32_t top = (i - 2u) * al;")]),
+    "join-wraps-past-bit-31": ("Algorithm 3: a0 has 32 bits", [
+        ("else { if (k + al > 32u && (add >> (32u - k))) continue; hi = add << k; }",
+         "else { hi = add << k; }")]),
+    "join-stage-wraps-past-bit-31": ("Algorithm 4: a0 has 32 bits", [
+        ("else { if (pos + al > 32u && (add >> (32u - pos))) continue; hi = add << pos; }",
+         "else { hi = add << pos; }")]),
+    "preimage-skips-row-1": ("K needs every row hot", [
+        ("for (uint32_t i = 1; i < p->r && all; i++)\n                all = hot[(uint64_t)i * ncell + dh(h.A0[dir], k, p->alpha, i, a)];",
+         "for (uint32_t i = 2; i < p->r && all; i++)\n                all = hot[(uint64_t)i * ncell + dh(h.A0[dir], k, p->alpha, i, a)];")]),
 }
 
 
