@@ -144,6 +144,34 @@ def test_every_host_restores_to_itself(O, g, r, k, alpha):
         assert all(O.dh(p, 0, i, int(a)) in hot[i] for i in range(p.r))
 
 
+def test_restore_routines_agree_across_parameter_space(O):
+    """§3.3 allows any r >= 3 and alpha with alpha <= k and (r-2) alpha + k
+    >= 32.  For seeded random parameter sets across that space (not only the
+    default alpha), the staged join and the preimage enumeration return the
+    same K, which holds every host whose estimators were made hot, and every
+    member of K has all r estimators hot."""
+    rng = np.random.default_rng(2018)
+    done = 0
+    while done < 16:
+        r = int(rng.integers(3, 9))
+        k = int(rng.integers(14, 21))
+        lo = -(-(32 - k) // (r - 2))
+        if lo > k:
+            continue
+        alpha = int(rng.integers(max(1, lo), k + 1))
+        p = O.make_params(64, r, k, alpha, 1024.0, seed=int(rng.integers(1 << 62)))
+        assert O.check_params(p), (r, k, alpha)
+        P = rng.choice(2**32, size=8, replace=False)
+        he, nhe = _hot_from_keys(O, p, P, extra=12, seed=done)
+        hot = [set(he[i, :nhe[i]].tolist()) for i in range(p.r)]
+        _, kj = O.restore_join(p, 0, he, nhe)
+        _, kp = O.restore_preimage(p, 0, he, nhe)
+        assert np.array_equal(kj, kp), (r, k, alpha)
+        assert set(P.tolist()) <= set(kj.tolist())
+        assert all(O.dh(p, 0, i, int(a)) in hot[i] for a in kj for i in range(p.r))
+        done += 1
+
+
 def test_join_stops_at_bit_31(O):
     """Algorithm 3 joins BL(1) and the new bits of BL(2) into bits [0, k +
     alpha) of a0.  With k + alpha > 32, a tuple whose BL(2) sets a bit at or
