@@ -190,7 +190,10 @@ class Server:
 
     def attach_ring(self, link_id, ring) -> None:
         """Make a device tensor of 2R 4-byte words (R pairs) the link's
-        input ring; the producer writes pair j to slot j mod R."""
+        input ring; the producer writes pair j to slot j mod R.  A slot is
+        free again once a step has enqueued the update that reads it, so the
+        producer writes on the engine's stream (`Server.stream`, where the
+        batched updates run) or orders its writes after that stream."""
         if ring.numel() % 2 or not ring.numel():
             raise ValueError("a ring holds a positive number of (src, dst) pairs")
         L = self.links[link_id]
