@@ -159,7 +159,7 @@ class Server:
         L = self.links[link_id]
         out = None
         if L.h is not None:
-            while L.closing:
+            while L.closing and self._closing:
                 self._collect(block=True)
             while L.has_work():
                 self._feed([link_id], flush=True)
@@ -167,15 +167,21 @@ class Server:
                 reps, close_s, done_at = self._close_now([L.h])
                 out = WindowReport(link_id, L.window, reps[0], close_s, done_at, L.last_arrival)
                 self.reports.append(out)
+        self._release(link_id)
+        return out
+
+    def _release(self, link_id) -> None:
+        """Free the link's handle (if admitted) or its place in the queue,
+        forget the link and admit waiting links."""
+        L = self.links.pop(link_id)
+        if L.h is not None:
             sd.sd_destroy(L.h)
             L.h = None
             del self.admitted[link_id]
             self.used -= self.link_bytes()
         else:
             self.waiting.remove(link_id)
-        del self.links[link_id]
         self._admit_waiting()
-        return out
 
     # --------------------------------------------------------------- work
     def submit(self, link_id, pairs, arrival: float = 0.0) -> None:
@@ -285,7 +291,15 @@ class Server:
         out = []
         while self._closing and (self._closing[0][0].done() or (block and not out)):
             fut, lids = self._closing.popleft()
-            out += self._finish(lids, *fut.result())
+            try:
+                res = fut.result()
+            except BaseException:
+                # the close failed: its links hold a full window, no longer
+                # closing (a later close of the link tries again)
+                for lid in lids:
+                    self.links[lid].closing = False
+                raise
+            out += self._finish(lids, *res)
         return out
 
     def step(self) -> list[WindowReport]:
@@ -318,16 +332,28 @@ class Server:
 
     def shutdown(self) -> list[WindowReport]:
         """Close every link (admitted links first, then those that get
-        admitted as slots free)."""
-        out = []
+        admitted as slots free) and free every handle.  A close or update
+        that fails does not stop the others: its link is freed without a
+        report, and the first error is raised once everything is freed."""
+        out, err = [], None
         while self._closing:
-            out += self._collect(block=True)
+            try:
+                out += self._collect(block=True)
+            except Exception as e:  # noqa: BLE001 - re-raised below
+                err = err or e
         while self.links:
             lid = next(iter(self.admitted), None)
             if lid is None:
                 self._admit_waiting()
                 lid = next(iter(self.admitted))
-            r = self.close_link(lid)
+            try:
+                r = self.close_link(lid)
+            except Exception as e:  # noqa: BLE001 - re-raised below
+                err = err or e
+                if lid in self.links:
+                    self.links[lid].pending.clear()
+                    self._release(lid)
+                continue
             if r:
                 out.append(r)
         if self.driver is not None:
@@ -335,4 +361,6 @@ class Server:
             self.driver = None
             self.used -= self.fixed
             self._closer.shutdown()
+        if err is not None:
+            raise err
         return out

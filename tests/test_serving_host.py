@@ -161,3 +161,44 @@ def test_server_as_context_manager_releases_everything(fake):
         srv.step()
     assert fake.live == 0 and srv.used == 0 and not srv.links
     assert [len(w) for w in _windows(srv, "a")] == [10, 10, 5]
+
+
+def test_failed_close_raises_and_shutdown_frees_everything(fake):
+    """A close that fails on the closing thread (an error from the library,
+    injected here on the host) is raised by the step that collects it; its
+    links are not left waiting for a close that will never come, and
+    shutdown frees every handle, then raises the first error."""
+    real = fake.sd_close_many
+    calls = {"n": 0}
+
+    def flaky(hs):
+        calls["n"] += 1
+        if calls["n"] == 2:
+            raise RuntimeError("injected close failure")
+        return real(hs)
+
+    fake.sd_close_many = flaky
+    W = 100
+    srv = serving.Server({}, W, hbm_budget=10_000)
+    for lid in ("a", "b"):
+        srv.open_link(lid, seed=1)
+    with pytest.raises(RuntimeError, match="injected"):
+        for k in range(20):
+            for lid in ("a", "b"):
+                srv.submit(lid, torch.from_numpy(_stream(W, k).reshape(-1)))
+            srv.step()
+        srv.drain()
+    assert not any(L.closing for L in srv.links.values())
+    srv.submit("a", torch.from_numpy(_stream(30, 99).reshape(-1)))
+    srv.shutdown()  # the other closes succeed again
+    assert fake.live == 0 and srv.used == 0 and not srv.links
+
+    fake.sd_close_many = lambda hs: (_ for _ in ()).throw(RuntimeError("injected close failure"))
+    srv = serving.Server({}, W, hbm_budget=10_000)
+    for lid in ("a", "b", "c"):
+        srv.open_link(lid, seed=2)
+        srv.submit(lid, torch.from_numpy(_stream(W // 2, 7).reshape(-1)))
+    with pytest.raises(RuntimeError, match="injected"):
+        srv.shutdown()
+    assert fake.live == 0 and srv.used == 0 and not srv.links and srv.driver is None
+
