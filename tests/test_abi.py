@@ -78,3 +78,36 @@ def test_create_rejects_invalid_parameters_without_touching_a_gpu(sdmod):
         sdmod.sd_create(p)
     assert e.value.code == sdmod.SD_ERR_ARG
     assert "invalid parameters" in sdmod.sd_last_error(None)
+
+
+def test_entry_points_reject_null_arguments_without_touching_a_gpu(sdmod):
+    """The header's error contract for missing arguments: every entry point
+    that takes a handle or a buffer returns SD_ERR_ARG for NULL (a NULL
+    handle to sd_destroy is a no-op, an empty batch is SD_OK) before any
+    CUDA call, so the checks hold on a machine without a GPU."""
+    L = sdmod.lib()
+    ARG, OK = sdmod.SD_ERR_ARG, sdmod.SD_OK
+    buf = (ctypes.c_uint32 * 64)()
+    rep = sdmod.sd_report()
+    tun = sdmod.sd_tuning()
+    assert L.sd_update(None, buf, 1) == ARG
+    assert L.sd_close_window(None, ctypes.byref(rep)) == ARG
+    assert L.sd_sync(None) == ARG
+    assert L.sd_destroy(None) == OK
+    assert L.sd_get_grid(None, 0, buf) == ARG
+    assert L.sd_set_grid(None, 0, buf) == ARG
+    assert L.sd_get_hot(None, 0, 0, buf) == ARG
+    assert L.sd_get_candidates(None, 0, buf, 64) == ARG
+    assert L.sd_merge(None, None) == ARG
+    assert L.sd_get_tuning(None, ctypes.byref(tun)) == ARG
+    assert L.sd_set_tuning(None, ctypes.byref(tun)) == ARG
+    assert L.sd_scratch_bytes(None, 1) == 0
+    assert L.sd_check_params(None) == ARG
+    assert L.sd_update_many(None, None, None, 0) == OK
+    assert L.sd_update_many(None, None, None, 2) == ARG
+    assert L.sd_close_many(None, 0, None, None) == OK
+    assert L.sd_close_many(None, 2, None, None) == ARG
+    p = sdmod.sd_default_params()
+    assert L.sd_update_noalloc(ctypes.byref(p), None, buf, 1, None) == ARG  # no DHLA
+    assert L.sd_update_noalloc(None, buf, buf, 1, None) == ARG              # no parameters
+    assert isinstance(L.sd_last_error(None), bytes)
