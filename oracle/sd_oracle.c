@@ -57,8 +57,9 @@
  * sweep of the key space; planted keys with cardinality >= 2 theta are found;
  * SZ of hand-built estimators (Definition 1).  Copies of this file with one
  * planted mistake each must fail at least one pin (the mutation tests).
- * The estimate's value beyond Eq. 4's special cases is "parity unpinned":
- * the paper prints no worked example.
+ * Eq. 4 is pinned by its special cases and by inverting Theorem 1's
+ * expected zero count for random g, r, c and psi (the paper prints no worked
+ * example).
  */
 #include <math.h>
 #include <stdint.h>

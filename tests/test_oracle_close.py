@@ -89,6 +89,28 @@ def test_eq4_special_cases(O):
     assert all(a > b for a, b in zip(vals, vals[1:]))
 
 
+def test_eq4_inverts_the_expected_zero_count(O):
+    """Theorem 1's model: a host with c peers keeps a bit of ULE at zero when
+    none of its c peers hashed there ((1 - 1/g)^c) and the bit is not set in
+    all r estimators by other hosts (1 - psi^r), so E[SZ] = g (1 - 1/g)^c
+    (1 - psi^r).  Eq. 4 maps that SZ back to -g c ln(1 - 1/g) (= c to within
+    c/2g) for any g, r, c and psi; psi is solved here so that E[SZ] is the
+    integer the oracle takes."""
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        g = int(2 ** rng.integers(5, 13))
+        r = int(rng.integers(3, 9))
+        c = float(rng.uniform(0, 4 * g))
+        own = g * (1 - 1 / g) ** c          # expected zero bits of the host's own estimator
+        if own < 2:
+            continue
+        sz = int(rng.integers(1, int(own)))  # any integer below it fixes psi
+        psi = (1 - sz / own) ** (1 / r)
+        want = -g * c * math.log1p(-1 / g)
+        got = O.estimate(g, r, psi, sz)
+        assert abs(got - want) <= 1e-9 * max(1.0, abs(want)), (g, r, c, psi, sz)
+
+
 def test_theorem1_removes_shared_bits(O):
     """Theorem 1 model: a host's r estimators each hold its own c peers plus
     bits set by other hosts independently with probability psi.  ULE is the
