@@ -45,9 +45,14 @@
  *   Restore keeps a tuple only when the restored a0 also satisfies
  *     DH_0(a0) = CL_0, so K = { a : DH_i(a) in HE(i) for every i }.
  *   Report a0 when C(a0) >= theta (Algorithm 2 skips C < theta).
- *   Overload: |HE(0)|*|HE(1)| > pair_cap, or |K| > cand_cap, gives no hits for
- *     that direction and a flag.  A row with ZR(i) = 0 makes psi = 1 and Eq. 4
- *     undefined: the direction is flagged saturated and gives no hits.
+ *   Overload (the paper has no bound): a restore work bound |HE(0)|*2^(32-k),
+ *     the number of keys whose DH_0 is a hot estimator of row 0, above
+ *     pair_cap, or |K| > cand_cap, gives no hits for that direction and a
+ *     flag.  An overloaded |K| is reported as cand_cap + 1 ("more than the
+ *     cap"): the enumeration stops once it has found cand_cap + 1 members,
+ *     which happens exactly when |K| > cand_cap, in whatever order K is
+ *     walked.  A row with ZR(i) = 0 makes psi = 1 and Eq. 4 undefined: the
+ *     direction is flagged saturated and gives no hits.
  *
  * Parity pins (tests check these against the paper and mathematics, not
  * against this code): splitmix64 published output; Eq. 2/3 round trip;
@@ -70,7 +75,7 @@ typedef struct {
     uint32_t g, r, k, alpha, dirs, reserved;
     double theta;
     uint64_t seed;
-    uint64_t pair_cap; /* bound on |HE(0)|*|HE(1)| */
+    uint64_t pair_cap; /* bound on the restore work |HE(0)|*2^(32-k) */
     uint64_t cand_cap; /* bound on |K| */
 } or_params;
 
@@ -397,7 +402,9 @@ uint32_t or_inverse_odd(uint32_t A)
 
 /* Same set K, by enumerating for each CL_0 in HE(0) the 2^(32-k) keys with
  * DH_0(a) = CL_0 (A0 is odd, so a -> A0*a mod 2^32 is a bijection) and keeping
- * those whose DH_i(a) is hot in every other row. */
+ * those whose DH_i(a) is hot in every other row.  Returns |K| when it is at
+ * most cap; otherwise stops at the first member past the cap and returns
+ * cap + 1. */
 uint64_t or_restore_preimage(const or_params *p, uint32_t dir, const uint32_t *he, const uint32_t *nhe,
                              uint32_t *out, uint64_t cap)
 {
@@ -417,8 +424,10 @@ uint64_t or_restore_preimage(const or_params *p, uint32_t dir, const uint32_t *h
             for (uint32_t i = 1; i < p->r && all; i++)
                 all = hot[(uint64_t)i * ncell + dh(h.A0[dir], k, p->alpha, i, a)];
             if (all) emit(out, cap, &count, a);
+            if (count > cap) goto done;
         }
     }
+done:
     free(hot);
     if (count <= cap) qsort(out, count, sizeof(uint32_t), cmp_u32);
     return count;
@@ -460,7 +469,7 @@ uint64_t or_close_window(const or_params *p, const uint32_t *grid, or_summary *s
         psi = or_psi(p, sum->zr[dir]);
         sum->psi[dir] = psi;
         if (psi < 0.0) { sum->flags[dir] |= OR_FLAG_SATURATED; continue; }
-        if ((uint64_t)sum->n_hot[dir][0] * (uint64_t)sum->n_hot[dir][1] > p->pair_cap) {
+        if (((uint64_t)sum->n_hot[dir][0] << (32u - p->k)) > p->pair_cap) {
             sum->flags[dir] |= OR_FLAG_OVERLOAD_PAIRS;
             continue;
         }

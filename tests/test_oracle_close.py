@@ -285,20 +285,46 @@ def test_accuracy_statistics_small_core(O):
 
 
 def test_overload_flags(O):
+    """Overload reading (the paper has no bound): the restore work bound
+    |HE(0)| 2^(32-k) above pair_cap skips the restore; |K| above cand_cap
+    drops the direction's hits and reports |K| as cand_cap + 1.  Both caps
+    are checked on each side of their boundary."""
     w = T.WORKLOADS["tiny"]
     win = T.make_window(w, T.window_seed(1))
     p = O.params_from(w.sketch(), seed=1234)
     grid = O.new_grid(p)
     O.update(p, grid, win.pairs)
     full = O.close_window(p, grid)
-    nh0, nh1 = full["n_hot"][0][0], full["n_hot"][0][1]
-    p2 = O.params_from(w.sketch(), seed=1234, pair_cap=int(nh0 * nh1) - 1)
+    nk = full["n_cand"][0]
+    work = int(full["n_hot"][0][0]) << (32 - w.k)
+    p2 = O.params_from(w.sketch(), seed=1234, pair_cap=work - 1)
     r2 = O.close_window(p2, grid)
-    assert r2["flags"][0] == O.FLAG_OVERLOAD_PAIRS and r2["n_hits"] == 0
-    p3 = O.params_from(w.sketch(), seed=1234, cand_cap=full["n_cand"][0] - 1)
+    assert r2["flags"][0] == O.FLAG_OVERLOAD_PAIRS and r2["n_hits"] == 0 and r2["n_cand"][0] == 0
+    p2b = O.params_from(w.sketch(), seed=1234, pair_cap=work)
+    assert O.close_window(p2b, grid)["flags"][0] == 0
+    p3 = O.params_from(w.sketch(), seed=1234, cand_cap=nk - 1)
     r3 = O.close_window(p3, grid)
     assert r3["flags"][0] == O.FLAG_OVERLOAD_CANDS and r3["n_hits"] == 0
-    assert r3["n_cand"][0] == full["n_cand"][0]
-    p4 = O.params_from(w.sketch(), seed=1234, cand_cap=full["n_cand"][0])
+    assert r3["n_cand"][0] == nk
+    p3b = O.params_from(w.sketch(), seed=1234, cand_cap=nk // 3)
+    r3b = O.close_window(p3b, grid)
+    assert r3b["flags"][0] == O.FLAG_OVERLOAD_CANDS and r3b["n_cand"][0] == nk // 3 + 1
+    p4 = O.params_from(w.sketch(), seed=1234, cand_cap=nk)
     r4 = O.close_window(p4, grid)
-    assert r4["flags"][0] == 0 and r4["n_hits"] == full["n_hits"]
+    assert r4["flags"][0] == 0 and r4["n_hits"] == full["n_hits"] and r4["n_cand"][0] == nk
+
+
+def test_overloaded_restore_stops_at_the_cap(O):
+    """A DHLA whose estimators are all full: every key is in K (|K| = 2^32),
+    so the close must flag the overload after cand_cap + 1 members instead of
+    walking the whole key space."""
+    import time
+    w = T.WORKLOADS["tiny"]
+    p = O.params_from(w.sketch(), seed=77, cand_cap=1 << 16)
+    grid = np.full(O.new_grid(p).shape, 0xFFFFFFFF, dtype=np.uint32)
+    grid[::w.g // 32] = 0xFFFFFFFE   # one zero bit per estimator: ZR(i) = 2^k, psi defined
+    t0 = time.perf_counter()
+    r = O.close_window(p, grid)
+    assert time.perf_counter() - t0 < 5.0
+    assert r["flags"][0] == O.FLAG_OVERLOAD_CANDS and r["n_cand"][0] == (1 << 16) + 1
+    assert list(r["n_hot"][0]) == [1 << w.k] * w.r and r["n_hits"] == 0

@@ -90,8 +90,12 @@ MUTANTS = {
         ("if (C < p->theta) continue;", "if (C >= p->theta) continue;")]),
     "saturation-ignored": ("a row with ZR(i) = 0 has no psi", [
         ("if (zr[i] == 0) return -1.0;", "if (zr[i] == 0) continue;")]),
-    "overload-cap-off-by-one": ("pair_cap bounds |HE(0)| |HE(1)|", [
-        ("(uint64_t)sum->n_hot[dir][1] > p->pair_cap)", "(uint64_t)sum->n_hot[dir][1] > p->pair_cap + 1u)")]),
+    "overload-cap-off-by-one": ("pair_cap bounds |HE(0)| 2^(32-k)", [
+        ("<< (32u - p->k)) > p->pair_cap)", "<< (32u - p->k)) > p->pair_cap + 1u)")]),
+    "overload-bound-uses-k-bits": ("the work bound counts the 2^(32-k) preimages of each hot c0", [
+        ("<< (32u - p->k)) > p->pair_cap)", "<< p->k) > p->pair_cap)")]),
+    "overloaded-k-counted-exactly": ("an overloaded |K| is reported as cand_cap + 1", [
+        ("            if (count > cap) goto done;\n", "")]),
     "cand-cap-off-by-one": ("cand_cap bounds |K|", [
         ("if (nk > kcap) { sum->flags[dir] |= OR_FLAG_OVERLOAD_CANDS; continue; }",
          "if (nk >= kcap) { sum->flags[dir] |= OR_FLAG_OVERLOAD_CANDS; continue; }")]),
