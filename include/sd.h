@@ -52,9 +52,9 @@ extern "C" {
 
 /* Per-direction flags, in sd_report.flags at bit offset 8*dir. */
 #define SD_FLAG_SATURATED 1u
-#define SD_FLAG_OVERLOAD_PAIRS 2u  /* restore work over pair_cap: restore skipped */
+#define SD_FLAG_OVERLOAD_PAIRS 2u  /* restore work bound over pair_cap: restore skipped */
 #define SD_FLAG_OVERLOAD_CANDS 4u  /* |K| > cand_cap (or a staged-join list over its
-                                      buffer): candidates not kept */
+                                      buffer): no hits; n_cand = cand_cap + 1 */
 #define SD_FLAG_REPORT_OVERFLOW 8u /* hits beyond report_cap were dropped */
 
 typedef struct sd_handle sd_handle;
@@ -71,11 +71,16 @@ typedef struct {
     uint64_t seed;        /* seed of the hash constants */
     uint32_t dirs;        /* 1: outbound (src keyed) only; 2: outbound and inbound */
     int32_t device;       /* CUDA device ordinal */
-    uint64_t pair_cap;    /* restore is skipped (OVERLOAD) when its work bound exceeds
-                             this: |HE(0)|*|HE(1)| (c0, c1) pairs, or |HE(0)||HE(1)||HE(2)|
-                             tuples for the staged join (tuning restore = 1); default 2^32 */
+    uint64_t pair_cap;    /* restore work budget (the paper sets none): a direction's
+                             restore is skipped (SD_FLAG_OVERLOAD_PAIRS) when
+                             |HE(0)| * 2^(32-k), the number of keys whose DH_0 is a hot
+                             estimator of row 0 (a superset of K), exceeds it; the
+                             staged join (tuning restore = 1) is also skipped when its
+                             first-stage tuples |HE(0)||HE(1)||HE(2)| exceed it;
+                             default 2^32 */
     uint64_t cand_cap;    /* capacity for the candidate set K per direction;
-                             default 2^20 */
+                             default 2^20.  The restore stops once K has more members
+                             (SD_FLAG_OVERLOAD_CANDS) */
     uint64_t report_cap;  /* most hits returned per close; default dirs*cand_cap */
     uint64_t stage_pairs; /* pairs per host-ingest chunk; default 2^22, or 2^24 when the
                              DHLA has more than 64 MiB */
@@ -99,7 +104,10 @@ typedef struct {
     uint64_t zr[2][8];      /* ZR(i): zero bits of row i (§3.3) */
     double psi[2];          /* psi of Lemma 1 with w' averaged over rows; -1 if saturated */
     uint32_t n_hot[2][8];   /* |HE(i)| */
-    uint64_t n_cand[2];     /* |K| = #{a : DH_i(a) in HE(i) for all i} */
+    uint64_t n_cand[2];     /* |K| = #{a : DH_i(a) in HE(i) for all i}; cand_cap + 1 for a
+                               direction flagged SD_FLAG_OVERLOAD_CANDS (|K| exceeds the
+                               cap; the restore stopped there); 0 when the restore was
+                               skipped */
     uint32_t zhot;          /* largest z_0 that is hot (z_0 < Zmin = g e^(-theta/g)) */
     uint32_t szmax[2];      /* largest SZ with C(SZ) >= theta (Eq. 4): hits have SZ <= szmax */
     uint32_t flags;         /* SD_FLAG_* at bit 8*dir */
@@ -118,8 +126,15 @@ typedef struct {
                                3: a per-block shared-memory filter of bits known to
                                   be set, then 1;
                                4: the filter, then 0;
-                               5: binned: bit-sets sorted by DHLA slice through a
-                                  scratch buffer, each slice updated in shared memory */
+                               5: binned by DHLA slice: bit-sets sorted by slice through
+                                  a scratch buffer, each slice updated in shared memory;
+                               6: binned by estimator bit (the default where one bit
+                                  plane, r 2^k bits, fits 192 KiB of shared memory): the
+                                  keys of each direction sorted by H1(peer) -- the bit
+                                  Algorithm 1 sets in all r estimators of the key -- then
+                                  each bit plane's estimators DH_i(key) set in shared
+                                  memory and ORed into a plane-major copy of the DHLA,
+                                  folded into the DHLA before it is read */
     uint32_t block_threads; /* threads per block: 64..1024, multiple of 32 */
     uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (0: as
                                many as fit) */
@@ -144,8 +159,11 @@ typedef struct {
                                    direction SD_FLAG_OVERLOAD_CANDS, and a first
                                    stage above pair_cap tuples SD_FLAG_OVERLOAD_PAIRS.
                                 Both give the same K and the same report. */
-    uint32_t bin_batch_mib;  /* mode 5, sd_update_many: MiB of bins one batched round
-                                may use (bounds the links per round); default 8192 */
+    uint32_t bin_batch_mib;  /* modes 5 and 6, sd_update_many: MiB of bins one batched
+                                round may use (bounds the links per round); default 8192 */
+    uint32_t plane_tile_pairs; /* mode 6: pairs per binning tile: 1024, 2048 or 4096 */
+    uint32_t plane_round_log2; /* mode 6: pairs per count/bin/apply round, log2: 10..28 */
+    uint32_t plane_unit_log2;  /* mode 6: bin entries per apply step, log2: 8..24 */
 } sd_tuning;
 
 /* Fill *p with the core-link configuration (g=512, r=4, k=16, alpha=8,
@@ -168,8 +186,11 @@ uint64_t sd_grid_words(const sd_params *p);
  * (sd_scratch_bytes). */
 uint64_t sd_device_bytes(const sd_params *p);
 
-/* Create a handle: allocate a zeroed DHLA per direction and the scratch
- * of the close path on p->device.  *out is set only on success. */
+/* Create a handle: allocate a zeroed DHLA per direction (the r LAs of 2^k
+ * linear estimators of g bits each, §3.2, one per traffic direction of
+ * §3.1) and the scratch of the close path (hot sets, K and the report of
+ * Algorithm 2) on p->device.  *out is set only on success; on failure
+ * nothing stays allocated and sd_last_error(NULL) says why. */
 int sd_create(const sd_params *p, sd_handle **out);
 
 /* Algorithm 1 over n pairs.  `pairs` holds n (src, dst) uint32 pairs,
@@ -205,31 +226,36 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
 
 /* Algorithm 1 for `count` handles at once (batched windows of many links):
  * handle i gets the ns[i] pairs at pairs[i], exactly as sd_update would give
- * it.  When hs[0] uses the binned update (tuning mode 5), every link whose
+ * it.  When hs[0] uses a binned update (tuning mode 5 or 6), every link whose
  * pairs are device-resident on hs[0]'s device and whose DHLA has hs[0]'s
  * shape (g, r, k, alpha, dirs) is binned with the others: each round takes
  * links round-robin, each contributing up to 2^bin_chunk_log2 pairs, as
  * many as hs[0]'s bin_batch_mib of bins holds at the round's largest share
  * (and at most 4096 slices in all), with one bin launch and one apply
- * launch per round, on hs[0]'s stream and with hs[0]'s scratch
- * (ordered after each member's earlier work, and each member's later work
- * after it).  The other links take sd_update.  Returns
+ * launch per round (binned by DHLA slice, with mode 5's knobs), on hs[0]'s
+ * stream and with hs[0]'s scratch (ordered after each member's earlier work,
+ * and each member's later work after it).  The other links take sd_update.
+ * Returns
  * the first error, if any. */
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count);
 
-/* Device bytes of the binned update's scratch (bins and counters) that h
- * allocates, with its current tuning, when it updates alone (links <= 1)
- * or drives sd_update_many over `links` members (at most about
- * bin_batch_mib MiB then); the scratch grows to the largest such need and
- * is kept until sd_destroy.  0 when h does not bin
- * (tuning mode other than 5, or a DHLA of more than 4096 slices) or h is
- * NULL.  For memory budgets: a handle holds sd_device_bytes plus this. */
+/* Device bytes of the binned update's scratch that h allocates, with its
+ * current tuning, when it updates alone (links <= 1: for mode 6 the round's
+ * bins and counters plus the plane-major DHLA copy, which is as large as the
+ * DHLA) or drives sd_update_many over `links` members (slice bins, at most
+ * about bin_batch_mib MiB); the scratch grows to the largest such need and
+ * is kept until sd_destroy.  0 when h does not bin (tuning modes 0-4, or a
+ * DHLA of more than 4096 slices in a batch) or h is NULL.  For memory
+ * budgets: a handle holds sd_device_bytes plus this. */
 uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links);
 
 /* Wait for all work queued on the handle's stream. */
 int sd_sync(sd_handle *h);
 
-/* Release every resource of the handle.  NULL is a no-op. */
+/* Release every resource of the handle: its DHLAs (§3.2), the close
+ * scratch of Algorithm 2 and any staging or binning scratch, after the work
+ * queued on its stream has finished.  The report's hits become invalid.
+ * NULL is a no-op. */
 int sd_destroy(sd_handle *h);
 
 /* Message of the last error on h (or of the last failed sd_create when h is
@@ -283,8 +309,11 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t);
  * capture.  All calls share the array: calls whose work overlaps on the GPU
  * race and must be serialised by the caller.  Returns SD_ERR_TOO_LARGE when
  * the DHLA has more than 512 MiB (4096 slices of 128 KiB) or its bins would
- * not fit the scratch, SD_ERR_ARG for invalid parameters or pointers,
- * SD_ERR_CUDA when a CUDA call fails. */
+ * not fit the scratch; SD_ERR_ARG for invalid parameters, or for a `grid` or
+ * `pairs` that is not device (or managed) memory of the current device;
+ * SD_ERR_CUDA when a CUDA call fails, or, with nothing queued, when the
+ * calling thread already has a CUDA error pending from earlier work (that
+ * error is left in place for the caller). */
 int sd_update_noalloc(const sd_params *p, uint32_t *grid, const uint32_t *pairs, uint64_t n,
                       void *cuda_stream);
 

@@ -224,6 +224,16 @@ struct sd_handle {
     uint64_t bin_mem_words = 0;
     BinArgs bin{};
 
+    // plane-binned update (mode 6): the plane-major DHLA copy (the handle's
+    // DHLA is grid | planes^T; folded into grid before anything reads it)
+    // and the round's bins and counters, allocated on first use
+    uint32_t *planes = nullptr;
+    uint64_t planes_words = 0;
+    uint32_t *plane_mem = nullptr;     // bins, then ntot, binoff, fill, unit_start, ctl
+    uint64_t plane_mem_words = 0;
+    PlaneArgs pa{};
+    bool planes_dirty = false;
+
     // batched update (sd_update_many): link tables in two halves used by
     // alternate calls (a half is rewritten once the call two back has read
     // it, so consecutive calls do not wait for each other), an event per
@@ -388,6 +398,8 @@ static void release(sd_handle *h) {
     cudaFree(h->hits);
     cudaFree(h->hits_tmp);
     cudaFree(h->bin_mem);
+    cudaFree(h->planes);
+    cudaFree(h->plane_mem);
     cudaFree(h->he_all);
     cudaFree(h->jsub);
     cudaFree(h->cj_d);
@@ -416,6 +428,16 @@ static void release(sd_handle *h) {
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// Words of one bit plane (r estimators' bit b), 16-byte aligned.
+static uint32_t plane_words(const Geometry &G) {
+    return (uint32_t)((((uint64_t)G.r << G.k) / 32 + 3) & ~3ull);
+}
+
+// Most shared memory one bit plane may take in k_plane_apply.
+constexpr uint64_t kPlaneSmemMax = 192 * 1024;
+
+static bool plane_fits(const Geometry &G) { return (uint64_t)plane_words(G) * 4 <= kPlaneSmemMax; }
+
 static int create_impl(const sd_params *p, sd_handle *h) {
     h->p = *p;
     geometry_of(p, &h->G);
@@ -424,8 +446,11 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     // a DHLA of 1024 slices or more takes 2048-pair tiles, so that each
     // slice's run in a tile stays long enough for coalesced bin writes
     // (autotuned on the 2 x 128 MiB stress sketch: 50 ms vs 72 ms per 2^30 pairs)
-    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192};
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192, 4096, 22, 15};
     if ((uint64_t)p->dirs * G.dir_words >= (1ull << 25) && p->dirs * p->r <= 8) h->T.bin_tile_pairs = 2048;
+    // binned by estimator bit wherever one bit plane fits a block's shared
+    // memory (r 2^k bits: every workload of the scope table)
+    if (plane_fits(G)) h->T.mode = 6;
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -550,8 +575,78 @@ static int ensure_bins(sd_handle *h, bool *ok) {
     return ensure_bin_mem(h, B);
 }
 
+// Layout of the plane-binned update for the current tuning: bins for one
+// round of 2^plane_round_log2 pairs (dirs keys per pair, each plane's bin
+// padded to 4 entries), the counters, and the plane-major DHLA copy.
+static void plane_layout(const sd_handle *h, PlaneArgs *P, uint64_t *mem_words, uint64_t *plane_copy_words) {
+    const Geometry &G = h->G;
+    std::memset(P, 0, sizeof *P);
+    P->nbins = G.dirs * G.g;
+    P->ps = plane_words(G);
+    P->unit = 1u << h->T.plane_unit_log2;
+    P->tile_pairs = h->T.plane_tile_pairs;
+    const uint64_t round = 1ull << h->T.plane_round_log2;
+    const uint64_t bins = (uint64_t)G.dirs * round + 4ull * P->nbins;
+    *mem_words = bins + 4ull * P->nbins + 2 + 4;
+    *plane_copy_words = (uint64_t)P->nbins * P->ps;
+}
+
+static int ensure_plane_mem(sd_handle *h) {
+    PlaneArgs P;
+    uint64_t words = 0, pw = 0;
+    plane_layout(h, &P, &words, &pw);
+    if (!h->planes) {
+        SD_CK(h, cudaMalloc(&h->planes, pw * 4));
+        SD_CK(h, cudaMemsetAsync(h->planes, 0, pw * 4, h->stream));
+        h->planes_words = pw;
+    }
+    if (words > h->plane_mem_words) {
+        SD_CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->plane_mem);
+        h->plane_mem = nullptr;
+        h->plane_mem_words = 0;
+        SD_CK(h, cudaMalloc(&h->plane_mem, words * 4));
+        h->plane_mem_words = words;
+    }
+    const uint64_t bins = words - (4ull * P.nbins + 2 + 4);
+    uint32_t *c = h->plane_mem + bins;
+    P.bins = h->plane_mem;
+    P.ntot = c;
+    P.binoff = c + P.nbins;
+    P.fill = c + 2 * P.nbins + 1;
+    P.unit_start = c + 3 * P.nbins + 1;
+    P.ctl = c + 4 * P.nbins + 2;
+    P.planes = h->planes;
+    if (P.ntot != h->pa.ntot || P.nbins != h->pa.nbins)  // new counters: ntot, fill and ctl start at zero
+        SD_CK(h, cudaMemsetAsync(c, 0, (4ull * P.nbins + 2 + 4) * 4, h->stream));
+    h->pa = P;
+    return SD_OK;
+}
+
+// grid |= planes^T and planes = 0 (stream-ordered), when updates of the
+// plane-binned mode are pending.
+static int fold_planes(sd_handle *h) {
+    if (!h->planes_dirty) return SD_OK;
+    SD_CK(h, launch_plane_fold(h->grid, h->planes, h->G, h->pa.ps, h->num_sms, h->stream));
+    launched(1);
+    h->planes_dirty = false;
+    return SD_OK;
+}
+
 // Algorithm 1 over n device-resident pairs, with the handle's tuning.
 static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+    if (h->T.mode == 6) {
+        const int rc = ensure_plane_mem(h);
+        if (rc != SD_OK) return rc;
+        const uint64_t round = 1ull << h->T.plane_round_log2;
+        for (uint64_t off = 0; off < n; off += round) {
+            const uint64_t m = std::min(round, n - off);
+            SD_CK(h, launch_plane_round(pairs + 2 * off, m, h->G, h->pa, h->num_sms, h->stream));
+            launched(3);
+        }
+        h->planes_dirty = true;
+        return SD_OK;
+    }
     if (h->T.mode == 5) {
         bool ok = false;
         const int rc = ensure_bins(h, &ok);
@@ -654,7 +749,9 @@ struct BatchLayout {
 static bool batch_layout(const sd_handle *h, BatchLayout *L) {
     BinArgs B;
     uint64_t words = 0;
-    if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return false;
+    // a batch bins by DHLA slice (one slice range per member); handles in
+    // either binned mode take part
+    if ((h->T.mode != 5 && h->T.mode != 6) || !bin_layout(h, &B, &words)) return false;
     L->S_link = B.S;
     L->sl = B.slice_log2;
     L->upd = (uint64_t)h->p.dirs * h->p.r;
@@ -671,7 +768,13 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     if (!h) return 0;
     BinArgs B;
     uint64_t words = 0;
-    if (h->T.mode != 5 || !bin_layout(h, &B, &words)) return 0;
+    if (h->T.mode == 6 && links <= 1) {
+        PlaneArgs P;
+        uint64_t pw = 0;
+        plane_layout(h, &P, &words, &pw);
+        return (words + pw) * 4;
+    }
+    if ((h->T.mode != 5 && h->T.mode != 6) || !bin_layout(h, &B, &words)) return 0;
     if (links <= 1) return words * 4;
     BatchLayout L;
     if (!batch_layout(h, &L)) return words * 4;
@@ -868,6 +971,8 @@ static int close_phase_a(sd_handle *h, sd_report *out) {
     std::memset(&h->cs, 0, sizeof h->cs);
     h->report.clear();
     h->last_ncand[0] = h->last_ncand[1] = 0;
+    const int frc = fold_planes(h);
+    if (frc != SD_OK) return frc;
     SD_CK(h, launch_row_stats(h->grid, h->G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
     SD_CK(h, launch_compact(h->hotmap, h->G, h->he, 2, h->stream));
     launched(2);
@@ -895,9 +1000,15 @@ static bool close_decide(sd_handle *h, sd_report *out) {
         const int szmax = szmax_of(G.g, G.r, c.psi[d], h->p.theta);
         out->szmax[d] = szmax < 0 ? 0 : (uint32_t)szmax;
         const uint64_t n0 = h->st_h->nhot[d][0], n1 = h->st_h->nhot[d][1];
-        // the work bound: (c0, c1) pairs, or the staged join's first-stage tuples
-        const uint64_t n2 = h->T.restore == 1 ? h->st_h->nhot[d][2] : 1;
-        if (n0 * n1 > h->pair_cap || (n2 && n0 * n1 > h->pair_cap / n2)) {
+        // the restore work bound: |HE(0)| 2^(32-k) keys have a hot DH_0, a
+        // superset of K that bounds both restores' work; the staged join
+        // also bounds its first-stage tuples |HE(0)||HE(1)||HE(2)|
+        bool over = (n0 << (32u - G.k)) > h->pair_cap;
+        if (h->T.restore == 1) {
+            const uint64_t n2 = h->st_h->nhot[d][2];
+            over = over || (n2 && n0 * n1 > h->pair_cap / n2);
+        }
+        if (over) {
             c.flags |= SD_FLAG_OVERLOAD_PAIRS << (8 * d);
             continue;
         }
@@ -972,6 +1083,10 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
         if (h->T.restore == 1)
             for (uint32_t i = 2; i + 1 < h->G.r; i++) join_full |= h->st_h->jcount[d][i] > h->join_cap;
         if (nk > h->cand_cap || join_full) {
+            // the restore stopped once K passed its capacity: |K| is only
+            // known to exceed it
+            out->n_cand[d] = h->cand_cap + 1;
+            h->last_ncand[d] = h->cand_cap + 1;
             c.flags |= SD_FLAG_OVERLOAD_CANDS << (8 * d);
             continue;
         }
@@ -1132,9 +1247,16 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
         SD_CK(d, cudaStreamWaitEvent(s, h->ev_batch, 0));
     }
-    // phase A: row statistics and HE(0), HE(1) of every window
+    // phase A: row statistics and HE(0), HE(1) of every window (pending
+    // plane-binned updates folded into each DHLA first, on the driver's
+    // stream, which is ordered after every member's work)
     for (uint32_t i = 0; i < count; i++) {
         sd_handle *h = hs[i];
+        if (h->planes_dirty) {
+            SD_CK(d, launch_plane_fold(h->grid, h->planes, h->G, h->pa.ps, d->num_sms, s));
+            launched(1);
+            h->planes_dirty = false;
+        }
         std::memset(&outs[i], 0, sizeof outs[i]);
         std::memset(&h->cs, 0, sizeof h->cs);
         h->report.clear();
@@ -1318,6 +1440,8 @@ const char *sd_last_error(const sd_handle *h) {
 int sd_get_grid(sd_handle *h, uint32_t dir, uint32_t *host_dst) {
     if (!h || !host_dst || dir >= h->G.dirs) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
+    const int frc = fold_planes(h);
+    if (frc != SD_OK) return frc;
     SD_CK(h, cudaMemcpyAsync(host_dst, h->grid + (uint64_t)dir * h->G.dir_words, h->G.dir_words * 4,
                              cudaMemcpyDeviceToHost, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
@@ -1327,6 +1451,8 @@ int sd_get_grid(sd_handle *h, uint32_t dir, uint32_t *host_dst) {
 int sd_set_grid(sd_handle *h, uint32_t dir, const uint32_t *host_src) {
     if (!h || !host_src || dir >= h->G.dirs) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
+    const int frc = fold_planes(h);  // pending bits of the other direction stay
+    if (frc != SD_OK) return frc;
     SD_CK(h, cudaMemcpyAsync(h->grid + (uint64_t)dir * h->G.dir_words, host_src, h->G.dir_words * 4,
                              cudaMemcpyHostToDevice, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
@@ -1366,6 +1492,9 @@ int sd_merge(sd_handle *dst, sd_handle *src) {
         a.device != b.device)
         return dst->fail(SD_ERR_ARG, "sd_merge: handles differ in shape, seed or device");
     DeviceGuard dg(a.device);
+    int frc = fold_planes(src);
+    if (frc == SD_OK) frc = fold_planes(dst);
+    if (frc != SD_OK) return frc;
     cudaEvent_t ev;
     SD_CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     cudaError_t e = cudaEventRecord(ev, src->stream);
@@ -1397,13 +1526,19 @@ int sd_get_tuning(const sd_handle *h, sd_tuning *out) {
     out->bin_slack_pct = h->T.bin_slack_pct;
     out->restore = h->T.restore;
     out->bin_batch_mib = h->T.bin_batch_mib;
+    out->plane_tile_pairs = h->T.plane_tile_pairs;
+    out->plane_round_log2 = h->T.plane_round_log2;
+    out->plane_unit_log2 = h->T.plane_unit_log2;
     return SD_OK;
 }
 
 int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
     if (!h || !t) return SD_ERR_ARG;
     Tuning T = h->T;
-    if (t->mode > 5) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..5");
+    if (t->mode > 6) return h->fail(SD_ERR_ARG, "sd_set_tuning: mode must be 0..6");
+    if (t->mode == 6 && !plane_fits(h->G))
+        return h->fail(SD_ERR_ARG, "sd_set_tuning: mode 6 needs one bit plane (r 2^k bits) within %llu KiB",
+                       (unsigned long long)(kPlaneSmemMax >> 10));
     T.mode = t->mode;
     if (t->restore > 1) return h->fail(SD_ERR_ARG, "sd_set_tuning: restore must be 0 or 1");
     T.restore = t->restore;
@@ -1445,6 +1580,22 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
         if (t->bin_batch_mib > (1u << 20))
             return h->fail(SD_ERR_ARG, "sd_set_tuning: bin_batch_mib must be at most 2^20");
         T.bin_batch_mib = t->bin_batch_mib;
+    }
+    if (t->plane_tile_pairs) {
+        const uint32_t tp = t->plane_tile_pairs;
+        if (tp != 1024 && tp != 2048 && tp != 4096)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: plane_tile_pairs must be 1024, 2048 or 4096");
+        T.plane_tile_pairs = tp;
+    }
+    if (t->plane_round_log2) {
+        if (t->plane_round_log2 < 10 || t->plane_round_log2 > 28)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: plane_round_log2 must be in [10, 28]");
+        T.plane_round_log2 = t->plane_round_log2;
+    }
+    if (t->plane_unit_log2) {
+        if (t->plane_unit_log2 < 8 || t->plane_unit_log2 > 24)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: plane_unit_log2 must be in [8, 24]");
+        T.plane_unit_log2 = t->plane_unit_log2;
     }
     if (T.mode == 5) {
         // the binning tile must fit one block's shared memory

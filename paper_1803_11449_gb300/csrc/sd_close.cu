@@ -162,14 +162,13 @@ constexpr uint32_t kRestoreTileMax = 256;  // c0 values per k_restore tile
 constexpr int kWarpBuf = 64;
 
 __device__ __forceinline__ void flush_cands(const RestoreArgs &A, uint32_t dir, uint32_t *cbuf, uint32_t &ccount,
-                                            uint32_t lane, bool &overloaded) {
+                                            uint32_t lane) {
     if (ccount == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&A.stats->ncand[dir], (unsigned long long)ccount);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     for (uint32_t q = lane; q < ccount; q += 32)
         if (base + q < A.cand_cap) A.cand[(uint64_t)dir * A.cand_cap + base + q] = cbuf[q];
-    if (base + ccount > A.cand_cap) overloaded = true;
     ccount = 0;
     __syncwarp();
 }
@@ -192,6 +191,7 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_cbuf[8][kWarpBuf];
     __shared__ uint32_t s_c0[kRestoreTileMax];
+    __shared__ bool s_stop;
     __syncthreads();  // shared memory may still be in use by a previous call
     // per-direction scalars picked with selects: indexing the parameter
     // arrays with a run-time index would copy them to local memory
@@ -221,7 +221,6 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *cbuf = s_cbuf[threadIdx.x >> 5];
     uint32_t ccount = 0;  // warp-uniform
-    bool overloaded = false;
     const uint64_t J = (uint64_t)n1 << A.ulog;
     const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
     const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
@@ -237,8 +236,14 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
         const uint32_t c0_base = t0 * A.tile0;
         const uint32_t nc0 = min(A.tile0, n0 - c0_base);
         __syncthreads();
+        // once K has passed its capacity the direction reports nothing but
+        // the overload, so the rest of its enumeration is skipped (one read
+        // of the shared counter per tile, the same decision for the block)
+        if (threadIdx.x == 0)
+            s_stop = *reinterpret_cast<volatile unsigned long long *>(&A.stats->ncand[dir]) > A.cand_cap;
         for (uint32_t q = threadIdx.x; q < nc0; q += blockDim.x) s_c0[q] = he0[c0_base + q];
         __syncthreads();
+        if (s_stop) break;
         for (uint32_t m = 0; m < iters; m++) {
             const uint64_t j = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
             const bool jvalid = j < J;
@@ -268,12 +273,12 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
                 if (found) cbuf[ccount + __popc(fb & ((1u << lane) - 1u))] = a;
                 ccount += __popc(fb);
                 __syncwarp();
-                if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane, overloaded);
+                if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane);
             }
         }
     }
     __syncwarp();
-    flush_cands(A, dir, cbuf, ccount, lane, overloaded);
+    flush_cands(A, dir, cbuf, ccount, lane);
 }
 
 __global__ void __launch_bounds__(256)

@@ -32,7 +32,8 @@ struct Geometry {
 
 struct Tuning {
     uint32_t mode;           // 0 plain, 1 test-then-set, 2 test + warp de-dup,
-                             // 3 filter + test, 4 filter + plain, 5 binned
+                             // 3 filter + test, 4 filter + plain, 5 binned by
+                             // DHLA slice, 6 binned by estimator bit (planes)
     uint32_t block_threads;
     uint32_t blocks_per_sm;
     uint32_t unroll;
@@ -43,6 +44,25 @@ struct Tuning {
     uint32_t bin_slack_pct;  // mode 5: bin capacity over the mean fill, in percent
     uint32_t restore;        // 0 DH_0 inversion (k_restore), 1 staged join (sd_join.cu)
     uint32_t bin_batch_mib;  // mode 5, batched update: MiB of bins per round
+    uint32_t plane_tile_pairs;  // mode 6: pairs per binning tile (1024, 2048 or 4096)
+    uint32_t plane_round_log2;  // mode 6: pairs per count/bin/apply round, log2
+    uint32_t plane_unit_log2;   // mode 6: bin entries per apply unit, log2
+};
+
+// The plane-binned update (sd_plane.cu): bins of keys per plane (d, b) =
+// bit b of every estimator of direction d, and the plane-major DHLA copy.
+struct PlaneArgs {
+    uint32_t *bins;        // the round's keys, each plane's bin starting on 4 entries
+    uint32_t *ntot;        // [nbins] entries per plane (k_plane_count; zero between rounds)
+    uint32_t *binoff;      // [nbins + 1] first entry of each bin
+    uint32_t *fill;        // [nbins] entries appended (k_plane_bin): the bin's size
+    uint32_t *unit_start;  // [nbins + 1] first apply unit of each plane
+    uint32_t *ctl;         // [0] blocks done (k_plane_count), [1] apply units taken
+    uint32_t *planes;      // [nbins][ps] plane-major DHLA copy
+    uint32_t nbins;        // dirs * g
+    uint32_t ps;           // words per plane: r 2^k / 32 rounded up to 4
+    uint32_t unit;         // entries per apply unit (a multiple of 4)
+    uint32_t tile_pairs;   // pairs per binning tile
 };
 
 // One link of a batched binned update (device memory table).
@@ -217,6 +237,13 @@ cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, u
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
+size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins);
+// one round of the plane-binned update over n pairs (count, bin, apply)
+cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
+                               cudaStream_t s);
+// grid |= planes^T, planes = 0
+cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
+                              cudaStream_t s);
 cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                                 const BinArgs &B, int num_sms, cudaStream_t s);
 cudaError_t launch_binned_links(const LinkDesc *links_dev, uint32_t nlinks, uint64_t ntiles_all,

@@ -81,7 +81,12 @@ __global__ void __launch_bounds__(256) k_join_first(Geometry G, JoinArgs J) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t pairs = (uint64_t)n0 * n1;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // the list this stage fills: once past its buffer the direction is
+    // overloaded and the rest of the stage is skipped (a warp-uniform read)
+    const volatile unsigned long long *filled = last ? &J.stats->ncand[d] : &J.stats->jcount[d][2];
+    const uint64_t fill_cap = last ? J.cand_cap : J.cap;
     for (uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < pairs; p += nwarps) {
+        if (*filled > fill_cap) break;
         const uint32_t c0 = he0[p / n1], c1 = he1[p % n1];
         const uint32_t b1 = c0 ^ c1;  // bits [0, k) of the address
         for (uint32_t j0 = 0; j0 < n2; j0 += 32) {
@@ -117,7 +122,8 @@ __global__ void __launch_bounds__(256) k_join_next(Geometry G, JoinArgs J, uint3
     const uint32_t m = (1u << ov) - 1u;
     const uint32_t A0 = d ? G.h[1].A0 : G.h[0].A0;
     const uint64_t produced = J.stats->jcount[d][i - 1];
-    const uint64_t nin = produced < J.cap ? produced : J.cap;
+    if (produced > J.cap) return;  // the previous stage overflowed: the direction is overloaded
+    const uint64_t nin = produced;
     const unsigned long long *in = (((i - 3) & 1u) ? J.sub[1] : J.sub[0]) + (uint64_t)d * J.cap;
     unsigned long long *out = (((i - 2) & 1u) ? J.sub[1] : J.sub[0]) + (uint64_t)d * J.cap;
     const uint32_t ni = d ? pick(J.n[1], i) : pick(J.n[0], i);
@@ -127,7 +133,10 @@ __global__ void __launch_bounds__(256) k_join_next(Geometry G, JoinArgs J, uint3
     const bool last = i == G.r - 1;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const volatile unsigned long long *filled = last ? &J.stats->ncand[d] : &J.stats->jcount[d][i];
+    const uint64_t fill_cap = last ? J.cand_cap : J.cap;
     for (uint64_t q = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nin; q += nwarps) {
+        if (*filled > fill_cap) break;
         const unsigned long long e = in[q];
         const uint32_t part = (uint32_t)(e >> 32), c0 = (uint32_t)e;
         const uint32_t shared_bits = s_ov >= 32 ? 0u : ((part >> s_ov) & m);

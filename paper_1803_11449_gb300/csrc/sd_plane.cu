@@ -1,0 +1,494 @@
+// sd_plane.cu -- Algorithm 1 (Update DHLA) binned by estimator bit: the
+// default update of sd_update (tuning mode 6).
+//
+// For one pair and one direction, Algorithm 1 sets the SAME bit b = H1(elem)
+// in each of the r estimators DH_i(key), i < r (Eq. 2): one hash H1 per pair
+// and direction, shared by the rows (§3.2).  Call "plane (d, b)" bit b of
+// every estimator of direction d: r rows of 2^k bits, one bit per estimator.
+// All r bit-sets of a (pair, direction) fall in one plane, at positions that
+// depend on the key alone.  So the update is binned by plane with ONE entry
+// per pair and direction -- the key itself -- and the rows are hashed where
+// the plane is held, in shared memory:
+//
+//   k_plane_count  the entries of every plane for one round of pairs; the
+//                  last block lays the bins out back to back (exact sizes,
+//                  each bin starting on a 16-byte boundary) and cuts each
+//                  plane's bin into apply units.
+//   k_plane_bin    tiles of pairs: the keys sorted by plane in shared memory,
+//                  each plane's run appended to its bin with coalesced
+//                  stores (one reservation atomic per plane and tile).  The
+//                  bins are sized exactly by the count, so nothing overflows.
+//   k_plane_apply  one unit (a plane and a range of its bin) per block step:
+//                  the plane in shared memory, DH_0 and Eq. 2 of every key,
+//                  r shared-memory ORs, then one bulk OR of the plane into
+//                  the plane-major copy of the DHLA in L2
+//                  (cp.reduce.async.bulk ... .or.b32, so units of one plane
+//                  may run on several SMs).
+//   k_plane_fold   (window close, sd_get_grid, sd_merge) transposes the
+//                  plane-major copy into the estimator-major DHLA
+//                  (grid |= planes^T, 32 x 32 bit blocks by warp shuffles)
+//                  and clears it.
+//
+// Per pair this moves dirs keys (4 bytes each) through the bins instead of
+// r * dirs bit positions, and the plane copy is swept once per round by
+// the bulk reduction.  The result equals Algorithm 1's DHLA bit for bit: the
+// effective DHLA of a handle is grid | planes^T at all times, and every step
+// only ORs bits in.
+//
+// Plane-major layout: plane (d, b) is plane index d*g + b; its row i starts
+// at word i * 2^k/32 and holds estimator c's bit at word c >> 5, bit c & 31;
+// planes are ps words apart (r 2^k / 32 rounded up to 4 words).
+#include "sd_common.cuh"
+
+namespace sd {
+
+namespace {
+
+constexpr uint32_t kPlaneThreads = 512;   // k_plane_bin / k_plane_count block
+constexpr uint32_t kApplyThreads = 512;   // k_plane_apply block
+constexpr uint32_t kHeldReservations = 2;  // reservation results a thread holds across the scatter
+
+__device__ __forceinline__ uint32_t h1v(uint64_t A1, uint64_t B1, uint32_t lg, uint32_t y) {
+    return (uint32_t)((A1 * (uint64_t)y + B1) >> (64u - lg));
+}
+
+// 16-byte load that stays in L2 for the next kernel of the round.
+__device__ __forceinline__ uint4 ld_l2_v4(const uint4 *p) {
+    uint4 v;
+    asm("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+// Block-wide exclusive scan of get(0..N) written through put(i, prefix);
+// put(N, total) as well.  Each thread takes a contiguous chunk of indices.
+// Ends with a barrier; s_warp holds 32 words of shared scratch.
+template <typename Get, typename Put>
+__device__ __forceinline__ void block_scan(uint32_t N, Get get, Put put, uint32_t *s_warp) {
+    const uint32_t per = (N + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = min(threadIdx.x * per, N), i1 = min(i0 + per, N);
+    uint32_t sum = 0;
+    for (uint32_t i = i0; i < i1; i++) sum += get(i);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    __syncthreads();  // s_warp may still be read by an earlier scan
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t x = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if ((int)lane >= o) x += v;
+        }
+        if (lane < nw) s_warp[lane] = x;
+    }
+    __syncthreads();
+    uint32_t run = incl - sum + (wid ? s_warp[wid - 1] : 0u);
+    for (uint32_t i = i0; i < i1; i++) {
+        const uint32_t v = get(i);
+        put(i, run);
+        run += v;
+    }
+    if (threadIdx.x == blockDim.x - 1) put(N, run);
+    __syncthreads();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ count
+template <int DIRS>
+__global__ void __launch_bounds__(kPlaneThreads)
+k_plane_count(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArgs P) {
+    extern __shared__ uint32_t hist[];  // [nbins]
+    __shared__ uint32_t s_warp[32];
+    __shared__ bool s_last;
+    const uint32_t NB = P.nbins, g = G.g, lg = G.lg;
+    const uint64_t A1a = G.h[0].A1, B1a = G.h[0].B1, A1b = G.h[1].A1, B1b = G.h[1].B1;
+    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    auto count = [&](uint32_t s, uint32_t t) {
+        atomicAdd(&hist[h1v(A1a, B1a, lg, t)], 1u);
+        if (DIRS == 2) atomicAdd(&hist[g + h1v(A1b, B1b, lg, s)], 1u);
+    };
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (((uintptr_t)pairs & 15u) == 0) {
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(pairs);
+        const uint64_t n2 = n / 2;
+        for (uint64_t u = first; u < n2; u += stride) {
+            const uint4 v = ld_l2_v4(v4 + u);
+            count(v.x, v.y);
+            count(v.z, v.w);
+        }
+        if ((n & 1) && first == 0) count(pairs[2 * (n - 1)], pairs[2 * (n - 1) + 1]);
+    } else {
+        for (uint64_t p = first; p < n; p += stride) count(ld_stream_u32(pairs + 2 * p), ld_stream_u32(pairs + 2 * p + 1));
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x)
+        if (hist[b]) atomicAdd(&P.ntot[b], hist[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&P.ctl[0], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // the last block to finish: every count is in ntot
+    __threadfence();
+    const uint32_t U = P.unit;
+    block_scan(NB, [&](uint32_t i) { return (__ldcg(&P.ntot[i]) + 3u) & ~3u; },
+               [&](uint32_t i, uint32_t v) { P.binoff[i] = v; }, s_warp);
+    block_scan(NB, [&](uint32_t i) { return (__ldcg(&P.ntot[i]) + U - 1u) / U; },
+               [&](uint32_t i, uint32_t v) { P.unit_start[i] = v; }, s_warp);
+    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) {
+        P.ntot[b] = 0;
+        P.fill[b] = 0;
+    }
+    if (threadIdx.x == 0) {
+        P.ctl[0] = 0;
+        P.ctl[1] = 0;
+    }
+}
+
+// -------------------------------------------------------------------- bin
+// A thread keeps PPT pairs' DIRS entries in registers as (key, bin << 16 |
+// rank) while the block counts them per plane; the tile is then scattered
+// into plane order in shared memory and written out one thread per entry,
+// so each plane's run goes to consecutive addresses of its bin.
+template <int DIRS, int PPT>
+__global__ void __launch_bounds__(kPlaneThreads, 2)
+k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArgs P) {
+    constexpr int E = PPT * DIRS;
+    extern __shared__ uint32_t sm[];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t NB = P.nbins, g = G.g, lg = G.lg;
+    const uint32_t TP = blockDim.x * PPT;
+    uint32_t *hist = sm;                 // [NB] entries of each plane in the tile
+    uint32_t *offs = hist + NB;          // [NB] first sorted position of each plane
+    uint32_t *gdst = offs + NB;          // [NB] bin index of sorted position 0 (mod 2^32)
+    uint32_t *skey = gdst + NB;          // [DIRS TP] keys in plane order
+    uint16_t *sbin = reinterpret_cast<uint16_t *>(skey + (size_t)DIRS * TP);  // [DIRS TP]
+    const uint64_t A1a = G.h[0].A1, B1a = G.h[0].B1, A1b = G.h[1].A1, B1b = G.h[1].B1;
+    const uint64_t ntiles = (n + TP - 1) / TP;
+    const bool vec = ((uintptr_t)pairs & 15u) == 0;
+    // bins owned by this thread in the scan (contiguous chunk)
+    const uint32_t per = (NB + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = min(threadIdx.x * per, NB), b1 = min(b0 + per, NB);
+    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t base = t * TP;
+        const uint64_t left = n - base;
+        const uint32_t cnt = left < TP ? (uint32_t)left : TP;
+        uint32_t key[E], tag[E];
+#pragma unroll
+        for (int j = 0; j < PPT / 2; j++) {
+            const uint32_t pu = threadIdx.x + (uint32_t)j * blockDim.x;  // 2-pair unit within the tile
+            const uint64_t p = base + 2ull * pu;
+            uint32_t s0 = 0, t0 = 0, s1 = 0, t1 = 0;
+            const bool ok0 = 2 * pu < cnt, ok1 = 2 * pu + 1 < cnt;
+            if (vec && ok1) {
+                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p));
+                s0 = v.x; t0 = v.y; s1 = v.z; t1 = v.w;
+            } else {
+                if (ok0) { s0 = ld_stream_u32(pairs + 2 * p); t0 = ld_stream_u32(pairs + 2 * p + 1); }
+                if (ok1) { s1 = ld_stream_u32(pairs + 2 * p + 2); t1 = ld_stream_u32(pairs + 2 * p + 3); }
+            }
+            const uint32_t ss[2] = {s0, s1}, tt[2] = {t0, t1};
+            const bool ok[2] = {ok0, ok1};
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+#pragma unroll
+                for (int d = 0; d < DIRS; d++) {
+                    const int e = (2 * j + q) * DIRS + d;
+                    key[e] = d ? tt[q] : ss[q];
+                    const uint32_t b = d ? g + h1v(A1b, B1b, lg, ss[q]) : h1v(A1a, B1a, lg, tt[q]);
+                    tag[e] = 0xFFFFFFFFu;
+                    if (ok[q]) tag[e] = (b << 16) | atomicAdd(&hist[b], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        // planes of this thread's chunk: sorted offsets, and their runs
+        // reserved in the bins (the atomics' results are used after the
+        // scatter, so their round trip overlaps it)
+        uint32_t run = 0;
+        {
+            uint32_t sum = 0;
+            for (uint32_t b = b0; b < b1; b++) sum += hist[b];
+            const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            if (lane == 31) s_warp[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                uint32_t x = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if ((int)lane >= o) x += v;
+                }
+                if (lane < nw) s_warp[lane] = x;
+            }
+            __syncthreads();
+            run = incl - sum + (wid ? s_warp[wid - 1] : 0u);
+        }
+        // (the first kHeldReservations of a thread's planes keep their
+        // results in registers until after the scatter; with more planes per
+        // thread than that, the rest are resolved at once)
+        uint32_t res[kHeldReservations], rrun[kHeldReservations];
+#pragma unroll
+        for (uint32_t q = 0; q < kHeldReservations; q++) {
+            const uint32_t b = b0 + q;
+            res[q] = 0;
+            rrun[q] = run;
+            if (b < b1) {
+                const uint32_t h = hist[b];
+                offs[b] = run;
+                if (h) res[q] = atomicAdd(&P.fill[b], h);
+                hist[b] = 0;
+                run += h;
+            }
+        }
+        for (uint32_t b = b0 + kHeldReservations; b < b1; b++) {
+            const uint32_t h = hist[b];
+            offs[b] = run;
+            if (h) gdst[b] = P.binoff[b] + atomicAdd(&P.fill[b], h) - run;
+            hist[b] = 0;
+            run += h;
+        }
+        __syncthreads();
+        // scatter into plane order
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            if (tag[e] == 0xFFFFFFFFu) continue;
+            const uint32_t b = tag[e] >> 16;
+            const uint32_t pos = offs[b] + (tag[e] & 0xFFFFu);
+            skey[pos] = key[e];
+            sbin[pos] = (uint16_t)b;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kHeldReservations; q++) {
+            const uint32_t b = b0 + q;
+            if (b < b1) gdst[b] = P.binoff[b] + res[q] - rrun[q];
+        }
+        __syncthreads();
+        // write-out: sorted entry q of plane b goes to bins[gdst[b] + q]
+        const uint32_t nent = cnt * DIRS;
+        for (uint32_t q = threadIdx.x; q < nent; q += blockDim.x) {
+            const uint32_t b = sbin[q];
+            __stcs(P.bins + (uint32_t)(gdst[b] + q), skey[q]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ apply
+template <int R>
+__device__ __forceinline__ void apply_key(uint32_t *pl, const Geometry &G, uint32_t A0, uint32_t rw, uint32_t key) {
+    const uint32_t c0 = dh0(A0, G.k, key);
+    atomicOr(&pl[c0 >> 5], 1u << (c0 & 31u));
+#pragma unroll
+    for (int i = 1; i < R; i++) {
+        const uint32_t ci = dh_row(G, (uint32_t)i, key, c0);
+        atomicOr(&pl[(uint32_t)i * rw + (ci >> 5)], 1u << (ci & 31u));
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kApplyThreads)
+k_plane_apply(Geometry G, PlaneArgs P) {
+    extern __shared__ uint4 pl4[];  // the plane, ps words
+    __shared__ uint32_t s_unit;
+    uint32_t *pl = reinterpret_cast<uint32_t *>(pl4);
+    const uint32_t NB = P.nbins;
+    const uint32_t rw = (1u << G.k) >> 5;
+    const uint32_t total = P.unit_start[NB];
+    for (;;) {
+        __syncthreads();  // the previous unit's bulk reduction has read the plane
+        if (threadIdx.x == 0) s_unit = atomicAdd(&P.ctl[1], 1u);
+        __syncthreads();
+        const uint32_t x = s_unit;
+        if (x >= total) break;
+        uint32_t lo = 0, hi = NB;  // the plane b with unit_start[b] <= x < unit_start[b + 1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (P.unit_start[mid] <= x) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t b = lo;
+        const uint32_t beg = P.binoff[b] + (x - P.unit_start[b]) * P.unit;
+        const uint32_t stop = P.binoff[b] + P.fill[b];
+        const uint32_t end = stop - beg < P.unit ? stop : beg + P.unit;
+        const uint32_t A0 = (b >> G.lg) ? G.h[1].A0 : G.h[0].A0;
+        for (uint32_t i = threadIdx.x; i < P.ps / 4; i += blockDim.x) pl4[i] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        const uint4 *e4 = reinterpret_cast<const uint4 *>(P.bins + beg);  // beg is a multiple of 4
+        const uint32_t n4 = (end - beg) / 4;
+        uint32_t q = threadIdx.x;
+        for (; q + blockDim.x < n4; q += 2 * blockDim.x) {
+            const uint4 a = ld_stream_v4(e4 + q), c = ld_stream_v4(e4 + q + blockDim.x);
+            apply_key<R>(pl, G, A0, rw, a.x); apply_key<R>(pl, G, A0, rw, a.y);
+            apply_key<R>(pl, G, A0, rw, a.z); apply_key<R>(pl, G, A0, rw, a.w);
+            apply_key<R>(pl, G, A0, rw, c.x); apply_key<R>(pl, G, A0, rw, c.y);
+            apply_key<R>(pl, G, A0, rw, c.z); apply_key<R>(pl, G, A0, rw, c.w);
+        }
+        if (q < n4) {
+            const uint4 a = ld_stream_v4(e4 + q);
+            apply_key<R>(pl, G, A0, rw, a.x); apply_key<R>(pl, G, A0, rw, a.y);
+            apply_key<R>(pl, G, A0, rw, a.z); apply_key<R>(pl, G, A0, rw, a.w);
+        }
+        for (uint32_t r = beg + 4 * n4 + threadIdx.x; r < end; r += blockDim.x)
+            apply_key<R>(pl, G, A0, rw, ld_stream_u32(P.bins + r));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // the plane's bits into the plane-major DHLA copy, ORed in L2
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.or.b32 [%0], [%1], %2;"
+                         ::"l"(P.planes + (uint64_t)b * P.ps), "r"((uint32_t)__cvta_generic_to_shared(pl)),
+                         "r"(P.ps * 4u)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+    }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ------------------------------------------------------------------- fold
+// One warp per (direction, row, 32 estimators): for each word t of those
+// estimators, lane j reads word w of plane 32t + j (bit l = estimator 32w+l
+// of that plane), a 32 x 32 bit transpose by shuffles gives lane l word t of
+// estimator 32w + l, staged in shared memory; then the 32 estimators'
+// words are ORed into the DHLA (contiguous) and the plane words cleared.
+__global__ void __launch_bounds__(256)
+k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometry G, uint32_t ps) {
+    extern __shared__ uint32_t stg[];  // [8 warps][32 estimators][wpc + 1]
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t wpc = G.wpc, sp = wpc + 1;
+    uint32_t *my = stg + (size_t)wid * 32 * sp;
+    const uint32_t rw = (1u << G.k) >> 5;
+    const uint64_t items = (uint64_t)G.dirs * G.r * rw;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wid; it < items; it += nwarps) {
+        const uint32_t w = (uint32_t)(it % rw);
+        const uint32_t di = (uint32_t)(it / rw);
+        const uint32_t d = di / G.r, i = di - d * G.r;
+        for (uint32_t t = 0; t < wpc; t++) {
+            uint32_t *src = planes + (uint64_t)(d * G.g + 32u * t + lane) * ps + (uint64_t)i * rw + w;
+            uint32_t x = *src;
+            if (x) *src = 0u;
+            // transpose the 32 x 32 bit block held one row per lane
+#pragma unroll
+            for (uint32_t j = 16; j > 0; j >>= 1) {
+                const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                                 : j == 2 ? 0x33333333u : 0x55555555u;
+                const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+                x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+            }
+            my[lane * sp + t] = x;  // word t of estimator 32w + lane
+        }
+        __syncwarp();
+        uint32_t *dst = grid + (uint64_t)d * G.dir_words + (uint64_t)i * G.row_words + (uint64_t)(32u * w) * wpc;
+        for (uint32_t q = lane; q < 32u * wpc; q += 32u) {
+            const uint32_t c = q / wpc, tq = q - c * wpc;
+            const uint32_t v = my[c * sp + tq];
+            if (v) dst[q] |= v;
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------------------- launchers
+size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins) {
+    return (size_t)3 * nbins * 4 + (size_t)dirs * tile_pairs * 6;
+}
+
+template <int DIRS, int PPT>
+static cudaError_t launch_plane_bin(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P,
+                                    int num_sms, cudaStream_t s) {
+    auto kern = k_plane_bin<DIRS, PPT>;
+    const size_t smem = plane_bin_smem_bytes(P.tile_pairs, DIRS, P.nbins);
+    int per_sm = 0;
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kPlaneThreads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t tiles = (n + P.tile_pairs - 1) / P.tile_pairs;
+    uint64_t blocks = (uint64_t)num_sms * per_sm;
+    if (tiles < blocks) blocks = tiles;
+    kern<<<(unsigned)blocks, kPlaneThreads, smem, s>>>(pairs, n, G, P);
+    return cudaGetLastError();
+}
+
+template <int DIRS>
+static cudaError_t launch_plane_bin_d(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P,
+                                      int num_sms, cudaStream_t s) {
+    switch (P.tile_pairs / kPlaneThreads) {
+        case 2: return launch_plane_bin<DIRS, 2>(pairs, n, G, P, num_sms, s);
+        case 4: return launch_plane_bin<DIRS, 4>(pairs, n, G, P, num_sms, s);
+        case 8: return launch_plane_bin<DIRS, 8>(pairs, n, G, P, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, int num_sms, cudaStream_t s) {
+    auto kern = k_plane_apply<R>;
+    const size_t smem = (size_t)P.ps * 4;
+    int per_sm = 0;
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kApplyThreads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(num_sms * per_sm), kApplyThreads, smem, s>>>(G, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    // count
+    {
+        auto kern = G.dirs == 2 ? k_plane_count<2> : k_plane_count<1>;
+        const size_t smem = (size_t)P.nbins * 4;
+        int per_sm = 0;
+        cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kPlaneThreads, smem, &per_sm);
+        if (e != cudaSuccess) return e;
+        uint64_t blocks = (uint64_t)num_sms * per_sm;
+        const uint64_t need = (n / 2 + kPlaneThreads - 1) / kPlaneThreads;
+        if (need < blocks) blocks = need ? need : 1;
+        kern<<<(unsigned)blocks, kPlaneThreads, smem, s>>>(pairs, n, G, P);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    cudaError_t e = G.dirs == 2 ? launch_plane_bin_d<2>(pairs, n, G, P, num_sms, s)
+                                : launch_plane_bin_d<1>(pairs, n, G, P, num_sms, s);
+    if (e != cudaSuccess) return e;
+    switch (G.r) {
+        case 3: return launch_plane_apply<3>(G, P, num_sms, s);
+        case 4: return launch_plane_apply<4>(G, P, num_sms, s);
+        case 5: return launch_plane_apply<5>(G, P, num_sms, s);
+        case 6: return launch_plane_apply<6>(G, P, num_sms, s);
+        case 7: return launch_plane_apply<7>(G, P, num_sms, s);
+        case 8: return launch_plane_apply<8>(G, P, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
+                              cudaStream_t s) {
+    const size_t smem = (size_t)8 * 32 * (G.wpc + 1) * 4;
+    int per_sm = 0;
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), 256, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t items = (uint64_t)G.dirs * G.r * (((uint64_t)1 << G.k) >> 5);
+    uint64_t blocks = (uint64_t)num_sms * per_sm;
+    if ((items + 7) / 8 < blocks) blocks = (items + 7) / 8;
+    k_plane_fold<<<(unsigned)blocks, 256, smem, s>>>(grid, planes, G, ps);
+    return cudaGetLastError();
+}
+
+}  // namespace sd

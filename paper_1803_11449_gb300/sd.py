@@ -72,7 +72,8 @@ class sd_tuning(ctypes.Structure):
                 ("filter_log2", ctypes.c_uint32), ("bin_slice_log2", ctypes.c_uint32),
                 ("bin_tile_pairs", ctypes.c_uint32), ("bin_chunk_log2", ctypes.c_uint32),
                 ("bin_slack_pct", ctypes.c_uint32), ("restore", ctypes.c_uint32),
-                ("bin_batch_mib", ctypes.c_uint32)]
+                ("bin_batch_mib", ctypes.c_uint32), ("plane_tile_pairs", ctypes.c_uint32),
+                ("plane_round_log2", ctypes.c_uint32), ("plane_unit_log2", ctypes.c_uint32)]
 
 
 HIT_DTYPE = np.dtype([("ip", "<u4"), ("sz", "<u4"), ("dir", "<u4"), ("reserved", "<u4"),
@@ -345,11 +346,13 @@ def sd_get_tuning(h: Handle) -> sd_tuning:
 
 def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0, filter_log2=0,
                   bin_slice_log2=0, bin_tile_pairs=0, bin_chunk_log2=0, bin_slack_pct=0, restore=0,
-                  bin_batch_mib=0) -> None:
+                  bin_batch_mib=0, plane_tile_pairs=0, plane_round_log2=0, plane_unit_log2=0) -> None:
     t = sd_tuning(mode=mode, block_threads=block_threads, blocks_per_sm=blocks_per_sm, unroll=unroll,
                   filter_log2=filter_log2, bin_slice_log2=bin_slice_log2,
                   bin_tile_pairs=bin_tile_pairs, bin_chunk_log2=bin_chunk_log2,
-                  bin_slack_pct=bin_slack_pct, restore=restore, bin_batch_mib=bin_batch_mib)
+                  bin_slack_pct=bin_slack_pct, restore=restore, bin_batch_mib=bin_batch_mib,
+                  plane_tile_pairs=plane_tile_pairs, plane_round_log2=plane_round_log2,
+                  plane_unit_log2=plane_unit_log2)
     _check(lib().sd_set_tuning(h.ptr, ctypes.byref(t)), h.ptr)
 
 

@@ -44,7 +44,7 @@ def test_struct_sizes_match_the_header(sdmod):
     assert ctypes.sizeof(sdmod.sd_params) == 80
     assert ctypes.sizeof(sdmod.sd_hit) == 24
     assert ctypes.sizeof(sdmod.sd_report) == 272
-    assert ctypes.sizeof(sdmod.sd_tuning) == 44
+    assert ctypes.sizeof(sdmod.sd_tuning) == 56
 
 
 def test_default_params_and_grid_words(sdmod):

@@ -94,14 +94,22 @@ def test_join_three_rows(sd, O):
 def test_join_overloads(sd, O):
     w = T.WORKLOADS["tiny"].with_(dirs=1)
     win = T.make_window(w, T.window_seed(1))
-    # intermediate buffers of 4 cand_cap entries overflow: the direction is flagged
+    # intermediate buffers of 4 cand_cap entries overflow: the direction is
+    # flagged, reports nothing, and gives |K| as cand_cap + 1
     p, rep, _ = _run(sd, w, win.pairs, 5, restore=1, cand_cap=64)
     assert rep.dir_flags(0) & sd.SD_FLAG_OVERLOAD_CANDS and len(rep.hits) == 0
-    # first-stage tuples above pair_cap, (c0, c1) pairs within it
+    assert rep.n_cand[0] == 65
+    # first-stage tuples |HE(0)||HE(1)||HE(2)| above pair_cap while the
+    # common work bound |HE(0)| 2^(32-k) stays within it (k = 16 and hot
+    # lists of about 300: |HE(1)||HE(2)| > 2^16)
+    w = T.WORKLOADS["core"].with_(n=1 << 22, planted=40, planted_c=("loguniform", 1024, 20000),
+                                  src_pool=1 << 20, dst_pool=1 << 22)
+    win = T.make_window(w, 99)
     n = [int(x) for x in O.close_window(*_oracle_grid(O, w, win.pairs, 5))["n_hot"][0][:3]]
     cap = n[0] * n[1] * n[2] - 1
+    assert (n[0] << (32 - w.k)) <= cap
     p, rep, _ = _run(sd, w, win.pairs, 5, restore=1, pair_cap=cap)
-    assert rep.dir_flags(0) & sd.SD_FLAG_OVERLOAD_PAIRS
+    assert rep.dir_flags(0) & sd.SD_FLAG_OVERLOAD_PAIRS and rep.n_cand[0] == 0
     p, rep, _ = _run(sd, w, win.pairs, 5, restore=0, pair_cap=cap)
     assert rep.dir_flags(0) == 0 and len(rep.hits) > 0
 

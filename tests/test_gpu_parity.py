@@ -100,7 +100,7 @@ def test_tiny_window_full_parity(sd, O, torch_mod):
 @pytest.mark.parametrize("mode,unroll,threads,flog", [
     (0, 1, 256, 13), (0, 4, 1024, 13), (1, 2, 512, 13), (2, 2, 512, 13), (2, 4, 256, 13),
     (1, 1, 128, 13), (3, 2, 512, 13), (3, 1, 1024, 14), (3, 4, 256, 8), (4, 2, 512, 12),
-    (4, 1, 64, 8), (5, 2, 512, 13)])
+    (4, 1, 64, 8), (5, 2, 512, 13), (6, 2, 512, 13)])
 def test_update_variants_give_identical_grids(sd, O, torch_mod, mode, unroll, threads, flog):
     w = T.WORKLOADS["tiny"].with_(dirs=2, n=(1 << 19) + 3)
     win = T.make_window(w, 8)
@@ -118,7 +118,9 @@ def test_filter_modes_on_heavy_hitters(sd, O, torch_mod):
     win = T.make_window(w, 19)
     for tuning in (dict(mode=3, filter_log2=10), dict(mode=4, filter_log2=10),
                    dict(mode=5, bin_chunk_log2=19, bin_slack_pct=0xFFFFFFFF),
-                   dict(mode=5, bin_chunk_log2=21, bin_slack_pct=400)):
+                   dict(mode=5, bin_chunk_log2=21, bin_slack_pct=400),
+                   dict(mode=6, plane_round_log2=19, plane_unit_log2=10),
+                   dict(mode=6, plane_round_log2=21, plane_unit_log2=20, plane_tile_pairs=1024)):
         _full_check(sd, O, torch_mod, w, win, tuning=tuning)
 
 
@@ -135,7 +137,58 @@ def test_binned_update_variants(sd, O, torch_mod, slice_log2, tile, chunk_log2, 
                             bin_chunk_log2=chunk_log2, bin_slack_pct=slack))
 
 
-@pytest.mark.parametrize("mode", [1, 3, 5])
+@pytest.mark.parametrize("tile,round_log2,unit_log2", [
+    (4096, 22, 15), (1024, 10, 8), (2048, 16, 12), (4096, 13, 24), (1024, 18, 9)])
+@pytest.mark.parametrize("dirs", [1, 2])
+def test_plane_update_variants(sd, O, torch_mod, tile, round_log2, unit_log2, dirs):
+    """Mode 6 (binned by estimator bit) with tiles, rounds and apply units
+    from tiny (many rounds of one partial tile; apply units of 256 keys, so
+    a plane's bin is split over many blocks) to one round; ragged pair
+    count."""
+    w = T.WORKLOADS["tiny"].with_(dirs=dirs, n=(1 << 19) + 5)
+    win = T.make_window(w, 23)
+    _full_check(sd, O, torch_mod, w, win,
+                tuning=dict(mode=6, plane_tile_pairs=tile, plane_round_log2=round_log2,
+                            plane_unit_log2=unit_log2))
+
+
+def test_plane_update_keeps_bits_across_calls_and_modes(sd, O, torch_mod):
+    """The DHLA of a handle in mode 6 is its DHLA plus the pending planes:
+    updates of several calls, a switch to another mode in mid-window, a
+    checkpoint read (which folds the planes) and more mode-6 updates all
+    end in Algorithm 1's DHLA of the whole stream."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    win = T.make_window(w, 71)
+    parts = np.array_split(win.pairs, 5)
+    p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    h = sd.sd_create(p)
+    try:
+        assert sd.sd_get_tuning(h).mode == 6
+        sd.sd_update(h, _dev(torch_mod, parts[0]))
+        sd.sd_update(h, _dev(torch_mod, parts[1]))
+        sd.sd_set_tuning(h, mode=5)
+        sd.sd_update(h, _dev(torch_mod, parts[2]))
+        mid = _grids(sd, h)
+        sd.sd_set_tuning(h, mode=6)
+        sd.sd_update(h, _dev(torch_mod, parts[3]))
+        sd.sd_set_tuning(h, mode=1)
+        sd.sd_update(h, _dev(torch_mod, parts[4]))
+        sd.sd_set_tuning(h, mode=6)
+        grid = _grids(sd, h)
+        rep = sd.sd_close_window(h)
+        after = _grids(sd, h)
+    finally:
+        sd.sd_destroy(h)
+    op = O.params_from(w.sketch(), seed=SEED)
+    og = O.new_grid(op)
+    O.update(op, og, np.concatenate(parts[:3]))
+    assert np.array_equal(mid, og)
+    _, og, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert np.array_equal(grid, og) and not after.any()
+    _assert_report_equal(O, rep, ref, p)
+
+
+@pytest.mark.parametrize("mode", [1, 3, 5, 6])
 def test_ragged_and_misaligned_inputs(sd, O, torch_mod, mode):
     """Odd pair counts and buffers starting 8 or 4 bytes past a 16-byte
     boundary take the head/tail and unaligned paths."""
@@ -230,7 +283,7 @@ def test_core_and_paper_parameters_small_window(sd, O, torch_mod, name):
     _full_check(sd, O, torch_mod, w, T.make_window(w, 99))
 
 
-@pytest.mark.parametrize("mode", [None, 1, 5])
+@pytest.mark.parametrize("mode", [None, 1, 5, 6])
 def test_core_link_window_full_size(sd, O, torch_mod, mode):
     """The benchmarked workload itself: 2^26 pairs, g=512, r=4, k=16, both
     directions; the default launch configuration and the update modes the
@@ -303,6 +356,41 @@ def _core_window():
     return _CORE["win"]
 
 
+def test_paper_parameter_full_window_overloads_quickly(sd, O, torch_mod):
+    """The paper's own sketch (g=1024, r=5, k=14, alpha=6: 10 MiB per
+    direction) on the full 2^26-pair core-link window: it saturates, most
+    estimators are hot and |K| is far above cand_cap.  Both sides flag the
+    overload the same way (|K| reported as cand_cap + 1), and the close
+    stops once K passes its capacity instead of enumerating ~10^9
+    candidates: under 5 ms."""
+    import time
+    w = T.WORKLOADS["paper"]
+    win = _core_window()   # the same traffic recipe and seed as the core window
+    p = sd.params_for(w, SEED, cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
+    dev = _dev(torch_mod, win.pairs)
+    h = sd.sd_create(p)
+    try:
+        sd.sd_update(h, dev)
+        grid = _grids(sd, h)
+        rep = sd.sd_close_window(h)
+        times = []
+        for _ in range(3):    # the same window again, timed without first-use allocations
+            sd.sd_update(h, dev)
+            sd.sd_sync(h)
+            t0 = time.perf_counter()
+            again = sd.sd_close_window(h)
+            times.append(time.perf_counter() - t0)
+            assert again.flags == rep.flags and again.n_cand == rep.n_cand
+    finally:
+        sd.sd_destroy(h)
+    op, og, ref = _oracle_run(O, w, win.pairs, SEED)
+    assert np.array_equal(grid, og), "DHLA bits differ"
+    _assert_report_equal(O, rep, ref, p)
+    assert all(f & O.FLAG_OVERLOAD_CANDS for f in ref["flags"])
+    assert rep.n_cand == [(p.cand_cap or (1 << 20)) + 1] * 2 and rep.rc == sd.SD_ERR_OVERLOAD
+    assert min(times) < 5e-3, times
+
+
 def test_saturated_row(sd, O, torch_mod):
     w = T.WORKLOADS["tiny"]
     win = T.make_window(w, 3)
@@ -326,15 +414,21 @@ def test_saturated_row(sd, O, torch_mod):
 
 
 def test_overload_caps(sd, O, torch_mod):
+    """Each cap on each side of its boundary: the work bound |HE(0)| 2^(32-k)
+    against pair_cap, and |K| against cand_cap (an overloaded |K| is
+    reported as cand_cap + 1 by both sides)."""
     w = T.WORKLOADS["tiny"]
     win = T.make_window(w, T.window_seed(1))
     _, _, full = _oracle_run(O, w, win.pairs, SEED)
-    nh = full["n_hot"][0]
-    for caps in (dict(pair_cap=int(nh[0] * nh[1]) - 1), dict(cand_cap=full["n_cand"][0] - 1),
-                 dict(cand_cap=full["n_cand"][0])):
+    work = int(full["n_hot"][0][0]) << (32 - w.k)
+    nk = full["n_cand"][0]
+    for caps in (dict(pair_cap=work - 1), dict(pair_cap=work), dict(cand_cap=nk - 1), dict(cand_cap=nk),
+                 dict(cand_cap=nk // 5)):
         rep, ref = _full_check(sd, O, torch_mod, w, win, **caps)
         if ref["flags"][0]:
             assert rep.rc == sd.SD_ERR_OVERLOAD and rep.n_hits_total == 0
+        if "cand_cap" in caps and caps["cand_cap"] < nk:
+            assert rep.n_cand[0] == caps["cand_cap"] + 1
 
 
 def test_report_cap_truncates_in_order(sd, O, torch_mod):
