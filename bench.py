@@ -127,30 +127,90 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, power,
+    clock-event reasons); None when the library is absent."""
+    SM = 1
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.L = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.L.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.L.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        fn = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn or self.L.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        c = self.ct
+        mhz, mx, mw, rs = c.c_uint(), c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, self.SM, c.byref(mhz)) != 0:
+            return None
+        self.L.nvmlDeviceGetMaxClockInfo(self.h, self.SM, c.byref(mx))
+        self.L.nvmlDeviceGetPowerUsage(self.h, c.byref(mw))
+        self.reasons_fn(self.h, c.byref(rs))
+        return (float(mhz.value), float(mx.value), mw.value / 1000.0, int(rs.value))
+
+    def close(self):
+        self.L.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed
-    region (read-only queries)."""
+    """SM clock and clock-event reasons sampled during the timed region
+    (read-only queries): NVML every 2 ms from a thread, else nvidia-smi
+    every 10 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
+        self.period = period_s
         self.proc = None
         self.tmp = None
+        self.nvml = None
+        self.rows = []
+        self.thread = None
+        self.stop = None
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = _Nvml(self.index)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.stop = threading.Event()
+
+            def run():
+                while not self.stop.is_set():
+                    r = self.nvml.sample()
+                    if r is not None:
+                        self.rows.append(r)
+                    self.stop.wait(self.period)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def __exit__(self, *exc):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            self.nvml.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -159,6 +219,14 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.rows:
+                return None
+            reasons = sorted({n for r in self.rows for n, b in self.BITS.items() if r[3] & b})
+            return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                    "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
+                    "samples": len(self.rows), "power_w_max": max(r[2] for r in self.rows),
+                    "source": f"NVML every {self.period * 1e3:.0f} ms"}
         if self.proc is None or self.tmp is None:
             return None
         self.tmp.flush()
@@ -176,7 +244,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "source": "nvidia-smi every 10 ms"}
 
 
 def dist_setup(n_gpus: int):

@@ -281,6 +281,66 @@ int64_t sd_get_candidates(sd_handle *h, uint32_t dir, uint32_t *host_dst, uint64
  * streams.  Stream-ordered after the work already queued on both handles. */
 int sd_merge(sd_handle *dst, sd_handle *src);
 
+/* ------------------------------------------------------------------------
+ * Several GPUs.  Two ways to spread a detection over GPUs follow from the
+ * paper; the collectives themselves (NCCL or any other transport) are the
+ * caller's, these calls are the device steps around them.
+ *
+ * Stream split, then merge (§4.2: the local DHLAs of several monitors or
+ * GPUs merged into a global DHLA, read as a bitwise OR): each GPU runs
+ * sd_update on its part of the window's stream; the DHLA images are
+ * exported, ORed across GPUs (e.g. a reduce-scatter by all-to-all whose
+ * parts sd_or_words combines, then an all-gather), ORed back into each
+ * handle with sd_or_grid, and the window closed.  The merged DHLA equals
+ * the DHLA of the whole stream, so the report is the one-GPU report.
+ *
+ * Key partition (§5: hosts divided by the low bits of their address): each
+ * direction's pairs are grouped by key & (parts - 1) with
+ * sd_partition_pairs, each group sent to the GPU that owns those keys
+ * (e.g. an all-to-all), and fed there with sd_update_dir; each GPU's DHLA
+ * holds its own keys only and nothing is merged.  A GPU's report is valid
+ * for its own keys (hits of other keys are estimator collisions and are
+ * dropped by the caller).
+ * ------------------------------------------------------------------------ */
+
+/* Algorithm 1 for direction `dir` alone: `pairs` holds n (key, peer) pairs
+ * of that direction, interleaved -- (src, dst) for direction 0, (dst, src)
+ * for direction 1 -- with the same memory rules as sd_update.  Used to feed
+ * a key partition (each direction's keys arrive separately).  The window's
+ * n_pairs counts the pairs given to sd_update and, of sd_update_dir, those
+ * of direction 0. */
+int sd_update_dir(sd_handle *h, uint32_t dir, const uint32_t *pairs, uint64_t n);
+
+/* Copy h's DHLA, both directions in the sd_get_grid layout (dirs *
+ * sd_grid_words words, direction 0 first), to `dst`: 16-byte aligned device
+ * memory on h's device.  Stream-ordered on h's stream; returns once queued
+ * (the image of the DHLA as of the work queued before it). */
+int sd_export_grid(sd_handle *h, uint32_t *dst);
+
+/* h's DHLA |= the image at `src` (layout as sd_export_grid; 16-byte aligned
+ * device memory on h's device): the §4.2 merge of local DHLAs, read as a
+ * bitwise OR, so the result is the DHLA of the union of the streams.
+ * Stream-ordered on h's stream; `src` must stay valid until it has run. */
+int sd_or_grid(sd_handle *h, const uint32_t *src);
+
+/* dst[j] = src[j] | src[words + j] | ... | src[(count-1) words + j] for
+ * j < words: the OR of `count` DHLA parts laid end to end (the reduction
+ * step of an OR all-reduce; no collective library offers a bitwise-OR
+ * reduction).  words must be a multiple of 4; dst and src are 16-byte
+ * aligned device memory of the current device.  Runs on `cuda_stream`
+ * (NULL: the legacy default stream); returns once queued. */
+int sd_or_words(uint32_t *dst, const uint32_t *src, uint64_t words, uint32_t count, void *cuda_stream);
+
+/* Group n (src, dst) pairs (device memory on h's device) by the key of
+ * direction dir (src for 0, dst for 1): `out` (2n words, device memory)
+ * receives (key, peer) pairs part by part, part q = key & (parts - 1) for
+ * q = 0..parts-1 (within a part in no particular order), and counts[q]
+ * (host) the pairs of part q.  parts is a power of two up to 1024.  Runs on
+ * h's stream and blocks until `out` and counts are complete (the counts
+ * size the caller's exchange).  §5's division of hosts by their low bits. */
+int sd_partition_pairs(sd_handle *h, uint32_t dir, const uint32_t *pairs, uint64_t n, uint32_t parts,
+                       uint32_t *out, uint64_t *counts);
+
 /* Number of CUDA kernels the library has launched in this process, over all
  * handles (the init clear of sd_create included); for benchmarks that report
  * their launch count. */

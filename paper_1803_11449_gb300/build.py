@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsd.so")
-SOURCES = ["sd_update.cu", "sd_binned.cu", "sd_plane.cu", "sd_close.cu", "sd_join.cu", "sd_api.cu",
-           "sd_noalloc.cu"]
+SOURCES = ["sd_update.cu", "sd_binned.cu", "sd_plane.cu", "sd_close.cu", "sd_join.cu", "sd_shard.cu",
+           "sd_api.cu", "sd_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "sd_common.cuh"), os.path.join(INCLUDE, "sd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",

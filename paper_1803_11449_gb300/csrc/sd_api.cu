@@ -233,6 +233,12 @@ struct sd_handle {
     uint64_t plane_mem_words = 0;
     PlaneArgs pa{};
     bool planes_dirty = false;
+    uint64_t plane_layout_pairs = 0;   // round size the device's bin layout was made for (0: none)
+    int plane_layout_view = -2;        // the directions it was made for (-1 both, else one)
+
+    // key partition (sd_partition_pairs): per-part counts and cursors
+    unsigned long long *part_d = nullptr;  // [2][1024]
+    unsigned long long *part_h = nullptr;  // pinned [1024]
 
     // batched update (sd_update_many): link tables in two halves used by
     // alternate calls (a half is rewritten once the call two back has read
@@ -284,7 +290,12 @@ cudaError_t prepare_launch(const void *kernel, int threads, size_t smem, int *pe
             *per_sm = k.per_sm;
             return cudaSuccess;
         }
-    if (smem > 48 * 1024) {
+    // dynamic shared memory beyond the default 48 KiB (counting the kernel's
+    // static shared memory, which shares that limit) needs an opt-in
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (smem + fa.sharedSizeBytes > 48 * 1024) {
         size_t *have = nullptr;
         for (auto &p : g_smem_set)
             if (p.first.first == kernel && p.first.second == dev) have = &p.second;
@@ -400,6 +411,8 @@ static void release(sd_handle *h) {
     cudaFree(h->bin_mem);
     cudaFree(h->planes);
     cudaFree(h->plane_mem);
+    cudaFree(h->part_d);
+    cudaFreeHost(h->part_h);
     cudaFree(h->he_all);
     cudaFree(h->jsub);
     cudaFree(h->cj_d);
@@ -446,7 +459,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     // a DHLA of 1024 slices or more takes 2048-pair tiles, so that each
     // slice's run in a tile stays long enough for coalesced bin writes
     // (autotuned on the 2 x 128 MiB stress sketch: 50 ms vs 72 ms per 2^30 pairs)
-    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192, 4096, 22, 15};
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192, 4096, 23, 15};
     if ((uint64_t)p->dirs * G.dir_words >= (1ull << 25) && p->dirs * p->r <= 8) h->T.bin_tile_pairs = 2048;
     // binned by estimator bit wherever one bit plane fits a block's shared
     // memory (r 2^k bits: every workload of the scope table)
@@ -576,8 +589,14 @@ static int ensure_bins(sd_handle *h, bool *ok) {
 }
 
 // Layout of the plane-binned update for the current tuning: bins for one
-// round of 2^plane_round_log2 pairs (dirs keys per pair, each plane's bin
-// padded to 4 entries), the counters, and the plane-major DHLA copy.
+// round of 2^plane_round_log2 pairs (dirs keys per pair; each plane's bin
+// holds its count of the previous round plus an eighth and 32 slots, rounded
+// up to 4), the counters, and the plane-major DHLA copy.
+constexpr uint64_t kPlaneCounterWords = 4;  // words after the 4 nbins + 2 per-plane arrays
+static uint64_t plane_bin_words(const Geometry &G, uint64_t round) {
+    const uint64_t keys = (uint64_t)G.dirs * round;
+    return keys + keys / 8 + 40ull * G.dirs * G.g;
+}
 static void plane_layout(const sd_handle *h, PlaneArgs *P, uint64_t *mem_words, uint64_t *plane_copy_words) {
     const Geometry &G = h->G;
     std::memset(P, 0, sizeof *P);
@@ -585,9 +604,8 @@ static void plane_layout(const sd_handle *h, PlaneArgs *P, uint64_t *mem_words, 
     P->ps = plane_words(G);
     P->unit = 1u << h->T.plane_unit_log2;
     P->tile_pairs = h->T.plane_tile_pairs;
-    const uint64_t round = 1ull << h->T.plane_round_log2;
-    const uint64_t bins = (uint64_t)G.dirs * round + 4ull * P->nbins;
-    *mem_words = bins + 4ull * P->nbins + 2 + 4;
+    const uint64_t bins = plane_bin_words(G, 1ull << h->T.plane_round_log2);
+    *mem_words = bins + 4ull * P->nbins + 2 + kPlaneCounterWords;
     *plane_copy_words = (uint64_t)P->nbins * P->ps;
 }
 
@@ -608,17 +626,21 @@ static int ensure_plane_mem(sd_handle *h) {
         SD_CK(h, cudaMalloc(&h->plane_mem, words * 4));
         h->plane_mem_words = words;
     }
-    const uint64_t bins = words - (4ull * P.nbins + 2 + 4);
-    uint32_t *c = h->plane_mem + bins;
+    const uint64_t cwords = 4ull * P.nbins + 2 + kPlaneCounterWords;
+    uint32_t *c = h->plane_mem + (words - cwords);
     P.bins = h->plane_mem;
-    P.ntot = c;
+    P.cnt = c;
     P.binoff = c + P.nbins;
-    P.fill = c + 2 * P.nbins + 1;
+    P.cap = c + 2 * P.nbins + 1;
     P.unit_start = c + 3 * P.nbins + 1;
     P.ctl = c + 4 * P.nbins + 2;
     P.planes = h->planes;
-    if (P.ntot != h->pa.ntot || P.nbins != h->pa.nbins)  // new counters: ntot, fill and ctl start at zero
-        SD_CK(h, cudaMemsetAsync(c, 0, (4ull * P.nbins + 2 + 4) * 4, h->stream));
+    if (P.cnt != h->pa.cnt || P.nbins != h->pa.nbins) {
+        // new counters start at zero, with no bin layout yet
+        SD_CK(h, cudaMemsetAsync(c, 0, cwords * 4, h->stream));
+        h->plane_layout_pairs = 0;
+        h->plane_layout_view = -2;
+    }
     h->pa = P;
     return SD_OK;
 }
@@ -633,16 +655,37 @@ static int fold_planes(sd_handle *h) {
     return SD_OK;
 }
 
-// Algorithm 1 over n device-resident pairs, with the handle's tuning.
-static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+// Algorithm 1 over n device-resident pairs, with the handle's tuning: both
+// directions of (src, dst) pairs (dir < 0), or direction dir alone of
+// (key, peer) pairs.  A single direction runs the same kernels on a
+// one-direction view of the DHLA: that direction's hash constants and its
+// part of the DHLA (and of the plane copy).
+static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n, int dir = -1) {
+    Geometry G = h->G;
+    uint32_t *grid = h->grid;
+    if (dir >= 0) {
+        G.dirs = 1;
+        G.h[0] = h->G.h[dir];
+        grid += (uint64_t)dir * h->G.dir_words;
+    }
     if (h->T.mode == 6) {
         const int rc = ensure_plane_mem(h);
         if (rc != SD_OK) return rc;
+        PlaneArgs P = h->pa;
+        if (dir >= 0) {
+            P.nbins = h->G.g;
+            P.planes += (uint64_t)dir * h->G.g * P.ps;
+        }
         const uint64_t round = 1ull << h->T.plane_round_log2;
         for (uint64_t off = 0; off < n; off += round) {
             const uint64_t m = std::min(round, n - off);
-            SD_CK(h, launch_plane_round(pairs + 2 * off, m, h->G, h->pa, h->num_sms, h->stream));
-            launched(3);
+            // the bins of a round are laid out from the previous round of the
+            // same directions, when it was at least as large; else counted
+            const bool count = m > h->plane_layout_pairs || dir != h->plane_layout_view;
+            SD_CK(h, launch_plane_round(pairs + 2 * off, m, G, P, h->num_sms, h->stream, count));
+            launched(count ? 3 : 2);
+            h->plane_layout_pairs = m;
+            h->plane_layout_view = dir;
         }
         h->planes_dirty = true;
         return SD_OK;
@@ -652,54 +695,59 @@ static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n) {
         const int rc = ensure_bins(h, &ok);
         if (rc != SD_OK) return rc;
         if (ok) {
+            BinArgs B = h->bin;
+            if (dir >= 0) {  // the same bins and slice size over one direction's words
+                B.total_words = h->G.dir_words;
+                B.S = (uint32_t)((B.total_words + (1ull << B.slice_log2) - 1) >> B.slice_log2);
+            }
             const uint64_t chunk = 1ull << h->T.bin_chunk_log2;
             for (uint64_t off = 0; off < n; off += chunk) {
                 const uint64_t m = std::min(chunk, n - off);
-                SD_CK(h, launch_binned_chunk(pairs + 2 * off, m, h->grid, h->G, h->bin, h->num_sms, h->stream));
+                SD_CK(h, launch_binned_chunk(pairs + 2 * off, m, grid, G, B, h->num_sms, h->stream));
                 launched(2);
             }
             return SD_OK;
         }
         Tuning T = h->T;  // DHLA too large to bin: test-then-set
         T.mode = 1;
-        SD_CK(h, launch_update(pairs, n, h->grid, h->G, T, h->num_sms, h->stream));
+        SD_CK(h, launch_update(pairs, n, grid, G, T, h->num_sms, h->stream));
         launched(1);
         return SD_OK;
     }
-    SD_CK(h, launch_update(pairs, n, h->grid, h->G, h->T, h->num_sms, h->stream));
+    SD_CK(h, launch_update(pairs, n, grid, G, h->T, h->num_sms, h->stream));
     launched(1);
     return SD_OK;
 }
 
-int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
-    NvtxRange nvtx("sd_update");
-    if (!h) return SD_ERR_ARG;
-    if (n == 0) return SD_OK;
-    if (!pairs) return h->fail(SD_ERR_ARG, "sd_update: pairs is NULL");
-    if ((uintptr_t)pairs & 3u) return h->fail(SD_ERR_ARG, "sd_update: pairs is not 4-byte aligned");
+// sd_update and sd_update_dir: device pointers in place, pageable host
+// memory in place where the device reads it, other host memory through the
+// pinned double-buffered staging.
+static int update_any(sd_handle *h, const uint32_t *pairs, uint64_t n, int dir, const char *who) {
+    if (!pairs) return h->fail(SD_ERR_ARG, "%s: pairs is NULL", who);
+    if ((uintptr_t)pairs & 3u) return h->fail(SD_ERR_ARG, "%s: pairs is not 4-byte aligned", who);
     DeviceGuard dg(h->p.device);
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, pairs) != cudaSuccess) {
         cudaGetLastError();
         attr.type = cudaMemoryTypeUnregistered;
     }
+    const uint64_t counted = dir <= 0 ? n : 0;  // a window's pairs: those of direction 0
     if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
         if (attr.type == cudaMemoryTypeDevice && attr.device != h->p.device)
-            return h->fail(SD_ERR_ARG, "sd_update: pairs live on device %d, handle on %d", attr.device,
-                           h->p.device);
-        const int rc = update_device(h, pairs, n);
+            return h->fail(SD_ERR_ARG, "%s: pairs live on device %d, handle on %d", who, attr.device, h->p.device);
+        const int rc = update_device(h, pairs, n, dir);
         if (rc != SD_OK) return rc;
-        h->n_pairs += n;
+        h->n_pairs += counted;
         return SD_OK;
     }
     const bool pinned = attr.type == cudaMemoryTypeHost;
     if (!pinned && h->pageable_access) {
         // pageable memory the GPU reads in place (coherent link): no staging;
         // the caller may reuse the buffer once the kernels are done
-        const int rc = update_device(h, pairs, n);
+        const int rc = update_device(h, pairs, n, dir);
         if (rc != SD_OK) return rc;
         SD_CK(h, cudaStreamSynchronize(h->stream));
-        h->n_pairs += n;
+        h->n_pairs += counted;
         return SD_OK;
     }
     // host memory: chunked, double-buffered H2D overlapped with the kernel
@@ -719,14 +767,30 @@ int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
         SD_CK(h, cudaMemcpyAsync(h->dstage[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream));
         SD_CK(h, cudaEventRecord(h->ev_h2d[b], h->copy_stream));
         SD_CK(h, cudaStreamWaitEvent(h->stream, h->ev_h2d[b], 0));
-        const int urc = update_device(h, h->dstage[b], m);
+        const int urc = update_device(h, h->dstage[b], m, dir);
         if (urc != SD_OK) return urc;
         SD_CK(h, cudaEventRecord(h->ev_kern[b], h->stream));
     }
     // the caller may reuse a pinned buffer only once its copies are done
     if (pinned) SD_CK(h, cudaEventSynchronize(h->ev_h2d[(c - 1) & 1]));
-    h->n_pairs += n;
+    h->n_pairs += counted;
     return SD_OK;
+}
+
+int sd_update(sd_handle *h, const uint32_t *pairs, uint64_t n) {
+    NvtxRange nvtx("sd_update");
+    if (!h) return SD_ERR_ARG;
+    if (n == 0) return SD_OK;
+    return update_any(h, pairs, n, -1, "sd_update");
+}
+
+int sd_update_dir(sd_handle *h, uint32_t dir, const uint32_t *pairs, uint64_t n) {
+    NvtxRange nvtx("sd_update_dir");
+    if (!h) return SD_ERR_ARG;
+    if (dir >= h->G.dirs) return h->fail(SD_ERR_ARG, "sd_update_dir: direction %u of a %u-direction handle", dir,
+                                          h->G.dirs);
+    if (n == 0) return SD_OK;
+    return update_any(h, pairs, n, (int)dir, "sd_update_dir");
 }
 
 // Layout of a batched update driven by h (sd_update_many): slices per
@@ -1508,6 +1572,105 @@ int sd_merge(sd_handle *dst, sd_handle *src) {
     cudaEventDestroy(ev);
     if (e != cudaSuccess) return dst->fail(SD_ERR_CUDA, "sd_merge: %s", cudaGetErrorString(e));
     dst->n_pairs += src->n_pairs;
+    return SD_OK;
+}
+
+// Is p 16-byte aligned device (or managed) memory of `dev`?
+static bool device_buffer(const void *p, int dev) {
+    if (!p || ((uintptr_t)p & 15u)) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+int sd_export_grid(sd_handle *h, uint32_t *dst) {
+    NvtxRange nvtx("sd_export_grid");
+    if (!h) return SD_ERR_ARG;
+    if (!device_buffer(dst, h->p.device))
+        return h->fail(SD_ERR_ARG, "sd_export_grid: dst is not 16-byte aligned memory of device %d", h->p.device);
+    DeviceGuard dg(h->p.device);
+    const int frc = fold_planes(h);
+    if (frc != SD_OK) return frc;
+    SD_CK(h, cudaMemcpyAsync(dst, h->grid, (uint64_t)h->G.dirs * h->G.dir_words * 4, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    return SD_OK;
+}
+
+int sd_or_grid(sd_handle *h, const uint32_t *src) {
+    NvtxRange nvtx("sd_or_grid");
+    if (!h) return SD_ERR_ARG;
+    if (!device_buffer(src, h->p.device))
+        return h->fail(SD_ERR_ARG, "sd_or_grid: src is not 16-byte aligned memory of device %d", h->p.device);
+    DeviceGuard dg(h->p.device);
+    const int frc = fold_planes(h);
+    if (frc != SD_OK) return frc;
+    SD_CK(h, launch_merge(h->grid, src, (uint64_t)h->G.dirs * h->G.dir_words, h->num_sms, h->stream));
+    launched(1);
+    return SD_OK;
+}
+
+int sd_or_words(uint32_t *dst, const uint32_t *src, uint64_t words, uint32_t count, void *cuda_stream) {
+    NvtxRange nvtx("sd_or_words");
+    if (!dst || !src || !count || (words & 3u)) return SD_ERR_ARG;
+    if (!words) return SD_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SD_ERR_CUDA;
+    if (!device_buffer(dst, dev) || !device_buffer(src, dev)) return SD_ERR_ARG;
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SD_ERR_CUDA;
+    if (launch_or_words(dst, src, words, count, num_sms, (cudaStream_t)cuda_stream) != cudaSuccess)
+        return SD_ERR_CUDA;
+    launched(1);
+    return SD_OK;
+}
+
+int sd_partition_pairs(sd_handle *h, uint32_t dir, const uint32_t *pairs, uint64_t n, uint32_t parts,
+                       uint32_t *out, uint64_t *counts) {
+    NvtxRange nvtx("sd_partition_pairs");
+    if (!h || !counts || (n && (!pairs || !out))) return SD_ERR_ARG;
+    if (dir > 1 || parts < 1 || parts > 1024 || (parts & (parts - 1)))
+        return h->fail(SD_ERR_ARG, "sd_partition_pairs: dir must be 0 or 1 and parts a power of two up to 1024");
+    if (n == 0) {
+        for (uint32_t q = 0; q < parts; q++) counts[q] = 0;
+        return SD_OK;
+    }
+    DeviceGuard dg(h->p.device);
+    auto on_device = [&](const void *ptr) {
+        if (!ptr || ((uintptr_t)ptr & 3u)) return false;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return (a.type == cudaMemoryTypeDevice && a.device == h->p.device) || a.type == cudaMemoryTypeManaged;
+    };
+    if (!on_device(pairs) || !on_device(out))
+        return h->fail(SD_ERR_ARG, "sd_partition_pairs: pairs and out must be 4-byte aligned memory of device %d",
+                       h->p.device);
+    if (!h->part_d) {
+        SD_CK(h, cudaMalloc(&h->part_d, 2 * 1024 * sizeof(unsigned long long)));
+        SD_CK(h, cudaMallocHost(&h->part_h, 1024 * sizeof(unsigned long long)));
+    }
+    SD_CK(h, cudaMemsetAsync(h->part_d, 0, parts * sizeof(unsigned long long), h->stream));
+    SD_CK(h, launch_partition(pairs, n, dir, parts, h->part_d, nullptr, nullptr, h->num_sms, h->stream, false));
+    SD_CK(h, cudaMemcpyAsync(h->part_h, h->part_d, parts * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             h->stream));
+    SD_CK(h, cudaStreamSynchronize(h->stream));
+    unsigned long long run = 0;
+    for (uint32_t q = 0; q < parts; q++) {
+        counts[q] = h->part_h[q];
+        h->part_h[q] = run;  // cursor of part q: its first slot
+        run += counts[q];
+    }
+    unsigned long long *cursor = h->part_d + 1024;
+    SD_CK(h, cudaMemcpyAsync(cursor, h->part_h, parts * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                             h->stream));
+    SD_CK(h, launch_partition(pairs, n, dir, parts, nullptr, cursor, out, h->num_sms, h->stream, true));
+    launched(2);
+    SD_CK(h, cudaStreamSynchronize(h->stream));  // the cursors' host copy is reused by the next call
     return SD_OK;
 }
 

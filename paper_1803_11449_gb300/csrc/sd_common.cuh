@@ -51,13 +51,15 @@ struct Tuning {
 
 // The plane-binned update (sd_plane.cu): bins of keys per plane (d, b) =
 // bit b of every estimator of direction d, and the plane-major DHLA copy.
+// A round's bins are laid out from the previous round's counts (with slack)
+// or, for a round without a usable history, from an exact count.
 struct PlaneArgs {
-    uint32_t *bins;        // the round's keys, each plane's bin starting on 4 entries
-    uint32_t *ntot;        // [nbins] entries per plane (k_plane_count; zero between rounds)
-    uint32_t *binoff;      // [nbins + 1] first entry of each bin
-    uint32_t *fill;        // [nbins] entries appended (k_plane_bin): the bin's size
+    uint32_t *bins;        // the round's keys, plane by plane (each bin starts on 4 entries)
+    uint32_t *cnt;         // [nbins] keys of each plane this round (zero between rounds)
+    uint32_t *binoff;      // [nbins + 1] first slot of each plane's bin
+    uint32_t *cap;         // [nbins] slots of each plane's bin; keys beyond them are set directly
     uint32_t *unit_start;  // [nbins + 1] first apply unit of each plane
-    uint32_t *ctl;         // [0] blocks done (k_plane_count), [1] apply units taken
+    uint32_t *ctl;         // [0] blocks done (count or bin), [1] apply units taken, [2] apply blocks done
     uint32_t *planes;      // [nbins][ps] plane-major DHLA copy
     uint32_t nbins;        // dirs * g
     uint32_t ps;           // words per plane: r 2^k / 32 rounded up to 4
@@ -238,9 +240,18 @@ cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
 size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins);
-// one round of the plane-binned update over n pairs (count, bin, apply)
+// one round of the plane-binned update over n pairs: an exact count first
+// when `count` (no usable layout from an earlier round), then bin and apply
 cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
-                               cudaStream_t s);
+                               cudaStream_t s, bool count);
+// dst = OR of `count` arrays of `words` words at src (words a multiple of 4)
+cudaError_t launch_or_words(uint32_t *dst, const uint32_t *src, uint64_t words, uint32_t count, int num_sms,
+                            cudaStream_t s);
+// key partition: counting pass (counts[parts] += ...) or scatter pass
+// (cursor[parts] = each part's next slot; out gets (key, peer) pairs)
+cudaError_t launch_partition(const uint32_t *pairs, uint64_t n, uint32_t dir, uint32_t parts,
+                             unsigned long long *counts, unsigned long long *cursor, uint32_t *out, int num_sms,
+                             cudaStream_t s, bool scatter);
 // grid |= planes^T, planes = 0
 cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
                               cudaStream_t s);

@@ -15,6 +15,12 @@
 // contents, so each call clears the counters it relies on; calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // it and must be serialised by the caller.
+//
+// Launch failures are read from the runtime's per-thread error state, which
+// also holds errors that earlier, unrelated runtime calls left there.  So a
+// call first looks at that state without clearing it, and when an error is
+// already pending it returns SD_ERR_CUDA with nothing queued: it neither
+// reports nor consumes the caller's own error.
 #include <cstring>
 #include <mutex>
 
@@ -45,8 +51,19 @@ extern "C" int sd_update_noalloc(const sd_params *p, uint32_t *grid, const uint3
         ((uintptr_t)grid & 15u))
         return SD_ERR_ARG;
     if (n == 0) return SD_OK;
+    if (cudaPeekAtLastError() != cudaSuccess) return SD_ERR_CUDA;  // an earlier call's error is pending
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SD_ERR_CUDA;
+    // both buffers must be device (or managed) memory of the current device
+    for (const void *ptr : {static_cast<const void *>(grid), static_cast<const void *>(pairs)}) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();  // the lookup's own error (none was pending before it)
+            return SD_ERR_ARG;
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != dev) return SD_ERR_ARG;
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return SD_ERR_ARG;
+    }
 
     // set-up, once per device, with that device current
     uint32_t *scratch = nullptr;
@@ -92,8 +109,14 @@ extern "C" int sd_update_noalloc(const sd_params *p, uint32_t *grid, const uint3
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SD_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // the counters start at zero; the array keeps whatever the last call left
-    k_clear_counts<<<1, 256, 0, s>>>(B.count, (uint32_t)(S + 4));
-    if (cudaGetLastError() != cudaSuccess) return SD_ERR_CUDA;
+    uint32_t *counts = B.count;
+    uint32_t ncount = (uint32_t)(S + 4);
+    void *args[] = {&counts, &ncount};
+    if (cudaLaunchKernel(reinterpret_cast<const void *>(k_clear_counts), dim3(1), dim3(256), args, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return SD_ERR_CUDA;
+    }
     for (uint64_t off = 0; off < n; off += chunk) {
         const uint64_t m = n - off < chunk ? n - off : chunk;
         if (launch_binned_chunk(pairs + 2 * off, m, grid, G, B, num_sms, s) != cudaSuccess) return SD_ERR_CUDA;

@@ -10,20 +10,24 @@
 // per pair and direction -- the key itself -- and the rows are hashed where
 // the plane is held, in shared memory:
 //
-//   k_plane_count  the entries of every plane for one round of pairs; the
-//                  last block lays the bins out back to back (exact sizes,
-//                  each bin starting on a 16-byte boundary) and cuts each
-//                  plane's bin into apply units.
 //   k_plane_bin    tiles of pairs: the keys sorted by plane in shared memory,
 //                  each plane's run appended to its bin with coalesced
 //                  stores (one reservation atomic per plane and tile).  The
-//                  bins are sized exactly by the count, so nothing overflows.
+//                  bins are laid out back to back (each starting on a
+//                  16-byte boundary) from the previous round's counts plus
+//                  slack; keys beyond a bin's capacity (traffic that shifted
+//                  between rounds) set their bits directly with atomic ORs.
+//                  The last block cuts each plane's bin into apply units.
+//   k_plane_count  for a round without a usable layout (the first one, or
+//                  one larger than the round the layout came from): the
+//                  exact keys of every plane, and a layout without slack.
 //   k_plane_apply  one unit (a plane and a range of its bin) per block step:
 //                  the plane in shared memory, DH_0 and Eq. 2 of every key,
 //                  r shared-memory ORs, then one bulk OR of the plane into
 //                  the plane-major copy of the DHLA in L2
 //                  (cp.reduce.async.bulk ... .or.b32, so units of one plane
-//                  may run on several SMs).
+//                  may run on several SMs).  The last block lays out the
+//                  next round's bins from this round's counts.
 //   k_plane_fold   (window close, sd_get_grid, sd_merge) transposes the
 //                  plane-major copy into the estimator-major DHLA
 //                  (grid |= planes^T, 32 x 32 bit blocks by warp shuffles)
@@ -98,6 +102,52 @@ __device__ __forceinline__ void block_scan(uint32_t N, Get get, Put put, uint32_
     __syncthreads();
 }
 
+// One block: the bins of the next round from this round's per-plane counts
+// (cnt, then cleared): capacity = count rounded up to 4, plus an eighth and
+// 32 slots of slack when `slack`; bins back to back.  The caller has seen
+// every count (last-block pattern).
+__device__ __forceinline__ void write_layout(const PlaneArgs &P, bool slack, uint32_t *s_warp) {
+    const uint32_t NB = P.nbins;
+    auto cap_of = [&](uint32_t i) {
+        const uint32_t c = __ldcg(&P.cnt[i]);
+        return (c + (slack ? c / 8u + 32u : 0u) + 3u) & ~3u;
+    };
+    block_scan(NB, cap_of, [&](uint32_t i, uint32_t v) { P.binoff[i] = v; }, s_warp);
+    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) {
+        P.cap[b] = cap_of(b);
+        P.cnt[b] = 0;
+    }
+}
+
+// The last block to call this (one call per block, counter at *done) gets
+// true, after a fence that makes every earlier block's writes visible.
+__device__ __forceinline__ bool last_block(uint32_t *done, bool *s_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!*s_last) return false;
+    __threadfence();
+    return true;
+}
+
+// Set the r bits of `key` in plane b of the plane-major copy directly (a
+// key its bin had no room for).
+template <int DIRS>
+__device__ __forceinline__ void set_key_bits(const Geometry &G, const PlaneArgs &P, uint32_t b, uint32_t key) {
+    const uint32_t A0 = (DIRS == 2 && (b >> G.lg)) ? G.h[1].A0 : G.h[0].A0;
+    const uint32_t rw = (1u << G.k) >> 5;
+    uint32_t *pl = P.planes + (uint64_t)b * P.ps;
+    const uint32_t c0 = dh0(A0, G.k, key);
+    red_or(pl + (c0 >> 5), 1u << (c0 & 31u));
+    for (uint32_t i = 1; i < G.r; i++) {
+        const uint32_t ci = dh_row(G, i, key, c0);
+        red_or(pl + i * rw + (ci >> 5), 1u << (ci & 31u));
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ count
@@ -118,9 +168,21 @@ k_plane_count(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneA
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (((uintptr_t)pairs & 15u) == 0) {
+        // four 16-byte loads in flight per thread
         const uint4 *v4 = reinterpret_cast<const uint4 *>(pairs);
         const uint64_t n2 = n / 2;
-        for (uint64_t u = first; u < n2; u += stride) {
+        uint64_t u = first;
+        for (; u + 3 * stride < n2; u += 4 * stride) {
+            uint4 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] = ld_l2_v4(v4 + u + j * stride);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                count(v[j].x, v[j].y);
+                count(v[j].z, v[j].w);
+            }
+        }
+        for (; u < n2; u += stride) {
             const uint4 v = ld_l2_v4(v4 + u);
             count(v.x, v.y);
             count(v.z, v.w);
@@ -131,27 +193,11 @@ k_plane_count(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneA
     }
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x)
-        if (hist[b]) atomicAdd(&P.ntot[b], hist[b]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&P.ctl[0], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    // the last block to finish: every count is in ntot
-    __threadfence();
-    const uint32_t U = P.unit;
-    block_scan(NB, [&](uint32_t i) { return (__ldcg(&P.ntot[i]) + 3u) & ~3u; },
-               [&](uint32_t i, uint32_t v) { P.binoff[i] = v; }, s_warp);
-    block_scan(NB, [&](uint32_t i) { return (__ldcg(&P.ntot[i]) + U - 1u) / U; },
-               [&](uint32_t i, uint32_t v) { P.unit_start[i] = v; }, s_warp);
-    for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) {
-        P.ntot[b] = 0;
-        P.fill[b] = 0;
-    }
-    if (threadIdx.x == 0) {
-        P.ctl[0] = 0;
-        P.ctl[1] = 0;
-    }
+        if (hist[b]) atomicAdd(&P.cnt[b], hist[b]);
+    if (!last_block(&P.ctl[0], &s_last)) return;
+    // every count is in cnt: bins of exactly this round's sizes
+    write_layout(P, false, s_warp);
+    if (threadIdx.x == 0) P.ctl[0] = 0;
 }
 
 // -------------------------------------------------------------------- bin
@@ -165,12 +211,14 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
     constexpr int E = PPT * DIRS;
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t s_warp[32];
+    __shared__ bool s_last;
     const uint32_t NB = P.nbins, g = G.g, lg = G.lg;
     const uint32_t TP = blockDim.x * PPT;
     uint32_t *hist = sm;                 // [NB] entries of each plane in the tile
     uint32_t *offs = hist + NB;          // [NB] first sorted position of each plane
     uint32_t *gdst = offs + NB;          // [NB] bin index of sorted position 0 (mod 2^32)
-    uint32_t *skey = gdst + NB;          // [DIRS TP] keys in plane order
+    uint32_t *lim = gdst + NB;           // [NB] sorted positions below this fit the plane's bin
+    uint32_t *skey = lim + NB;           // [DIRS TP] keys in plane order
     uint16_t *sbin = reinterpret_cast<uint16_t *>(skey + (size_t)DIRS * TP);  // [DIRS TP]
     const uint64_t A1a = G.h[0].A1, B1a = G.h[0].B1, A1b = G.h[1].A1, B1b = G.h[1].B1;
     const uint64_t ntiles = (n + TP - 1) / TP;
@@ -178,8 +226,34 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
     // bins owned by this thread in the scan (contiguous chunk)
     const uint32_t per = (NB + blockDim.x - 1) / blockDim.x;
     const uint32_t b0 = min(threadIdx.x * per, NB), b1 = min(b0 + per, NB);
+    // this thread's pairs of tile t: 2-pair units threadIdx.x + j blockDim.x
+    // (coalesced 16-byte loads where the buffer allows)
+    auto load_tile = [&](uint64_t t, uint32_t (&ps)[PPT], uint32_t (&pt)[PPT]) {
+        const uint64_t base = t * TP;
+        const uint64_t left = t < ntiles ? n - base : 0;
+        const uint32_t cnt = left < TP ? (uint32_t)left : TP;
+#pragma unroll
+        for (int j = 0; j < PPT / 2; j++) {
+            const uint32_t pu = threadIdx.x + (uint32_t)j * blockDim.x;
+            const uint64_t p = base + 2ull * pu;
+            const bool ok0 = 2 * pu < cnt, ok1 = 2 * pu + 1 < cnt;
+            ps[2 * j] = pt[2 * j] = ps[2 * j + 1] = pt[2 * j + 1] = 0u;
+            if (vec && ok1) {
+                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p));
+                ps[2 * j] = v.x; pt[2 * j] = v.y; ps[2 * j + 1] = v.z; pt[2 * j + 1] = v.w;
+            } else {
+                if (ok0) { ps[2 * j] = ld_stream_u32(pairs + 2 * p); pt[2 * j] = ld_stream_u32(pairs + 2 * p + 1); }
+                if (ok1) {
+                    ps[2 * j + 1] = ld_stream_u32(pairs + 2 * p + 2);
+                    pt[2 * j + 1] = ld_stream_u32(pairs + 2 * p + 3);
+                }
+            }
+        }
+    };
     for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
     __syncthreads();
+    uint32_t nps[PPT], npt[PPT];  // the next tile's pairs, loaded while the current one is written out
+    load_tile(blockIdx.x, nps, npt);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t base = t * TP;
         const uint64_t left = n - base;
@@ -188,18 +262,8 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
 #pragma unroll
         for (int j = 0; j < PPT / 2; j++) {
             const uint32_t pu = threadIdx.x + (uint32_t)j * blockDim.x;  // 2-pair unit within the tile
-            const uint64_t p = base + 2ull * pu;
-            uint32_t s0 = 0, t0 = 0, s1 = 0, t1 = 0;
-            const bool ok0 = 2 * pu < cnt, ok1 = 2 * pu + 1 < cnt;
-            if (vec && ok1) {
-                const uint4 v = ld_stream_v4(reinterpret_cast<const uint4 *>(pairs + 2 * p));
-                s0 = v.x; t0 = v.y; s1 = v.z; t1 = v.w;
-            } else {
-                if (ok0) { s0 = ld_stream_u32(pairs + 2 * p); t0 = ld_stream_u32(pairs + 2 * p + 1); }
-                if (ok1) { s1 = ld_stream_u32(pairs + 2 * p + 2); t1 = ld_stream_u32(pairs + 2 * p + 3); }
-            }
-            const uint32_t ss[2] = {s0, s1}, tt[2] = {t0, t1};
-            const bool ok[2] = {ok0, ok1};
+            const uint32_t ss[2] = {nps[2 * j], nps[2 * j + 1]}, tt[2] = {npt[2 * j], npt[2 * j + 1]};
+            const bool ok[2] = {2 * pu < cnt, 2 * pu + 1 < cnt};
 #pragma unroll
             for (int q = 0; q < 2; q++) {
 #pragma unroll
@@ -244,16 +308,23 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
         // (the first kHeldReservations of a thread's planes keep their
         // results in registers until after the scatter; with more planes per
         // thread than that, the rest are resolved at once)
-        uint32_t res[kHeldReservations], rrun[kHeldReservations];
+        uint32_t res[kHeldReservations], rrun[kHeldReservations], rcap[kHeldReservations],
+            roff[kHeldReservations];
 #pragma unroll
         for (uint32_t q = 0; q < kHeldReservations; q++) {
             const uint32_t b = b0 + q;
             res[q] = 0;
             rrun[q] = run;
+            rcap[q] = 0;
+            roff[q] = 0;
             if (b < b1) {
                 const uint32_t h = hist[b];
                 offs[b] = run;
-                if (h) res[q] = atomicAdd(&P.fill[b], h);
+                if (h) {
+                    res[q] = atomicAdd(&P.cnt[b], h);
+                    rcap[q] = P.cap[b];
+                    roff[q] = P.binoff[b];
+                }
                 hist[b] = 0;
                 run += h;
             }
@@ -261,7 +332,11 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
         for (uint32_t b = b0 + kHeldReservations; b < b1; b++) {
             const uint32_t h = hist[b];
             offs[b] = run;
-            if (h) gdst[b] = P.binoff[b] + atomicAdd(&P.fill[b], h) - run;
+            if (h) {
+                const uint32_t pos = atomicAdd(&P.cnt[b], h), c = P.cap[b];
+                gdst[b] = P.binoff[b] + pos - run;
+                lim[b] = run + (c > pos ? c - pos : 0u);
+            }
             hist[b] = 0;
             run += h;
         }
@@ -275,18 +350,36 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
             skey[pos] = key[e];
             sbin[pos] = (uint16_t)b;
         }
+        load_tile(t + gridDim.x, nps, npt);
 #pragma unroll
         for (uint32_t q = 0; q < kHeldReservations; q++) {
             const uint32_t b = b0 + q;
-            if (b < b1) gdst[b] = P.binoff[b] + res[q] - rrun[q];
+            if (b < b1) {
+                gdst[b] = roff[q] + res[q] - rrun[q];
+                lim[b] = rrun[q] + (rcap[q] > res[q] ? rcap[q] - res[q] : 0u);
+            }
         }
         __syncthreads();
         // write-out: sorted entry q of plane b goes to bins[gdst[b] + q]
+        // while its bin has room (plain stores: a plane's run is a fraction
+        // of a line, and the line is completed by other tiles; streaming
+        // stores would push the partial lines to DRAM several times over)
         const uint32_t nent = cnt * DIRS;
         for (uint32_t q = threadIdx.x; q < nent; q += blockDim.x) {
             const uint32_t b = sbin[q];
-            __stcs(P.bins + (uint32_t)(gdst[b] + q), skey[q]);
+            if (q < lim[b]) P.bins[(uint32_t)(gdst[b] + q)] = skey[q];
+            else set_key_bits<DIRS>(G, P, b, skey[q]);
         }
+    }
+    // the last block: apply units of the bins' actual contents
+    if (!last_block(&P.ctl[0], &s_last)) return;
+    const uint32_t U = P.unit;
+    block_scan(NB, [&](uint32_t i) { return (min(__ldcg(&P.cnt[i]), P.cap[i]) + U - 1u) / U; },
+               [&](uint32_t i, uint32_t v) { P.unit_start[i] = v; }, s_warp);
+    if (threadIdx.x == 0) {
+        P.ctl[0] = 0;
+        P.ctl[1] = 0;
+        P.ctl[2] = 0;
     }
 }
 
@@ -302,19 +395,30 @@ __device__ __forceinline__ void apply_key(uint32_t *pl, const Geometry &G, uint3
     }
 }
 
+// With two plane buffers (nbuf = 2, where two planes fit the block's shared
+// memory) a unit is applied in one buffer while the bulk reduction of the
+// previous unit still reads the other; before a buffer is reused, its
+// reduction must have finished reading it (wait_group.read allows one
+// reduction, the other buffer's, to stay in flight).
 template <int R>
 __global__ void __launch_bounds__(kApplyThreads)
-k_plane_apply(Geometry G, PlaneArgs P) {
-    extern __shared__ uint4 pl4[];  // the plane, ps words
+k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf) {
+    extern __shared__ uint4 pl4_all[];  // nbuf planes of ps words
     __shared__ uint32_t s_unit;
-    uint32_t *pl = reinterpret_cast<uint32_t *>(pl4);
+    __shared__ uint32_t s_warp[32];
+    __shared__ bool s_last;
     const uint32_t NB = P.nbins;
     const uint32_t rw = (1u << G.k) >> 5;
     const uint32_t total = P.unit_start[NB];
-    for (;;) {
-        __syncthreads();  // the previous unit's bulk reduction has read the plane
-        if (threadIdx.x == 0) s_unit = atomicAdd(&P.ctl[1], 1u);
-        __syncthreads();
+    for (uint32_t it = 0;; it++) {
+        uint4 *pl4 = pl4_all + (size_t)(it % nbuf) * (P.ps / 4);
+        uint32_t *pl = reinterpret_cast<uint32_t *>(pl4);
+        if (threadIdx.x == 0) {
+            if (nbuf == 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            else asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            s_unit = atomicAdd(&P.ctl[1], 1u);
+        }
+        __syncthreads();  // this buffer is free again; the unit is known
         const uint32_t x = s_unit;
         if (x >= total) break;
         uint32_t lo = 0, hi = NB;  // the plane b with unit_start[b] <= x < unit_start[b + 1]
@@ -325,7 +429,7 @@ k_plane_apply(Geometry G, PlaneArgs P) {
         }
         const uint32_t b = lo;
         const uint32_t beg = P.binoff[b] + (x - P.unit_start[b]) * P.unit;
-        const uint32_t stop = P.binoff[b] + P.fill[b];
+        const uint32_t stop = P.binoff[b] + min(P.cnt[b], P.cap[b]);
         const uint32_t end = stop - beg < P.unit ? stop : beg + P.unit;
         const uint32_t A0 = (b >> G.lg) ? G.h[1].A0 : G.h[0].A0;
         for (uint32_t i = threadIdx.x; i < P.ps / 4; i += blockDim.x) pl4[i] = make_uint4(0, 0, 0, 0);
@@ -356,51 +460,135 @@ k_plane_apply(Geometry G, PlaneArgs P) {
                          "r"(P.ps * 4u)
                          : "memory");
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    // the last block: the next round's bins from this round's counts
+    if (!last_block(&P.ctl[2], &s_last)) return;
+    write_layout(P, true, s_warp);
 }
 
 // ------------------------------------------------------------------- fold
-// One warp per (direction, row, 32 estimators): for each word t of those
-// estimators, lane j reads word w of plane 32t + j (bit l = estimator 32w+l
-// of that plane), a 32 x 32 bit transpose by shuffles gives lane l word t of
-// estimator 32w + l, staged in shared memory; then the 32 estimators'
-// words are ORed into the DHLA (contiguous) and the plane words cleared.
-__global__ void __launch_bounds__(256)
+// One warp per (direction, row, group of 32 WQ estimators, TC of their bit
+// words), WQ = 8 plane words (256 estimators) where rows are that long.  For
+// each bit word t, lane j reads the group's WQ words of plane 32t + j (one
+// 32-byte sector) and clears them, four words t in flight; a 32 x 32 bit
+// transpose by shuffles turns each into word t of 32 estimators (lane l:
+// estimator 32q + l); the TC words of every estimator are staged in shared
+// memory and ORed into the DHLA, where they are contiguous.
+constexpr uint32_t kFoldWarps = 8;
+constexpr uint32_t kFoldTC = 8;    // estimator words per warp item
+constexpr uint32_t kFoldBatch = 4; // plane words t loaded before transposing
+
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
+#pragma unroll
+    for (uint32_t j = 16; j > 0; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                         : j == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(kFoldWarps * 32)
 k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometry G, uint32_t ps) {
-    extern __shared__ uint32_t stg[];  // [8 warps][32 estimators][wpc + 1]
+    extern __shared__ uint32_t stg[];  // [warps][256 estimators][kFoldTC + 1]
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    const uint32_t wpc = G.wpc, sp = wpc + 1;
-    uint32_t *my = stg + (size_t)wid * 32 * sp;
-    const uint32_t rw = (1u << G.k) >> 5;
-    const uint64_t items = (uint64_t)G.dirs * G.r * rw;
+    constexpr uint32_t SP = kFoldTC + 1;
+    uint32_t *my = stg + (size_t)wid * 256 * SP;
+    const uint32_t wpc = G.wpc;
+    const uint32_t tc = wpc < kFoldTC ? wpc : kFoldTC;
+    const uint32_t nchunks = wpc / tc;
+    const uint32_t rw = (1u << G.k) >> 5;      // plane words per row
+    const uint32_t wq = rw < 8u ? rw : 8u;     // plane words per warp item
+    const uint32_t groups = rw / wq;
+    const uint64_t items = (uint64_t)G.dirs * G.r * groups * nchunks;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wid; it < items; it += nwarps) {
-        const uint32_t w = (uint32_t)(it % rw);
-        const uint32_t di = (uint32_t)(it / rw);
+        const uint32_t chunk = (uint32_t)(it % nchunks);
+        const uint64_t rest = it / nchunks;
+        const uint32_t grp = (uint32_t)(rest % groups);
+        const uint32_t di = (uint32_t)(rest / groups);
         const uint32_t d = di / G.r, i = di - d * G.r;
-        for (uint32_t t = 0; t < wpc; t++) {
-            uint32_t *src = planes + (uint64_t)(d * G.g + 32u * t + lane) * ps + (uint64_t)i * rw + w;
-            uint32_t x = *src;
-            if (x) *src = 0u;
-            // transpose the 32 x 32 bit block held one row per lane
+        const uint32_t w0 = grp * wq, tc0 = chunk * tc;
+        uint32_t *row = grid + (uint64_t)d * G.dir_words + (uint64_t)i * G.row_words;
+        for (uint32_t t0 = 0; t0 < tc; t0 += kFoldBatch) {
+            uint32_t x[kFoldBatch][8];
 #pragma unroll
-            for (uint32_t j = 16; j > 0; j >>= 1) {
-                const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
-                                 : j == 2 ? 0x33333333u : 0x55555555u;
-                const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-                x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+            for (uint32_t bt = 0; bt < kFoldBatch; bt++) {
+                const uint32_t tt = t0 + bt;
+                uint32_t *src = planes + (uint64_t)(d * G.g + 32u * (tc0 + tt) + lane) * ps + (uint64_t)i * rw + w0;
+                if (tt >= tc) {
+#pragma unroll
+                    for (uint32_t q = 0; q < 8; q++) x[bt][q] = 0u;
+                } else if (wq == 8) {
+                    uint4 *s4 = reinterpret_cast<uint4 *>(src);
+                    const uint4 a = s4[0], b = s4[1];
+                    x[bt][0] = a.x; x[bt][1] = a.y; x[bt][2] = a.z; x[bt][3] = a.w;
+                    x[bt][4] = b.x; x[bt][5] = b.y; x[bt][6] = b.z; x[bt][7] = b.w;
+                } else {
+#pragma unroll
+                    for (uint32_t q = 0; q < 8; q++) x[bt][q] = q < wq ? src[q] : 0u;
+                }
             }
-            my[lane * sp + t] = x;  // word t of estimator 32w + lane
+#pragma unroll
+            for (uint32_t bt = 0; bt < kFoldBatch; bt++) {
+                const uint32_t tt = t0 + bt;
+                if (tt >= tc) continue;  // warp-uniform
+                uint32_t *src = planes + (uint64_t)(d * G.g + 32u * (tc0 + tt) + lane) * ps + (uint64_t)i * rw + w0;
+                if (wq == 8) {  // clear the plane words just read
+                    uint4 *s4 = reinterpret_cast<uint4 *>(src);
+                    if (x[bt][0] | x[bt][1] | x[bt][2] | x[bt][3]) s4[0] = make_uint4(0, 0, 0, 0);
+                    if (x[bt][4] | x[bt][5] | x[bt][6] | x[bt][7]) s4[1] = make_uint4(0, 0, 0, 0);
+                } else {
+#pragma unroll
+                    for (uint32_t q = 0; q < 8; q++)
+                        if (q < wq && x[bt][q]) src[q] = 0u;
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < 8; q++) {
+                    if (q >= wq) continue;
+                    my[(32u * q + lane) * SP + tt] = transpose32(x[bt][q], lane);
+                }
+            }
         }
         __syncwarp();
-        uint32_t *dst = grid + (uint64_t)d * G.dir_words + (uint64_t)i * G.row_words + (uint64_t)(32u * w) * wpc;
-        for (uint32_t q = lane; q < 32u * wpc; q += 32u) {
-            const uint32_t c = q / wpc, tq = q - c * wpc;
-            const uint32_t v = my[c * sp + tq];
-            if (v) dst[q] |= v;
+        // OR the staged words into the estimators (32 wq of them, tc words
+        // each, contiguous in the DHLA when tc = wpc): four words per lane and
+        // step, four steps' loads issued before their stores
+        const uint32_t lt = tc == 8 ? 3u : tc == 4 ? 2u : tc == 2 ? 1u : 0u;  // log2 tc
+        const uint32_t quads = (32u * wq * tc) / 4u;
+        if (tc >= 4) {
+            for (uint32_t q0 = lane; q0 < quads; q0 += 128u) {
+                uint4 cur[4];
+                uint4 *dst[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t q = q0 + 32u * u;
+                    dst[u] = nullptr;
+                    if (q < quads) {
+                        const uint32_t w = 4u * q, e = w >> lt, tt = w & (tc - 1u);
+                        dst[u] = reinterpret_cast<uint4 *>(row + (uint64_t)(32u * w0 + e) * wpc + tc0 + tt);
+                        cur[u] = *dst[u];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (!dst[u]) continue;
+                    const uint32_t w = 4u * (q0 + 32u * u), e = w >> lt, tt = w & (tc - 1u);
+                    const uint32_t *m = my + e * SP + tt;
+                    const uint4 v = make_uint4(cur[u].x | m[0], cur[u].y | m[1], cur[u].z | m[2], cur[u].w | m[3]);
+                    if (v.x != cur[u].x || v.y != cur[u].y || v.z != cur[u].z || v.w != cur[u].w) *dst[u] = v;
+                }
+            }
+        } else {
+            const uint32_t total = 32u * wq * tc;
+            for (uint32_t q = lane; q < total; q += 32u) {
+                const uint32_t e = q >> lt, tt = q & (tc - 1u);
+                const uint32_t v = my[e * SP + tt];
+                if (v) row[(uint64_t)(32u * w0 + e) * wpc + tc0 + tt] |= v;
+            }
         }
         __syncwarp();
     }
@@ -408,7 +596,7 @@ k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometr
 
 // --------------------------------------------------------------- launchers
 size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins) {
-    return (size_t)3 * nbins * 4 + (size_t)dirs * tile_pairs * 6;
+    return (size_t)4 * nbins * 4 + (size_t)dirs * tile_pairs * 6;
 }
 
 template <int DIRS, int PPT>
@@ -440,19 +628,19 @@ static cudaError_t launch_plane_bin_d(const uint32_t *pairs, uint64_t n, const G
 template <int R>
 static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, int num_sms, cudaStream_t s) {
     auto kern = k_plane_apply<R>;
-    const size_t smem = (size_t)P.ps * 4;
+    const uint32_t nbuf = (size_t)P.ps * 8 <= (size_t)100 * 1024 ? 2u : 1u;
+    const size_t smem = (size_t)P.ps * 4 * nbuf;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kApplyThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(num_sms * per_sm), kApplyThreads, smem, s>>>(G, P);
+    kern<<<(unsigned)(num_sms * per_sm), kApplyThreads, smem, s>>>(G, P, nbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool count) {
     if (n == 0) return cudaSuccess;
-    // count
-    {
+    if (count) {
         auto kern = G.dirs == 2 ? k_plane_count<2> : k_plane_count<1>;
         const size_t smem = (size_t)P.nbins * 4;
         int per_sm = 0;
@@ -480,14 +668,16 @@ cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry
 
 cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
                               cudaStream_t s) {
-    const size_t smem = (size_t)8 * 32 * (G.wpc + 1) * 4;
+    const size_t smem = (size_t)kFoldWarps * 256 * (kFoldTC + 1) * 4;
     int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), 256, smem, &per_sm);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldWarps * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    const uint64_t items = (uint64_t)G.dirs * G.r * (((uint64_t)1 << G.k) >> 5);
+    const uint64_t rw = ((uint64_t)1 << G.k) >> 5;
+    const uint64_t tc = G.wpc < kFoldTC ? G.wpc : kFoldTC;
+    const uint64_t items = (uint64_t)G.dirs * G.r * (rw / (rw < 8 ? rw : 8)) * (G.wpc / tc);
     uint64_t blocks = (uint64_t)num_sms * per_sm;
-    if ((items + 7) / 8 < blocks) blocks = (items + 7) / 8;
-    k_plane_fold<<<(unsigned)blocks, 256, smem, s>>>(grid, planes, G, ps);
+    if ((items + kFoldWarps - 1) / kFoldWarps < blocks) blocks = (items + kFoldWarps - 1) / kFoldWarps;
+    k_plane_fold<<<(unsigned)blocks, kFoldWarps * 32, smem, s>>>(grid, planes, G, ps);
     return cudaGetLastError();
 }
 

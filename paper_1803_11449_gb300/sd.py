@@ -40,7 +40,8 @@ EXPORTS = ["sd_default_params", "sd_check_params", "sd_grid_words", "sd_device_b
            "sd_update", "sd_close_window", "sd_close_many", "sd_update_many", "sd_scratch_bytes", "sd_sync", "sd_destroy",
            "sd_last_error", "sd_get_grid",
            "sd_set_grid", "sd_get_hot", "sd_get_candidates", "sd_merge", "sd_kernel_launches",
-           "sd_get_tuning", "sd_set_tuning", "sd_update_noalloc"]
+           "sd_get_tuning", "sd_set_tuning", "sd_update_noalloc", "sd_update_dir", "sd_export_grid",
+           "sd_or_grid", "sd_or_words", "sd_partition_pairs"]
 
 
 class sd_params(ctypes.Structure):
@@ -127,6 +128,12 @@ def lib():
                 "sd_get_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_set_tuning": (ctypes.c_int, [_VP, _P(sd_tuning)]),
                 "sd_update_noalloc": (ctypes.c_int, [_P(sd_params), _VP, _VP, ctypes.c_uint64, _VP]),
+                "sd_update_dir": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP, ctypes.c_uint64]),
+                "sd_export_grid": (ctypes.c_int, [_VP, _VP]),
+                "sd_or_grid": (ctypes.c_int, [_VP, _VP]),
+                "sd_or_words": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, _VP]),
+                "sd_partition_pairs": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP, ctypes.c_uint64,
+                                                      ctypes.c_uint32, _VP, _P(ctypes.c_uint64)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -354,6 +361,45 @@ def sd_set_tuning(h: Handle, mode=0, block_threads=0, blocks_per_sm=0, unroll=0,
                   plane_tile_pairs=plane_tile_pairs, plane_round_log2=plane_round_log2,
                   plane_unit_log2=plane_unit_log2)
     _check(lib().sd_set_tuning(h.ptr, ctypes.byref(t)), h.ptr)
+
+
+def sd_update_dir(h: Handle, direction: int, pairs) -> None:
+    """Algorithm 1 for one direction of (key, peer) pairs (see include/sd.h)."""
+    ptr, n, _keep = _buffer(pairs)
+    if n == 0:
+        return
+    _check(lib().sd_update_dir(h.ptr, direction, ptr, n), h.ptr)
+
+
+def sd_export_grid(h: Handle, dst) -> None:
+    """Queue a copy of h's DHLA (both directions) into the device tensor dst."""
+    ptr, _, _keep = _buffer(dst)
+    _check(lib().sd_export_grid(h.ptr, ptr), h.ptr)
+
+
+def sd_or_grid(h: Handle, src) -> None:
+    """Queue h's DHLA |= the DHLA image in the device tensor src."""
+    ptr, _, _keep = _buffer(src)
+    _check(lib().sd_or_grid(h.ptr, ptr), h.ptr)
+
+
+def sd_or_words(dst, src, words: int, count: int, stream=None) -> None:
+    """dst[:words] = OR of the count word arrays laid end to end in src (device tensors)."""
+    d, _, _k1 = _buffer(dst)
+    s_, _, _k2 = _buffer(src)
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().sd_or_words(d, s_, words, count, st))
+
+
+def sd_partition_pairs(h: Handle, direction: int, pairs, parts: int, out) -> np.ndarray:
+    """Group device pairs by the key of `direction` (& (parts - 1)) into the
+    device tensor out as (key, peer) pairs; returns the pairs per part."""
+    ptr, n, _keep = _buffer(pairs)
+    optr, _, _k2 = _buffer(out)
+    counts = (ctypes.c_uint64 * parts)()
+    _check(lib().sd_partition_pairs(h.ptr, direction, ptr if n else None, n, parts, optr if n else None,
+                                    counts), h.ptr)
+    return np.array(counts[:], dtype=np.int64)
 
 
 def sd_update_noalloc(p: sd_params, grid, pairs, stream=None) -> int:

@@ -110,4 +110,11 @@ def test_entry_points_reject_null_arguments_without_touching_a_gpu(sdmod):
     p = sdmod.sd_default_params()
     assert L.sd_update_noalloc(ctypes.byref(p), None, buf, 1, None) == ARG  # no DHLA
     assert L.sd_update_noalloc(None, buf, buf, 1, None) == ARG              # no parameters
+    assert L.sd_update_dir(None, 0, buf, 1) == ARG
+    assert L.sd_export_grid(None, buf) == ARG
+    assert L.sd_or_grid(None, buf) == ARG
+    assert L.sd_or_words(None, buf, 4, 1, None) == ARG
+    assert L.sd_or_words(buf, buf, 3, 1, None) == ARG                    # words not a multiple of 4
+    counts = (ctypes.c_uint64 * 4)()
+    assert L.sd_partition_pairs(None, 0, buf, 1, 4, buf, counts) == ARG
     assert isinstance(L.sd_last_error(None), bytes)

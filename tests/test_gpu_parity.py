@@ -188,6 +188,28 @@ def test_plane_update_keeps_bits_across_calls_and_modes(sd, O, torch_mod):
     _assert_report_equal(O, rep, ref, p)
 
 
+def test_plane_bins_follow_shifting_traffic(sd, O, torch_mod):
+    """Mode 6 lays out each round's bins from the previous round's counts.
+    Traffic that changes between rounds overflows them: rounds of uniform
+    pairs, then a flood to one destination from distinct sources (all its
+    outbound keys fall in one plane), then uniform pairs again (planes the
+    flood left nearly empty get many keys).  Keys beyond a bin's room set
+    their bits directly; the DHLA and the report still equal the oracle's."""
+    w = T.WORKLOADS["core"].with_(n=3 << 18)
+    rng = np.random.default_rng(5)
+    uni = rng.integers(0, 2**32, size=(1 << 18, 2), dtype=np.uint64).astype(np.uint32)
+    flood = np.empty((1 << 18, 2), np.uint32)
+    flood[:, 0] = T.mix32(np.arange(1 << 18, dtype=np.uint32) + np.uint32(7))
+    flood[:, 1] = 0xC0A80101
+    uni2 = rng.integers(0, 2**32, size=(1 << 18, 2), dtype=np.uint64).astype(np.uint32)
+    pairs = np.concatenate([uni, flood, uni2])
+    win = _window_of(w, pairs)
+    rep, ref = _full_check(sd, O, torch_mod, w, win,
+                           tuning=dict(mode=6, plane_round_log2=15, plane_unit_log2=12))
+    hit = rep.hits[(rep.hits["ip"] == 0xC0A80101) & (rep.hits["dir"] == 1)]
+    assert len(hit) == 1
+
+
 @pytest.mark.parametrize("mode", [1, 3, 5, 6])
 def test_ragged_and_misaligned_inputs(sd, O, torch_mod, mode):
     """Odd pair counts and buffers starting 8 or 4 bytes past a 16-byte
