@@ -53,18 +53,28 @@ GBITS_PER_PACKET = 800 * 8 / 1e9   # 800-byte average packet (§1, §5)
 CPU_SAMPLE_PAIRS = 1 << 26
 
 
+UPDATE_KERNELS = {5: "k_bin+k_apply", 6: "k_plane_bin+k_plane_apply"}
+UPDATE_SOURCES = {5: ["sd_binned.cu", "sd_common.cuh"], 6: ["sd_plane.cu", "sd_common.cuh"]}
+UPDATE_PROFILES = {5: "update_binned_core_window.txt", 6: "update_plane_core_window.txt"}
+
+
+def source_sha256(mode: int) -> str:
+    """sha256 of the update kernels' sources of a tuning mode, in order."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1803_11449_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in UPDATE_SOURCES.get(mode, ["sd_update.cu", "sd_common.cuh"]):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def profiled_traffic(mode: int, n: int):
     """DRAM bytes per launch set of the update for `n` pairs, from the
     committed ncu summary of the same kernel source; None when no summary
     matches the current source (the counters no longer describe it)."""
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_1803_11449_gb300", "csrc")
-    files = ["sd_binned.cu", "sd_common.cuh"] if mode == 5 else ["sd_update.cu", "sd_common.cuh"]
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    name = "update_binned_core_window.txt" if mode == 5 else "update_inplace_core_window.txt"
+    digest = source_sha256(mode)
+    name = UPDATE_PROFILES.get(mode, "update_inplace_core_window.txt")
     # the counters were taken for one mode-5 round; in-place modes have none committed
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
@@ -75,7 +85,7 @@ def profiled_traffic(mode: int, n: int):
             if ":" in line:
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-    if fields.get("source_sha256") != h.hexdigest() or "dram_bytes_per_pair" not in fields:
+    if fields.get("source_sha256") != digest or "dram_bytes_per_pair" not in fields:
         return None
     return float(fields["dram_bytes_per_pair"]) * n
 
@@ -116,6 +126,62 @@ def l2_roofline(ops_per_pair: int, n: int, t_upd: float) -> dict:
                     "ceiling_source": "profiles/update_inplace_uniform_l2_atomics.txt (measured: one "
                                       "red.or per bit-set, uniform pairs, L2 at 84.5% of peak)"})
     return out
+
+
+def ceilings_lib():
+    """libsd_ceilings.so: microbenchmarks of the rates that bound the update."""
+    import ctypes
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    L = ctypes.CDLL(b.CEILINGS_LIB)
+    d = ctypes.POINTER(ctypes.c_double)
+    L.sdc_smem_or_rate.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, d]
+    L.sdc_l2_rates.argtypes = [ctypes.c_uint64, d, d, d]
+    L.sdc_host_link.argtypes = [ctypes.c_uint64, d, d, d]
+    return L
+
+
+def smem_or_ceiling(words_log2: int = 13) -> float | None:
+    """Random shared-memory atomic ORs per second on this GPU (the bound of
+    the apply step, which sets every bit that way), measured now: the best
+    of a few block shapes."""
+    import ctypes
+    L = ceilings_lib()
+    best = None
+    for threads, bps in ((512, 2), (512, 4), (1024, 2)):
+        v = ctypes.c_double()
+        if L.sdc_smem_or_rate(words_log2, threads, bps, ctypes.byref(v)) == 0:
+            best = max(best or 0.0, v.value)
+    return best
+
+
+def run_ceilings(args, rank, world, local):
+    """The rates that bound the update, measured on this GPU (one JSON line)."""
+    import ctypes
+    import torch
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    L = ceilings_lib()
+    out = {"gpu": torch.cuda.get_device_name(local), "smem_atomic_or_per_s": {}}
+    for lw in (13, 15):
+        for threads, bps in ((256, 4), (512, 2), (512, 4), (1024, 1), (1024, 2)):
+            if (4 << lw) * bps > 200 * 1024:
+                continue
+            v = ctypes.c_double()
+            if L.sdc_smem_or_rate(lw, threads, bps, ctypes.byref(v)) == 0:
+                out["smem_atomic_or_per_s"][f"{4 << lw >> 10} KiB, {threads} threads x {bps} blocks/SM"] = v.value
+    out["l2"] = {}
+    for mib in (32, 64, 96):
+        r, w_, b_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        if L.sdc_l2_rates(mib << 20, ctypes.byref(r), ctypes.byref(w_), ctypes.byref(b_)) == 0:
+            out["l2"][f"{mib} MiB"] = {"read_gbs": r.value, "write_gbs": w_.value, "bulk_or_gbs": b_.value}
+    h2d, pr, pg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    if L.sdc_host_link(1 << 30, ctypes.byref(h2d), ctypes.byref(pr), ctypes.byref(pg)) == 0:
+        out["host_link_gbs"] = {"h2d_pinned_copy": h2d.value, "kernel_reads_pinned": pr.value,
+                                "kernel_reads_pageable": pg.value,
+                                "pairs_per_s_at_h2d": h2d.value * 1e9 / BYTES_PER_PAIR}
+    print(json.dumps(out), flush=True)
 
 
 def measured_peaks():
@@ -535,6 +601,17 @@ def run_ours(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     t_upd = statistics.mean(upd_alone)
+    # the on-chip bound of the binned updates: r * dirs random shared-memory
+    # atomic ORs per pair (the apply step), against their rate measured now
+    onchip = None
+    if tuning.mode in (5, 6):
+        ceiling = smem_or_ceiling()
+        achieved_ops = p.r * p.dirs * n / t_upd
+        onchip = {"bound": "shared-memory atomic ORs", "ops_per_pair": p.r * p.dirs,
+                  "achieved_ops_per_s": achieved_ops, "peak_ops_per_s": ceiling,
+                  "frac": achieved_ops / ceiling if ceiling else None,
+                  "peak_source": "sdc_smem_or_rate (random 32-bit atomic ORs into shared memory), measured in "
+                                 "this run"}
     achieved = BYTES_PER_PAIR * n / t_upd / 1e9
     clocks = clk.summary()
     if rank != 0:
@@ -581,12 +658,13 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak,
                      "traffic": profiled_traffic(tuning.mode, n) if WORKLOAD == "core" else None,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal": NOMINAL_HBM_GBS,
-                     "kernel": "k_bin+k_apply" if tuning.mode == 5 else "k_update",
+                     "kernel": UPDATE_KERNELS.get(tuning.mode, "k_update"),
                      "timed": "CUDA events around each sd_update of the sequential schedule "
                               "(the update kernels alone on the library's stream)",
                      "peak_source": f"hbm_gbs, {peak_kind}",
                      "algorithmic_bytes_per_pair": BYTES_PER_PAIR},
         "l2_random_op_roofline": l2_roofline(p.r * p.dirs, n, t_upd),
+        "onchip_roofline": onchip,
         "e2e": {"value": e2e, "unit": "Gpps", "h2d_bytes_per_step": BYTES_PER_PAIR * n,
                 "d2h_bytes_per_step": int(d2h / max(1, args.e2e_steps))},
         "gpu_launches": launches,
@@ -594,6 +672,70 @@ def run_ours(args, rank, world, local):
         "report": {"hits": int(rep.n_hits_total), "n_cand": rep.n_cand,
                    "n_hot_row0": [int(x) for x in rep.n_hot[:, 0]]},
         "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_shard(args, rank, world, local):
+    """One core window split over the ranks' GPUs (strong scaling): rank r
+    updates the r-th contiguous part of the window, the DHLAs are OR-merged
+    across ranks (shard.merge_across: all-to-all, the library's OR, an
+    all-gather), and the window is closed.  Every rank closes the merged
+    DHLA (the same report everywhere, and each rank's DHLA is cleared for the
+    next window); the elapsed time is the maximum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd, shard
+
+    torch.cuda.set_device(local)
+    win = window_for(0, n=args.pairs)          # the same window on every rank
+    n = len(win.pairs)
+    part = np.array_split(win.pairs, world)[rank]
+    mine = torch.from_numpy(np.ascontiguousarray(part).reshape(-1).view(np.int32)).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = T.WORKLOADS[WORKLOAD]
+    h = sd.sd_create(sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream.cuda_stream))
+    group = dist.group.WORLD if world > 1 else None
+
+    def step():
+        sd.sd_update(h, mine)
+        if world > 1:
+            shard.merge_across(h, group)
+        return sd.sd_close_window(h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    launches0 = sd.sd_kernel_launches()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            rep = step()
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+    launches = sd.sd_kernel_launches() - launches0
+    dist_barrier(world)
+    el = dist_max(elapsed, world)
+    sd.sd_destroy(h)
+    if rank != 0:
+        return
+    value = args.steps * n / el / 1e9
+    line = {
+        "metric": "packets/s (Gpps)", "value": value, "unit": "Gpps", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "pairs_per_step": n, "pairs_per_step_per_gpu": len(part),
+                   "parallelism": f"one window split over {world} GPU(s); DHLAs OR-merged across GPUs "
+                                  "(all-to-all, OR kernel, all-gather) before the close"},
+        "timed": "host clock around sd_update + merge + sd_close_window per step (report on the host)",
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "report": {"hits": int(rep.n_hits_total), "n_cand": rep.n_cand},
     }
     print(json.dumps(line), flush=True)
 
@@ -879,6 +1021,10 @@ def main():
                     help="window and sketch configuration of the default mode")
     ap.add_argument("--serving", action="store_true",
                     help="the serving engine in real time under Poisson arrivals")
+    ap.add_argument("--ceilings", action="store_true",
+                    help="measure the on-chip and host-link rates that bound the update")
+    ap.add_argument("--shard", action="store_true",
+                    help="one window split over the GPUs, DHLAs OR-merged across them (strong scaling)")
     ap.add_argument("--serve-links", type=int, default=16)
     ap.add_argument("--window-pairs", type=int, default=1 << 26)
     ap.add_argument("--serve-load", type=float, default=10.0, help="offered Gpps, all links")
@@ -903,6 +1049,10 @@ def main():
         run_batching(args, rank, world, local)
     elif args.serving:
         run_serving(args, rank, world, local)
+    elif args.shard:
+        run_shard(args, rank, world, local)
+    elif args.ceilings:
+        run_ceilings(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -17,8 +17,12 @@
  *     returns (sd_report.hits) belong to the handle.
  *   - A handle is not thread-safe: calls on one handle must be serialised by
  *     the caller.  Different handles are independent.
- *   - All device work runs on the handle's CUDA stream (sd_params.cuda_stream,
- *     or a stream the handle creates), in call order.
+ *   - All device work is ordered on the handle's CUDA stream
+ *     (sd_params.cuda_stream, or a stream the handle creates), in call order.
+ *     A window close runs its kernels on the handle's own side stream of the
+ *     device's highest priority, joined to that stream before and after (so
+ *     a close is scheduled ahead of other queued work, such as the next
+ *     window's update of another handle).
  *
  * Hash group (a reading of §3.1/§3.2, which ask only for "random hash
  * functions"), fixed so every implementation agrees bit for bit:
@@ -161,7 +165,9 @@ typedef struct {
                                 Both give the same K and the same report. */
     uint32_t bin_batch_mib;  /* modes 5 and 6, sd_update_many: MiB of bins one batched
                                 round may use (bounds the links per round); default 8192 */
-    uint32_t plane_tile_pairs; /* mode 6: pairs per binning tile: 1024, 2048 or 4096 */
+    uint32_t plane_tile_pairs; /* mode 6: pairs per binning tile: 1024, 2048, 4096 or 8192
+                                  (within 200 KiB of shared memory: 8 dirs bytes per pair
+                                  plus 16 bytes per plane) */
     uint32_t plane_round_log2; /* mode 6: pairs per count/bin/apply round, log2: 10..28 */
     uint32_t plane_unit_log2;  /* mode 6: bin entries per apply step, log2: 8..24 */
 } sd_tuning;

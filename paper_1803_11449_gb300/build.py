@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsd.so")
+# microbenchmarks of the rates that bound the update (the benchmark's
+# roofline lines); a library of its own, not part of the detection API
+CEILINGS_SRC = "sd_ceilings.cu"
+CEILINGS_LIB = os.path.join(OUT_DIR, "libsd_ceilings.so")
 SOURCES = ["sd_update.cu", "sd_binned.cu", "sd_plane.cu", "sd_close.cu", "sd_join.cu", "sd_shard.cu",
            "sd_api.cu", "sd_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "sd_common.cuh"), os.path.join(INCLUDE, "sd.h")]
@@ -69,6 +73,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
+    csrc = os.path.join(CSRC, CEILINGS_SRC)
+    if force or _stale(CEILINGS_LIB, [csrc]):
+        tmp = CEILINGS_LIB + f".tmp{os.getpid()}"
+        cmd = [cc] + FLAGS + ["-shared", csrc, "-o", tmp]
+        res = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if res.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout.decode(errors="replace"))
+        os.replace(tmp, CEILINGS_LIB)
     return LIB
 
 

@@ -459,11 +459,16 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     // a DHLA of 1024 slices or more takes 2048-pair tiles, so that each
     // slice's run in a tile stays long enough for coalesced bin writes
     // (autotuned on the 2 x 128 MiB stress sketch: 50 ms vs 72 ms per 2^30 pairs)
-    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192, 4096, 23, 15};
+    h->T = Tuning{5, 512, 0, 2, 13, 15, 1024, 24, 100, 0, 8192, 8192, 26, 14};
     if ((uint64_t)p->dirs * G.dir_words >= (1ull << 25) && p->dirs * p->r <= 8) h->T.bin_tile_pairs = 2048;
     // binned by estimator bit wherever one bit plane fits a block's shared
-    // memory (r 2^k bits: every workload of the scope table)
+    // memory (r 2^k bits: every workload of the scope table), with tiles of
+    // 8192 pairs and rounds of 2^26 (measured on GB300 over tiles 1024-8192,
+    // rounds 2^22-2^26 and apply units 2^13-2^16: 0.67 ms per 2^26-pair core
+    // window, against 0.79 ms at 4096 / 2^24 and 1.2 ms at 2048 / 2^24);
+    // 4096-pair tiles where 8192 would not fit shared memory
     if (plane_fits(G)) h->T.mode = 6;
+    if (plane_bin_smem_bytes(h->T.plane_tile_pairs, G.dirs, G.dirs * G.g) > 200 * 1024) h->T.plane_tile_pairs = 4096;
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
 
@@ -476,7 +481,12 @@ static int create_impl(const sd_params *p, sd_handle *h) {
         SD_CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
         h->own_stream = true;
     }
-    SD_CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    // the side stream (staged host copies, and the close's kernels) has the
+    // device's highest priority: a close is scheduled ahead of other queued
+    // work, e.g. another window's update, whenever an SM frees up
+    int prio_least = 0, prio_greatest = 0;
+    SD_CK(h, cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    SD_CK(h, cudaStreamCreateWithPriority(&h->copy_stream, cudaStreamNonBlocking, prio_greatest));
     for (int b = 0; b < 2; b++) {
         SD_CK(h, cudaEventCreateWithFlags(&h->ev_h2d[b], cudaEventDisableTiming));
         SD_CK(h, cudaEventCreateWithFlags(&h->ev_kern[b], cudaEventDisableTiming));
@@ -1236,6 +1246,19 @@ int sd_close_window(sd_handle *h, sd_report *out) {
     NvtxRange nvtx("sd_close_window");
     if (!h || !out) return SD_ERR_ARG;
     DeviceGuard dg(h->p.device);
+    // the close runs on the handle's high-priority side stream, after
+    // everything queued on its stream, and the stream waits for the close
+    SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
+    SD_CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_batch, 0));
+    std::swap(h->stream, h->copy_stream);
+    struct Rejoin {
+        sd_handle *h;
+        ~Rejoin() {
+            std::swap(h->stream, h->copy_stream);
+            cudaEventRecord(h->ev_batch, h->copy_stream);
+            cudaStreamWaitEvent(h->stream, h->ev_batch, 0);
+        }
+    } rejoin{h};
     CloseTrace trace;
     int rc = close_phase_a(h, out);
     if (rc != SD_OK) return rc;
@@ -1746,8 +1769,10 @@ int sd_set_tuning(sd_handle *h, const sd_tuning *t) {
     }
     if (t->plane_tile_pairs) {
         const uint32_t tp = t->plane_tile_pairs;
-        if (tp != 1024 && tp != 2048 && tp != 4096)
-            return h->fail(SD_ERR_ARG, "sd_set_tuning: plane_tile_pairs must be 1024, 2048 or 4096");
+        if (tp != 1024 && tp != 2048 && tp != 4096 && tp != 8192)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: plane_tile_pairs must be 1024, 2048, 4096 or 8192");
+        if (plane_bin_smem_bytes(tp, h->G.dirs, h->G.dirs * h->G.g) > 200 * 1024)
+            return h->fail(SD_ERR_ARG, "sd_set_tuning: a binning tile of %u pairs does not fit shared memory", tp);
         T.plane_tile_pairs = tp;
     }
     if (t->plane_round_log2) {

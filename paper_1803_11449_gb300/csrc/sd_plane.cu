@@ -51,6 +51,8 @@ namespace {
 constexpr uint32_t kPlaneThreads = 512;   // k_plane_bin / k_plane_count block
 constexpr uint32_t kApplyThreads = 512;   // k_plane_apply block
 constexpr uint32_t kHeldReservations = 2;  // reservation results a thread holds across the scatter
+constexpr uint32_t kBinTilesPerBlock = 8;   // k_plane_bin tiles per block (blocks retire as a round runs)
+constexpr uint32_t kApplyUnitsPerBlock = 4; // k_plane_apply units per block
 
 __device__ __forceinline__ uint32_t h1v(uint64_t A1, uint64_t B1, uint32_t lg, uint32_t y) {
     return (uint32_t)((A1 * (uint64_t)y + B1) >> (64u - lg));
@@ -201,29 +203,52 @@ k_plane_count(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneA
 }
 
 // -------------------------------------------------------------------- bin
-// A thread keeps PPT pairs' DIRS entries in registers as (key, bin << 16 |
-// rank) while the block counts them per plane; the tile is then scattered
-// into plane order in shared memory and written out one thread per entry,
-// so each plane's run goes to consecutive addresses of its bin.
-template <int DIRS, int PPT>
-__global__ void __launch_bounds__(kPlaneThreads, 2)
+// A thread keeps PPT pairs' DIRS entries in registers as (key, plane << 16
+// | rank) while the block counts them per plane; the tile is then scattered
+// into plane order in shared memory as 64-bit (plane << 32 | key) entries
+// and written out one thread per entry, so each plane's run goes to
+// consecutive addresses of its bin.
+template <int DIRS, int PPT, bool FULL>
+__device__ __forceinline__ void bin_hash(uint32_t cnt, const uint32_t (&ps)[PPT], const uint32_t (&pt)[PPT],
+                                         uint32_t g, uint32_t lg, uint64_t A1a, uint64_t B1a, uint64_t A1b,
+                                         uint64_t B1b, uint32_t *hist, uint32_t (&key)[PPT * DIRS],
+                                         uint32_t (&tag)[PPT * DIRS]) {
+#pragma unroll
+    for (int j = 0; j < PPT / 2; j++) {
+        const uint32_t pu = threadIdx.x + (uint32_t)j * blockDim.x;  // 2-pair unit within the tile
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const bool ok = FULL || 2 * pu + q < cnt;
+#pragma unroll
+            for (int d = 0; d < DIRS; d++) {
+                const int e = (2 * j + q) * DIRS + d;
+                key[e] = d ? pt[2 * j + q] : ps[2 * j + q];
+                const uint32_t b = d ? g + h1v(A1b, B1b, lg, ps[2 * j + q]) : h1v(A1a, B1a, lg, pt[2 * j + q]);
+                tag[e] = 0xFFFFFFFFu;
+                if (ok) tag[e] = (b << 16) | atomicAdd(&hist[b], 1u);
+            }
+        }
+    }
+}
+
+template <int DIRS, int PPT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArgs P) {
     constexpr int E = PPT * DIRS;
-    extern __shared__ uint32_t sm[];
+    extern __shared__ unsigned long long sm64[];
     __shared__ uint32_t s_warp[32];
     __shared__ bool s_last;
     const uint32_t NB = P.nbins, g = G.g, lg = G.lg;
     const uint32_t TP = blockDim.x * PPT;
-    uint32_t *hist = sm;                 // [NB] entries of each plane in the tile
-    uint32_t *offs = hist + NB;          // [NB] first sorted position of each plane
-    uint32_t *gdst = offs + NB;          // [NB] bin index of sorted position 0 (mod 2^32)
-    uint32_t *lim = gdst + NB;           // [NB] sorted positions below this fit the plane's bin
-    uint32_t *skey = lim + NB;           // [DIRS TP] keys in plane order
-    uint16_t *sbin = reinterpret_cast<uint16_t *>(skey + (size_t)DIRS * TP);  // [DIRS TP]
+    unsigned long long *sent = sm64;                               // [DIRS TP] (plane << 32 | key), plane order
+    uint2 *dst = reinterpret_cast<uint2 *>(sent + (size_t)DIRS * TP);  // [NB] (bin index of sorted position 0,
+                                                                   //  sorted positions below .y fit the bin)
+    uint32_t *hist = reinterpret_cast<uint32_t *>(dst + NB);       // [NB] entries of each plane in the tile
+    uint32_t *offs = hist + NB;                                    // [NB] first sorted position of each plane
     const uint64_t A1a = G.h[0].A1, B1a = G.h[0].B1, A1b = G.h[1].A1, B1b = G.h[1].B1;
     const uint64_t ntiles = (n + TP - 1) / TP;
     const bool vec = ((uintptr_t)pairs & 15u) == 0;
-    // bins owned by this thread in the scan (contiguous chunk)
+    // planes owned by this thread in the scan (contiguous chunk)
     const uint32_t per = (NB + blockDim.x - 1) / blockDim.x;
     const uint32_t b0 = min(threadIdx.x * per, NB), b1 = min(b0 + per, NB);
     // this thread's pairs of tile t: 2-pair units threadIdx.x + j blockDim.x
@@ -255,31 +280,17 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
     uint32_t nps[PPT], npt[PPT];  // the next tile's pairs, loaded while the current one is written out
     load_tile(blockIdx.x, nps, npt);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint64_t base = t * TP;
-        const uint64_t left = n - base;
+        const uint64_t left = n - t * TP;
         const uint32_t cnt = left < TP ? (uint32_t)left : TP;
+        const bool full = cnt == TP;
         uint32_t key[E], tag[E];
-#pragma unroll
-        for (int j = 0; j < PPT / 2; j++) {
-            const uint32_t pu = threadIdx.x + (uint32_t)j * blockDim.x;  // 2-pair unit within the tile
-            const uint32_t ss[2] = {nps[2 * j], nps[2 * j + 1]}, tt[2] = {npt[2 * j], npt[2 * j + 1]};
-            const bool ok[2] = {2 * pu < cnt, 2 * pu + 1 < cnt};
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-#pragma unroll
-                for (int d = 0; d < DIRS; d++) {
-                    const int e = (2 * j + q) * DIRS + d;
-                    key[e] = d ? tt[q] : ss[q];
-                    const uint32_t b = d ? g + h1v(A1b, B1b, lg, ss[q]) : h1v(A1a, B1a, lg, tt[q]);
-                    tag[e] = 0xFFFFFFFFu;
-                    if (ok[q]) tag[e] = (b << 16) | atomicAdd(&hist[b], 1u);
-                }
-            }
-        }
+        if (full) bin_hash<DIRS, PPT, true>(cnt, nps, npt, g, lg, A1a, B1a, A1b, B1b, hist, key, tag);
+        else bin_hash<DIRS, PPT, false>(cnt, nps, npt, g, lg, A1a, B1a, A1b, B1b, hist, key, tag);
         __syncthreads();
         // planes of this thread's chunk: sorted offsets, and their runs
-        // reserved in the bins (the atomics' results are used after the
-        // scatter, so their round trip overlaps it)
+        // reserved in the bins (the first kHeldReservations atomics' results
+        // are used after the scatter, so their round trip overlaps it; with
+        // more planes per thread the rest are resolved at once)
         uint32_t run = 0;
         {
             uint32_t sum = 0;
@@ -305,9 +316,6 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
             __syncthreads();
             run = incl - sum + (wid ? s_warp[wid - 1] : 0u);
         }
-        // (the first kHeldReservations of a thread's planes keep their
-        // results in registers until after the scatter; with more planes per
-        // thread than that, the rest are resolved at once)
         uint32_t res[kHeldReservations], rrun[kHeldReservations], rcap[kHeldReservations],
             roff[kHeldReservations];
 #pragma unroll
@@ -334,8 +342,7 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
             offs[b] = run;
             if (h) {
                 const uint32_t pos = atomicAdd(&P.cnt[b], h), c = P.cap[b];
-                gdst[b] = P.binoff[b] + pos - run;
-                lim[b] = run + (c > pos ? c - pos : 0u);
+                dst[b] = make_uint2(P.binoff[b] + pos - run, run + (c > pos ? c - pos : 0u));
             }
             hist[b] = 0;
             run += h;
@@ -346,29 +353,28 @@ k_plane_bin(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneArg
         for (int e = 0; e < E; e++) {
             if (tag[e] == 0xFFFFFFFFu) continue;
             const uint32_t b = tag[e] >> 16;
-            const uint32_t pos = offs[b] + (tag[e] & 0xFFFFu);
-            skey[pos] = key[e];
-            sbin[pos] = (uint16_t)b;
+            sent[offs[b] + (tag[e] & 0xFFFFu)] = ((unsigned long long)b << 32) | key[e];
         }
         load_tile(t + gridDim.x, nps, npt);
 #pragma unroll
         for (uint32_t q = 0; q < kHeldReservations; q++) {
             const uint32_t b = b0 + q;
-            if (b < b1) {
-                gdst[b] = roff[q] + res[q] - rrun[q];
-                lim[b] = rrun[q] + (rcap[q] > res[q] ? rcap[q] - res[q] : 0u);
-            }
+            if (b < b1)
+                dst[b] = make_uint2(roff[q] + res[q] - rrun[q], rrun[q] + (rcap[q] > res[q] ? rcap[q] - res[q] : 0u));
         }
         __syncthreads();
-        // write-out: sorted entry q of plane b goes to bins[gdst[b] + q]
+        // write-out: sorted entry q of plane b goes to bins[dst[b].x + q]
         // while its bin has room (plain stores: a plane's run is a fraction
         // of a line, and the line is completed by other tiles; streaming
         // stores would push the partial lines to DRAM several times over)
         const uint32_t nent = cnt * DIRS;
+#pragma unroll 4
         for (uint32_t q = threadIdx.x; q < nent; q += blockDim.x) {
-            const uint32_t b = sbin[q];
-            if (q < lim[b]) P.bins[(uint32_t)(gdst[b] + q)] = skey[q];
-            else set_key_bits<DIRS>(G, P, b, skey[q]);
+            const unsigned long long ent = sent[q];
+            const uint32_t b = (uint32_t)(ent >> 32);
+            const uint2 d = dst[b];
+            if (q < d.y) P.bins[(uint32_t)(d.x + q)] = (uint32_t)ent;
+            else set_key_bits<DIRS>(G, P, b, (uint32_t)ent);
         }
     }
     // the last block: apply units of the bins' actual contents
@@ -402,7 +408,7 @@ __device__ __forceinline__ void apply_key(uint32_t *pl, const Geometry &G, uint3
 // reduction, the other buffer's, to stay in flight).
 template <int R>
 __global__ void __launch_bounds__(kApplyThreads)
-k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf) {
+k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf, uint32_t per_block) {
     extern __shared__ uint4 pl4_all[];  // nbuf planes of ps words
     __shared__ uint32_t s_unit;
     __shared__ uint32_t s_warp[32];
@@ -410,7 +416,10 @@ k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf) {
     const uint32_t NB = P.nbins;
     const uint32_t rw = (1u << G.k) >> 5;
     const uint32_t total = P.unit_start[NB];
-    for (uint32_t it = 0;; it++) {
+    // a block takes at most per_block units (the grid holds enough blocks
+    // for every unit), so that blocks retire as the round proceeds and
+    // other streams' work (a window close) gets SMs in between
+    for (uint32_t it = 0; it < per_block; it++) {
         uint4 *pl4 = pl4_all + (size_t)(it % nbuf) * (P.ps / 4);
         uint32_t *pl = reinterpret_cast<uint32_t *>(pl4);
         if (threadIdx.x == 0) {
@@ -437,14 +446,17 @@ k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf) {
         const uint4 *e4 = reinterpret_cast<const uint4 *>(P.bins + beg);  // beg is a multiple of 4
         const uint32_t n4 = (end - beg) / 4;
         uint32_t q = threadIdx.x;
-        for (; q + blockDim.x < n4; q += 2 * blockDim.x) {
-            const uint4 a = ld_stream_v4(e4 + q), c = ld_stream_v4(e4 + q + blockDim.x);
-            apply_key<R>(pl, G, A0, rw, a.x); apply_key<R>(pl, G, A0, rw, a.y);
-            apply_key<R>(pl, G, A0, rw, a.z); apply_key<R>(pl, G, A0, rw, a.w);
-            apply_key<R>(pl, G, A0, rw, c.x); apply_key<R>(pl, G, A0, rw, c.y);
-            apply_key<R>(pl, G, A0, rw, c.z); apply_key<R>(pl, G, A0, rw, c.w);
+        for (; q + 3 * blockDim.x < n4; q += 4 * blockDim.x) {
+            uint4 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] = ld_stream_v4(e4 + q + j * blockDim.x);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                apply_key<R>(pl, G, A0, rw, v[j].x); apply_key<R>(pl, G, A0, rw, v[j].y);
+                apply_key<R>(pl, G, A0, rw, v[j].z); apply_key<R>(pl, G, A0, rw, v[j].w);
+            }
         }
-        if (q < n4) {
+        for (; q < n4; q += blockDim.x) {
             const uint4 a = ld_stream_v4(e4 + q);
             apply_key<R>(pl, G, A0, rw, a.x); apply_key<R>(pl, G, A0, rw, a.y);
             apply_key<R>(pl, G, A0, rw, a.z); apply_key<R>(pl, G, A0, rw, a.w);
@@ -596,44 +608,59 @@ k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometr
 
 // --------------------------------------------------------------- launchers
 size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins) {
-    return (size_t)4 * nbins * 4 + (size_t)dirs * tile_pairs * 6;
+    return (size_t)dirs * tile_pairs * 8 + (size_t)nbins * 16;
 }
 
-template <int DIRS, int PPT>
+template <int DIRS, int PPT, int THREADS>
 static cudaError_t launch_plane_bin(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P,
                                     int num_sms, cudaStream_t s) {
-    auto kern = k_plane_bin<DIRS, PPT>;
+    auto kern = k_plane_bin<DIRS, PPT, THREADS>;
     const size_t smem = plane_bin_smem_bytes(P.tile_pairs, DIRS, P.nbins);
     int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kPlaneThreads, smem, &per_sm);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), THREADS, smem, &per_sm);
     if (e != cudaSuccess) return e;
+    // about kBinTilesPerBlock tiles per block (not one persistent block per
+    // SM), so that blocks retire as the round proceeds and other streams'
+    // work gets SMs in between
     const uint64_t tiles = (n + P.tile_pairs - 1) / P.tile_pairs;
-    uint64_t blocks = (uint64_t)num_sms * per_sm;
+    uint64_t blocks = (tiles + kBinTilesPerBlock - 1) / kBinTilesPerBlock;
+    if (blocks < (uint64_t)num_sms * per_sm) blocks = (uint64_t)num_sms * per_sm;
     if (tiles < blocks) blocks = tiles;
-    kern<<<(unsigned)blocks, kPlaneThreads, smem, s>>>(pairs, n, G, P);
+    kern<<<(unsigned)blocks, THREADS, smem, s>>>(pairs, n, G, P);
     return cudaGetLastError();
 }
 
+// tiles of 1024 to 4096 pairs: 512 threads with 2, 4 or 8 pairs each;
+// 8192: 1024 threads with 8 each (one block per SM)
 template <int DIRS>
 static cudaError_t launch_plane_bin_d(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P,
                                       int num_sms, cudaStream_t s) {
-    switch (P.tile_pairs / kPlaneThreads) {
-        case 2: return launch_plane_bin<DIRS, 2>(pairs, n, G, P, num_sms, s);
-        case 4: return launch_plane_bin<DIRS, 4>(pairs, n, G, P, num_sms, s);
-        case 8: return launch_plane_bin<DIRS, 8>(pairs, n, G, P, num_sms, s);
+    switch (P.tile_pairs) {
+        case 1024: return launch_plane_bin<DIRS, 2, 512>(pairs, n, G, P, num_sms, s);
+        case 2048: return launch_plane_bin<DIRS, 4, 512>(pairs, n, G, P, num_sms, s);
+        case 4096: return launch_plane_bin<DIRS, 8, 512>(pairs, n, G, P, num_sms, s);
+        case 8192: return launch_plane_bin<DIRS, 8, 1024>(pairs, n, G, P, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int R>
-static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, int num_sms, cudaStream_t s) {
+static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, uint64_t n, int num_sms,
+                                     cudaStream_t s) {
     auto kern = k_plane_apply<R>;
     const uint32_t nbuf = (size_t)P.ps * 8 <= (size_t)100 * 1024 ? 2u : 1u;
     const size_t smem = (size_t)P.ps * 4 * nbuf;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kApplyThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(num_sms * per_sm), kApplyThreads, smem, s>>>(G, P, nbuf);
+    // units of the round: at most (keys + slack) / unit + one partial unit per plane
+    const uint64_t keys = (uint64_t)(P.nbins / G.g) * n;
+    const uint64_t most = (keys + keys / 8 + 40ull * P.nbins) / P.unit + P.nbins;
+    const uint32_t per_block = kApplyUnitsPerBlock;
+    uint64_t blocks = (most + per_block - 1) / per_block;
+    if (blocks < (uint64_t)num_sms * per_sm) blocks = (uint64_t)num_sms * per_sm;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    kern<<<(unsigned)blocks, kApplyThreads, smem, s>>>(G, P, nbuf, per_block);
     return cudaGetLastError();
 }
 
@@ -656,12 +683,12 @@ cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry
                                 : launch_plane_bin_d<1>(pairs, n, G, P, num_sms, s);
     if (e != cudaSuccess) return e;
     switch (G.r) {
-        case 3: return launch_plane_apply<3>(G, P, num_sms, s);
-        case 4: return launch_plane_apply<4>(G, P, num_sms, s);
-        case 5: return launch_plane_apply<5>(G, P, num_sms, s);
-        case 6: return launch_plane_apply<6>(G, P, num_sms, s);
-        case 7: return launch_plane_apply<7>(G, P, num_sms, s);
-        case 8: return launch_plane_apply<8>(G, P, num_sms, s);
+        case 3: return launch_plane_apply<3>(G, P, n, num_sms, s);
+        case 4: return launch_plane_apply<4>(G, P, n, num_sms, s);
+        case 5: return launch_plane_apply<5>(G, P, n, num_sms, s);
+        case 6: return launch_plane_apply<6>(G, P, n, num_sms, s);
+        case 7: return launch_plane_apply<7>(G, P, n, num_sms, s);
+        case 8: return launch_plane_apply<8>(G, P, n, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

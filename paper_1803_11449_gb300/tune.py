@@ -10,7 +10,7 @@ import itertools
 
 from . import sd
 
-MODES = (0, 1, 2, 3, 4, 5)
+MODES = (0, 1, 2, 3, 4, 5, 6)
 UNROLLS = (1, 2, 4)
 THREADS = (256, 512, 1024)
 FILTERS = (12, 13, 14)   # log2 entries of the shared-memory filter (modes 3, 4)
@@ -19,12 +19,19 @@ FILTERS = (12, 13, 14)   # log2 entries of the shared-memory filter (modes 3, 4)
 BINNED = [dict(bin_slice_log2=sl, bin_tile_pairs=tp, bin_chunk_log2=ch, bin_slack_pct=100)
           for sl in (13, 14, 15) for tp in (512, 1024, 2048) for ch in (21, 22, 23, 24)]
 
+PLANES = [dict(plane_tile_pairs=tp, plane_round_log2=rd, plane_unit_log2=un)
+          for tp in (1024, 2048, 4096) for rd in (21, 22, 23, 24) for un in (13, 14, 15, 16)]
+
 
 def _space(modes, unrolls, threads, filters):
     for mode in modes:
         if mode == 5:
             for b in BINNED:
                 yield dict(mode=5, **b)
+            continue
+        if mode == 6:
+            for b in PLANES:
+                yield dict(mode=6, **b)
             continue
         for unroll, nthr in itertools.product(unrolls, threads):
             for flog in (filters if mode >= 3 else (13,)):
