@@ -740,6 +740,59 @@ def run_shard(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_noalloc(args, rank, world, local):
+    """sd_update_noalloc (the binned update with its scratch in a fixed
+    array inside the library) on the core window, beside sd_update in the
+    same binned mode (5) and in the default mode: CUDA events around each
+    call, pairs resident in HBM (one JSON line)."""
+    import torch
+
+    from paper_1803_11449_gb300 import build as b
+    b.build()
+    from paper_1803_11449_gb300 import sd
+
+    torch.cuda.set_device(local)
+    win = window_for(rank, n=args.pairs)
+    n = len(win.pairs)
+    dev = torch.from_numpy(win.pairs.reshape(-1).view(np.int32)).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = T.WORKLOADS[WORKLOAD]
+    p = sd.params_for(w, seed=T.window_seed(2), device=local, cuda_stream=stream.cuda_stream)
+    grid = torch.zeros(p.dirs * sd.sd_grid_words(p), dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ts.append(a.elapsed_time(e))
+        return statistics.median(ts)
+
+    def noalloc():
+        rc = sd.sd_update_noalloc(p, grid, dev, stream)
+        assert rc == sd.SD_OK, rc
+    timed(noalloc, args.warmup)
+    t_na = timed(noalloc, args.steps)
+    out = {"metric": "sd_update_noalloc, pairs/s (Gpairs/s)", "n_pairs": n, "workload": WORKLOAD_DESC,
+           "noalloc_ms": t_na, "noalloc_gpps": n / t_na / 1e6}
+    for mode in (5, None):
+        h = sd.sd_create(p)
+        if mode is not None:
+            sd.sd_set_tuning(h, mode=mode)
+        timed(lambda: sd.sd_update(h, dev), args.warmup)
+        t = timed(lambda: sd.sd_update(h, dev), args.steps)
+        key = "sd_update_mode5" if mode == 5 else f"sd_update_default_mode{sd.sd_get_tuning(h).mode}"
+        out[key + "_ms"] = t
+        out[key + "_gpps"] = n / t / 1e6
+        sd.sd_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def _batch_window(args):
     """(pairs, planted count) of link `link` of the batching workload."""
     link, n, planted = args
@@ -962,7 +1015,12 @@ def run_serving(args, rank, world, local):
     close = [r.close_s for r in srv.reports]
     n_win = len(srv.reports)
     steps = srv.steps
+    admitted_links = list(srv.admitted)
     srv.shutdown()
+    # the same offered load, one window at a time: each batch through
+    # sd_update of its link's handle as it comes, each full window closed
+    # with sd_close_window before the next batch is taken
+    alone = _one_at_a_time(args, admitted_links, rings, arr_t, arr_n, T_run, local, stream, rank, nl)
     value = dist_max(elapsed, world)
     if rank != 0:
         return
@@ -982,9 +1040,104 @@ def run_serving(args, rank, world, local):
         "windows_closed": n_win, "attacks_reported_in_warmup_window": {str(k): v for k, v in found.items()},
         "latency_ms_last_arrival_to_report": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n": len(lat)},
         "close_ms": {"p50": pct(close, 50), "p99": pct(close, 99)},
+        "one_window_at_a_time": alone,
         "clocks": clock.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def _one_at_a_time(args, links, rings, arr_t, arr_n, T_run, local, stream, rank, nl):
+    """The serving workload without the engine: one handle per link, every
+    arriving batch fed by sd_update as it comes (oldest first), a link's
+    window closed by sd_close_window as soon as it is full, all on one
+    stream, one call at a time.  A batch that would leave a link with more
+    than one window of arrived pairs not yet fed is dropped, as the engine's
+    ring would.  Returns served Gpps,
+    dropped pairs and the latency from a window's last batch to its report."""
+    import heapq
+
+    from paper_1803_11449_gb300 import sd
+
+    W = args.window_pairs
+    w = T.WORKLOADS[WORKLOAD]
+    hs = {}
+    for i in links:
+        h = sd.sd_create(sd.params_for(w, seed=T.window_seed(4, link=rank * nl + i), device=local,
+                                       cuda_stream=stream.cuda_stream))
+        # batches are at most 2^22 pairs: bins for rounds of that size
+        sd.sd_set_tuning(h, mode=sd.sd_get_tuning(h).mode, plane_round_log2=22)
+        hs[i] = h
+    fill = {i: 0 for i in links}          # pairs of the open window
+    tail = {i: 0 for i in links}          # ring offset of the next pair
+    backlog = {i: 0 for i in links}       # accepted, not yet fed
+    events = []                           # (arrival, link, pairs): a global arrival-order queue
+    for i in links:
+        for t, n in zip(arr_t[i], arr_n[i]):
+            events.append((float(t), i, int(n)))
+    events.sort()
+    queue = []
+    served = dropped = 0
+    lat, close = [], []
+    nxt = 0
+
+    def feed(i, n):
+        ring = rings[i]
+        off = tail[i] % W
+        take = min(n, W - off)
+        sd.sd_update(hs[i], ring[2 * off:2 * (off + take)])
+        if take < n:
+            sd.sd_update(hs[i], ring[:2 * (n - take)])
+        tail[i] += n
+
+    # warm-up: one window on every link
+    for i in links:
+        feed(i, W)
+        sd.sd_close_window(hs[i])
+    tail = {i: 0 for i in links}
+    torch_sync = __import__("torch").cuda.synchronize
+    torch_sync()
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(events) and events[nxt][0] <= now:
+            t, i, n = events[nxt]
+            nxt += 1
+            if backlog[i] + n <= W:       # the engine's ring holds one window of arrived pairs
+                heapq.heappush(queue, (t, i, n))
+                backlog[i] += n
+            else:
+                dropped += n
+        if not queue:
+            if now >= T_run and nxt >= len(events):
+                break
+            time.sleep(20e-6)
+            continue
+        t, i, n = heapq.heappop(queue)
+        backlog[i] -= n
+        while n:
+            take = min(n, W - fill[i])
+            feed(i, take)
+            fill[i] += take
+            served += take
+            n -= take
+            if fill[i] == W:
+                c0 = time.perf_counter()
+                sd.sd_close_window(hs[i])
+                done = time.perf_counter()
+                close.append(done - c0)
+                lat.append(done - t0 - t)
+                fill[i] = 0
+    torch_sync()
+    elapsed = time.perf_counter() - t0
+    for h in hs.values():
+        sd.sd_destroy(h)
+    pct = lambda a, q: 1e3 * float(np.percentile(a, q)) if len(a) else None
+    return {"value": served / elapsed / 1e9, "unit": "Gpps", "served_pairs": int(served),
+            "dropped_pairs": int(dropped), "windows_closed": len(close),
+            "latency_ms_last_arrival_to_report": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n": len(lat)},
+            "close_ms": {"p50": pct(close, 50), "p99": pct(close, 99)},
+            "schedule": "plain sd_update per batch and sd_close_window per full window, one call at a time, "
+                        "one stream"}
 
 
 def main():
@@ -1021,6 +1174,8 @@ def main():
                     help="window and sketch configuration of the default mode")
     ap.add_argument("--serving", action="store_true",
                     help="the serving engine in real time under Poisson arrivals")
+    ap.add_argument("--noalloc", action="store_true",
+                    help="time sd_update_noalloc beside sd_update on the window")
     ap.add_argument("--ceilings", action="store_true",
                     help="measure the on-chip and host-link rates that bound the update")
     ap.add_argument("--shard", action="store_true",
@@ -1053,6 +1208,8 @@ def main():
         run_shard(args, rank, world, local)
     elif args.ceilings:
         run_ceilings(args, rank, world, local)
+    elif args.noalloc:
+        run_noalloc(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:
