@@ -163,12 +163,13 @@ typedef struct {
                                    direction SD_FLAG_OVERLOAD_CANDS, and a first
                                    stage above pair_cap tuples SD_FLAG_OVERLOAD_PAIRS.
                                 Both give the same K and the same report. */
-    uint32_t bin_batch_mib;  /* modes 5 and 6, sd_update_many: MiB of bins one batched
-                                round may use (bounds the links per round); default 8192 */
+    uint32_t bin_batch_mib;  /* mode 5, sd_update_many: MiB of bins one batched round
+                                may use (bounds the links per round); default 8192 */
     uint32_t plane_tile_pairs; /* mode 6: pairs per binning tile: 1024, 2048, 4096 or 8192
                                   (within 200 KiB of shared memory: 8 dirs bytes per pair
                                   plus 16 bytes per plane) */
-    uint32_t plane_round_log2; /* mode 6: pairs per count/bin/apply round, log2: 10..28 */
+    uint32_t plane_round_log2; /* mode 6: pairs per count/bin/apply round, log2: 10..28
+                                  (also the members' rounds of a batch the handle drives) */
     uint32_t plane_unit_log2;  /* mode 6: bin entries per apply step, log2: 8..24 */
 } sd_tuning;
 
@@ -185,11 +186,13 @@ int sd_check_params(const sd_params *p);
  * *p is invalid. */
 uint64_t sd_grid_words(const sd_params *p);
 
-/* Device bytes a handle with *p holds from sd_create on: the DHLA, the hot
- * sets, the candidate and hit buffers; 0 if *p is invalid.  Not counted,
- * because they are allocated on first use: the staging of host-pointer
- * updates (2 * stage_pairs * 8 bytes) and the binned update's scratch
- * (sd_scratch_bytes). */
+/* Device bytes a handle with *p holds once it has updated with its default
+ * tuning: the DHLA, the hot sets, the candidate and hit buffers, and where
+ * one bit plane fits (the default plane-binned update, tuning mode 6) the
+ * plane-major DHLA copy and its counters (allocated on the first update);
+ * 0 if *p is invalid.  Not counted, because they depend on the tuning or
+ * the caller: the staging of host-pointer updates (2 * stage_pairs * 8
+ * bytes) and the bins of the binned updates (sd_scratch_bytes). */
 uint64_t sd_device_bytes(const sd_params *p);
 
 /* Create a handle: allocate a zeroed DHLA per direction (the r LAs of 2^k
@@ -232,27 +235,32 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
 
 /* Algorithm 1 for `count` handles at once (batched windows of many links):
  * handle i gets the ns[i] pairs at pairs[i], exactly as sd_update would give
- * it.  When hs[0] uses a binned update (tuning mode 5 or 6), every link whose
- * pairs are device-resident on hs[0]'s device and whose DHLA has hs[0]'s
- * shape (g, r, k, alpha, dirs) is binned with the others: each round takes
- * links round-robin, each contributing up to 2^bin_chunk_log2 pairs, as
- * many as hs[0]'s bin_batch_mib of bins holds at the round's largest share
- * (and at most 4096 slices in all), with one bin launch and one apply
- * launch per round (binned by DHLA slice, with mode 5's knobs), on hs[0]'s
- * stream and with hs[0]'s scratch (ordered after each member's earlier work,
- * and each member's later work after it).  The other links take sd_update.
- * Returns
- * the first error, if any. */
+ * it.  Every link whose pairs are device-resident on hs[0]'s device and whose
+ * DHLA has hs[0]'s shape (g, r, k, alpha, dirs) joins the batch, which runs
+ * on hs[0]'s stream with hs[0]'s scratch (ordered after each member's
+ * earlier work, and each member's later work after it); the other links
+ * take sd_update.
+ *   hs[0] in mode 6: each member in mode 6 runs its plane rounds (of up to
+ *   2^plane_round_log2 pairs of hs[0]'s tuning, with its own tile and unit)
+ *   through hs[0]'s bins, one member after another; members in other modes
+ *   take sd_update.
+ *   hs[0] in mode 5: rounds take members round-robin, each contributing up
+ *   to 2^bin_chunk_log2 pairs, as many as hs[0]'s bin_batch_mib of bins
+ *   holds at the round's largest share (and at most 4096 slices in all),
+ *   with one bin launch and one apply launch per round (binned by DHLA
+ *   slice).
+ * Returns the first error, if any. */
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count);
 
-/* Device bytes of the binned update's scratch that h allocates, with its
- * current tuning, when it updates alone (links <= 1: for mode 6 the round's
- * bins and counters plus the plane-major DHLA copy, which is as large as the
- * DHLA) or drives sd_update_many over `links` members (slice bins, at most
- * about bin_batch_mib MiB); the scratch grows to the largest such need and
- * is kept until sd_destroy.  0 when h does not bin (tuning modes 0-4, or a
- * DHLA of more than 4096 slices in a batch) or h is NULL.  For memory
- * budgets: a handle holds sd_device_bytes plus this. */
+/* Device bytes of the binned update's bins that h allocates, with its
+ * current tuning: mode 6, the bins of one plane round (of
+ * 2^plane_round_log2 pairs), for its own rounds and for every member's
+ * rounds of a batch it drives (the plane copy is in sd_device_bytes); mode
+ * 5, the slice bins of its own chunks (links <= 1) or of batched rounds
+ * over `links` members (at most about bin_batch_mib MiB).  The bins grow to
+ * the largest such need and are kept until sd_destroy.  0 when h does not
+ * bin (tuning modes 0-4, or in mode 5 a DHLA of more than 4096 slices) or h
+ * is NULL.  For memory budgets: a handle holds sd_device_bytes plus this. */
 uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links);
 
 /* Wait for all work queued on the handle's stream. */

@@ -211,6 +211,7 @@ struct sd_handle {
     StatBlock *cb_st_d = nullptr, *cb_st_h = nullptr;
     unsigned long long *cb_hits_d = nullptr, *cb_hits_h = nullptr;
     unsigned long long *cb_base_d = nullptr, *cb_base_h = nullptr;  // tile and candidate offsets
+    FoldJob *fj_d = nullptr, *fj_h = nullptr;  // members' plane folds (fj_h pinned)
     uint32_t cj_cap = 0;
 
     // staged join (tuning restore = 1): all hot lists and the two
@@ -226,15 +227,18 @@ struct sd_handle {
 
     // plane-binned update (mode 6): the plane-major DHLA copy (the handle's
     // DHLA is grid | planes^T; folded into grid before anything reads it)
-    // and the round's bins and counters, allocated on first use
+    // and the per-plane counters, allocated on first use; the bins of its
+    // own rounds (a batch it drives runs every member's rounds through
+    // them), grown on demand
     uint32_t *planes = nullptr;
-    uint64_t planes_words = 0;
-    uint32_t *plane_mem = nullptr;     // bins, then ntot, binoff, fill, unit_start, ctl
-    uint64_t plane_mem_words = 0;
-    PlaneArgs pa{};
+    uint32_t *plane_ctr = nullptr;     // cnt, prev, binoff, cap, unit_start, ctl
+    uint32_t *plane_bins = nullptr;
+    uint64_t plane_bins_words = 0;
+    PlaneArgs pa{};                    // counters and plane copy (bins, tile, unit set per round)
     bool planes_dirty = false;
-    uint64_t plane_layout_pairs = 0;   // round size the device's bin layout was made for (0: none)
-    int plane_layout_view = -2;        // the directions it was made for (-1 both, else one)
+    bool grid_clean = false;           // the DHLA is all zero (reset, then plane updates only)
+    uint64_t plane_prev_pairs = 0;     // pairs of the round whose counts are in prev (0: none)
+    int plane_layout_view = -2;        // its directions (-1 both, else one)
 
     // key partition (sd_partition_pairs): per-part counts and cursors
     unsigned long long *part_d = nullptr;  // [2][1024]
@@ -388,14 +392,49 @@ static void resolve_caps(const sd_params *p, uint64_t *pair_cap, uint64_t *cand_
     *stage = p->stage_pairs ? p->stage_pairs : (dhla_bytes > (64ull << 20) ? (1ull << 24) : (1ull << 22));
 }
 
+}  // extern "C"
+
+// Words of one bit plane (r estimators' bit b), 16-byte aligned.
+static uint32_t plane_words(const Geometry &G) {
+    return (uint32_t)((((uint64_t)G.r << G.k) / 32 + 3) & ~3ull);
+}
+
+// Most shared memory one bit plane may take in k_plane_apply.
+constexpr uint64_t kPlaneSmemMax = 192 * 1024;
+
+static bool plane_fits(const Geometry &G) { return (uint64_t)plane_words(G) * 4 <= kPlaneSmemMax; }
+
+// Bins of a plane round of `round` pairs over G's directions: each plane's
+// bin holds a count (the previous round's, possibly scaled; exact for a
+// counted round) plus an eighth and 32 slots, rounded up to 4, and scaling
+// adds at most one slot per plane; so the total stays below keys + keys/8 +
+// 40 per plane.
+static uint64_t plane_bin_words(const Geometry &G, uint64_t round) {
+    const uint64_t keys = (uint64_t)G.dirs * round;
+    return keys + keys / 8 + 40ull * G.dirs * G.g;
+}
+// Words of a handle's plane state: the plane-major copy and the counters
+// (cnt, prev, cap: nbins each; binoff, unit_start: nbins + 1; ctl: 4).
+constexpr uint64_t kPlaneCtlWords = 4;
+static uint64_t plane_ctr_words(uint32_t nbins) { return 5ull * nbins + 2 + kPlaneCtlWords; }
+static uint64_t plane_state_words(const Geometry &G) {
+    const uint64_t nb = (uint64_t)G.dirs * G.g;
+    return nb * plane_words(G) + plane_ctr_words((uint32_t)nb);
+}
+
+extern "C" {
+
 uint64_t sd_device_bytes(const sd_params *p) {
     if (sd_check_params(p) != SD_OK) return 0;
     uint64_t pc, cc, hc, rc, sp;
     resolve_caps(p, &pc, &cc, &hc, &rc, &sp);
     const uint64_t cells = (uint64_t)p->r << p->k;
     (void)sp;  // the host-pointer staging is allocated on first use, not counted
+    Geometry G;
+    geometry_of(p, &G);
+    const uint64_t planes = plane_fits(G) ? plane_state_words(G) * 4 : 0;  // default mode 6
     return (uint64_t)p->dirs * (sd_grid_words(p) * 4 + cells / 8 + 2 * ((uint64_t)4 << p->k) + cc * 4 + 2 * hc * 8) +
-           sizeof(StatBlock);
+           sizeof(StatBlock) + planes;
 }
 
 static void release(sd_handle *h) {
@@ -410,7 +449,8 @@ static void release(sd_handle *h) {
     cudaFree(h->hits_tmp);
     cudaFree(h->bin_mem);
     cudaFree(h->planes);
-    cudaFree(h->plane_mem);
+    cudaFree(h->plane_ctr);
+    cudaFree(h->plane_bins);
     cudaFree(h->part_d);
     cudaFreeHost(h->part_h);
     cudaFree(h->he_all);
@@ -423,6 +463,8 @@ static void release(sd_handle *h) {
     cudaFreeHost(h->cb_hits_h);
     cudaFree(h->cb_base_d);
     cudaFreeHost(h->cb_base_h);
+    cudaFree(h->fj_d);
+    cudaFreeHost(h->fj_h);
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     cudaFreeHost(h->big_h);
@@ -440,16 +482,6 @@ static void release(sd_handle *h) {
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
-
-// Words of one bit plane (r estimators' bit b), 16-byte aligned.
-static uint32_t plane_words(const Geometry &G) {
-    return (uint32_t)((((uint64_t)G.r << G.k) / 32 + 3) & ~3ull);
-}
-
-// Most shared memory one bit plane may take in k_plane_apply.
-constexpr uint64_t kPlaneSmemMax = 192 * 1024;
-
-static bool plane_fits(const Geometry &G) { return (uint64_t)plane_words(G) * 4 <= kPlaneSmemMax; }
 
 static int create_impl(const sd_params *p, sd_handle *h) {
     h->p = *p;
@@ -506,6 +538,7 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     SD_CK(h, cudaMallocHost(&h->hits_h, (uint64_t)2 * kSortSmall * 8));
     SD_CK(h, launch_reset(h->grid, words, h->st_d, h->num_sms, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
+    h->grid_clean = true;
     return SD_OK;
 }
 
@@ -598,60 +631,86 @@ static int ensure_bins(sd_handle *h, bool *ok) {
     return ensure_bin_mem(h, B);
 }
 
-// Layout of the plane-binned update for the current tuning: bins for one
-// round of 2^plane_round_log2 pairs (dirs keys per pair; each plane's bin
-// holds its count of the previous round plus an eighth and 32 slots, rounded
-// up to 4), the counters, and the plane-major DHLA copy.
-constexpr uint64_t kPlaneCounterWords = 4;  // words after the 4 nbins + 2 per-plane arrays
-static uint64_t plane_bin_words(const Geometry &G, uint64_t round) {
-    const uint64_t keys = (uint64_t)G.dirs * round;
-    return keys + keys / 8 + 40ull * G.dirs * G.g;
-}
-static void plane_layout(const sd_handle *h, PlaneArgs *P, uint64_t *mem_words, uint64_t *plane_copy_words) {
-    const Geometry &G = h->G;
-    std::memset(P, 0, sizeof *P);
-    P->nbins = G.dirs * G.g;
-    P->ps = plane_words(G);
-    P->unit = 1u << h->T.plane_unit_log2;
-    P->tile_pairs = h->T.plane_tile_pairs;
-    const uint64_t bins = plane_bin_words(G, 1ull << h->T.plane_round_log2);
-    *mem_words = bins + 4ull * P->nbins + 2 + kPlaneCounterWords;
-    *plane_copy_words = (uint64_t)P->nbins * P->ps;
-}
+// A scaled layout needs a previous round of at least this many pairs per
+// plane of a direction (64 keys per plane on average), else the round is
+// counted exactly.
+constexpr uint64_t kPlaneScaleMinPerPlane = 64;
 
-static int ensure_plane_mem(sd_handle *h) {
-    PlaneArgs P;
-    uint64_t words = 0, pw = 0;
-    plane_layout(h, &P, &words, &pw);
+// The plane copy (zero) and the counters (zero: no layout yet), once.
+static int ensure_plane_state(sd_handle *h) {
     if (!h->planes) {
+        const uint32_t nb = h->G.dirs * h->G.g;
+        const uint64_t pw = (uint64_t)nb * plane_words(h->G), cw = plane_ctr_words(nb);
         SD_CK(h, cudaMalloc(&h->planes, pw * 4));
+        SD_CK(h, cudaMalloc(&h->plane_ctr, cw * 4));
         SD_CK(h, cudaMemsetAsync(h->planes, 0, pw * 4, h->stream));
-        h->planes_words = pw;
-    }
-    if (words > h->plane_mem_words) {
-        SD_CK(h, cudaStreamSynchronize(h->stream));
-        cudaFree(h->plane_mem);
-        h->plane_mem = nullptr;
-        h->plane_mem_words = 0;
-        SD_CK(h, cudaMalloc(&h->plane_mem, words * 4));
-        h->plane_mem_words = words;
-    }
-    const uint64_t cwords = 4ull * P.nbins + 2 + kPlaneCounterWords;
-    uint32_t *c = h->plane_mem + (words - cwords);
-    P.bins = h->plane_mem;
-    P.cnt = c;
-    P.binoff = c + P.nbins;
-    P.cap = c + 2 * P.nbins + 1;
-    P.unit_start = c + 3 * P.nbins + 1;
-    P.ctl = c + 4 * P.nbins + 2;
-    P.planes = h->planes;
-    if (P.cnt != h->pa.cnt || P.nbins != h->pa.nbins) {
-        // new counters start at zero, with no bin layout yet
-        SD_CK(h, cudaMemsetAsync(c, 0, cwords * 4, h->stream));
-        h->plane_layout_pairs = 0;
+        SD_CK(h, cudaMemsetAsync(h->plane_ctr, 0, cw * 4, h->stream));
+        PlaneArgs &P = h->pa;
+        std::memset(&P, 0, sizeof P);
+        P.nbins = nb;
+        P.ps = plane_words(h->G);
+        P.planes = h->planes;
+        uint32_t *c = h->plane_ctr;
+        P.cnt = c;
+        P.prev = c + nb;
+        P.cap = c + 2 * nb;
+        P.binoff = c + 3 * nb;
+        P.unit_start = c + 4 * nb + 1;
+        P.ctl = c + 5 * nb + 2;
+        h->plane_prev_pairs = 0;
         h->plane_layout_view = -2;
     }
-    h->pa = P;
+    return SD_OK;
+}
+
+// owner's bins, at least `words` of them (grown once the rounds that read
+// the old ones are done)
+static int ensure_plane_bins(sd_handle *owner, uint64_t words) {
+    if (words <= owner->plane_bins_words) return SD_OK;
+    SD_CK(owner, cudaStreamSynchronize(owner->stream));
+    cudaFree(owner->plane_bins);
+    owner->plane_bins = nullptr;
+    owner->plane_bins_words = 0;
+    SD_CK(owner, cudaMalloc(&owner->plane_bins, words * 4));
+    owner->plane_bins_words = words;
+    return SD_OK;
+}
+
+// Algorithm 1 binned by plane over n device pairs of h, in rounds of at
+// most `round` pairs through `bins` (bin_words of them, at least the bins
+// of one round), on stream s; failures are reported on `rep`.  A round
+// reuses the layout the previous round of the same directions left when it
+// is no larger than that round and that layout fits the bins; a round of
+// another size is laid out from the previous counts scaled to its size when
+// that round had enough pairs; any other round is counted exactly.
+static int plane_rounds(sd_handle *h, const uint32_t *pairs, uint64_t n, int dir, uint32_t *bins,
+                        uint64_t bin_words, uint64_t round, cudaStream_t s, sd_handle *rep) {
+    Geometry G = h->G;
+    PlaneArgs P = h->pa;
+    P.bins = bins;
+    P.unit = 1u << h->T.plane_unit_log2;
+    P.tile_pairs = h->T.plane_tile_pairs;
+    if (dir >= 0) {  // one direction's hash constants, counters and planes
+        G.dirs = 1;
+        G.h[0] = h->G.h[dir];
+        P.nbins = h->G.g;
+        P.planes += (uint64_t)dir * h->G.g * P.ps;
+    }
+    if (plane_bin_words(G, std::min(round, n)) > bin_words)
+        return rep->fail(SD_ERR_ARG, "plane update: %llu bin words for rounds of %llu pairs",
+                         (unsigned long long)bin_words, (unsigned long long)round);
+    for (uint64_t off = 0; off < n; off += round) {
+        const uint64_t m = std::min(round, n - off);
+        const uint64_t prev = h->plane_layout_view == dir ? h->plane_prev_pairs : 0;
+        PlaneLayout L = kLayoutCount;
+        if (prev && m <= prev && plane_bin_words(G, prev) <= bin_words) L = kLayoutReuse;
+        else if (prev >= kPlaneScaleMinPerPlane * G.g) L = kLayoutScale;
+        SD_CK(rep, launch_plane_round(pairs + 2 * off, m, G, P, h->num_sms, s, L, prev));
+        launched(L == kLayoutReuse ? 2 : 3);
+        h->plane_prev_pairs = m;
+        h->plane_layout_view = dir;
+    }
+    h->planes_dirty = true;
     return SD_OK;
 }
 
@@ -659,9 +718,11 @@ static int ensure_plane_mem(sd_handle *h) {
 // plane-binned mode are pending.
 static int fold_planes(sd_handle *h) {
     if (!h->planes_dirty) return SD_OK;
-    SD_CK(h, launch_plane_fold(h->grid, h->planes, h->G, h->pa.ps, h->num_sms, h->stream));
+    const FoldJob job{h->grid, h->planes, h->grid_clean ? 1u : 0u, 0u};
+    SD_CK(h, launch_plane_fold(job, nullptr, 1, h->G, h->pa.ps, h->num_sms, h->stream));
     launched(1);
     h->planes_dirty = false;
+    h->grid_clean = false;
     return SD_OK;
 }
 
@@ -679,27 +740,14 @@ static int update_device(sd_handle *h, const uint32_t *pairs, uint64_t n, int di
         grid += (uint64_t)dir * h->G.dir_words;
     }
     if (h->T.mode == 6) {
-        const int rc = ensure_plane_mem(h);
+        int rc = ensure_plane_state(h);
         if (rc != SD_OK) return rc;
-        PlaneArgs P = h->pa;
-        if (dir >= 0) {
-            P.nbins = h->G.g;
-            P.planes += (uint64_t)dir * h->G.g * P.ps;
-        }
         const uint64_t round = 1ull << h->T.plane_round_log2;
-        for (uint64_t off = 0; off < n; off += round) {
-            const uint64_t m = std::min(round, n - off);
-            // the bins of a round are laid out from the previous round of the
-            // same directions, when it was at least as large; else counted
-            const bool count = m > h->plane_layout_pairs || dir != h->plane_layout_view;
-            SD_CK(h, launch_plane_round(pairs + 2 * off, m, G, P, h->num_sms, h->stream, count));
-            launched(count ? 3 : 2);
-            h->plane_layout_pairs = m;
-            h->plane_layout_view = dir;
-        }
-        h->planes_dirty = true;
-        return SD_OK;
+        rc = ensure_plane_bins(h, plane_bin_words(h->G, round));
+        if (rc != SD_OK) return rc;
+        return plane_rounds(h, pairs, n, dir, h->plane_bins, h->plane_bins_words, round, h->stream, h);
     }
+    h->grid_clean = false;  // the other modes set bits in the DHLA itself
     if (h->T.mode == 5) {
         bool ok = false;
         const int rc = ensure_bins(h, &ok);
@@ -842,12 +890,9 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     if (!h) return 0;
     BinArgs B;
     uint64_t words = 0;
-    if (h->T.mode == 6 && links <= 1) {
-        PlaneArgs P;
-        uint64_t pw = 0;
-        plane_layout(h, &P, &words, &pw);
-        return (words + pw) * 4;
-    }
+    // plane mode: the bins of one round, for the handle's own rounds and for
+    // every member's rounds of a batch it drives
+    if (h->T.mode == 6) return plane_bin_words(h->G, 1ull << h->T.plane_round_log2) * 4;
     if ((h->T.mode != 5 && h->T.mode != 6) || !bin_layout(h, &B, &words)) return 0;
     if (links <= 1) return words * 4;
     BatchLayout L;
@@ -860,6 +905,69 @@ uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     return std::max<uint64_t>(words * 4, std::min<uint64_t>(full, std::max<uint64_t>(L.bin_bytes, (uint64_t)L.S_link * L.cap_link * 4)) + (S + 4) * 4);
 }
 
+// Whether member h (pairs p) joins a batch driven by d: device-resident
+// pairs on d's device, d's DHLA shape, and not already in the batch.
+static bool batch_member(const sd_handle *d, const sd_handle *h, const uint32_t *p, uint64_t n,
+                         sd_handle *const *hs, const std::vector<uint32_t> &batch) {
+    const sd_params &P = d->p;
+    bool ok = n > 0 && p && !((uintptr_t)p & 3u) && h->p.g == P.g && h->p.r == P.r && h->p.k == P.k &&
+              h->p.alpha == P.alpha && h->p.dirs == P.dirs && h->p.device == P.device;
+    for (uint32_t q : batch)
+        if (hs[q] == h) ok = false;
+    if (ok) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        } else {
+            ok = attr.type == cudaMemoryTypeDevice && attr.device == P.device;
+        }
+    }
+    return ok;
+}
+
+// sd_update_many with d in mode 6: each member in mode 6 runs its plane
+// rounds through d's bins on d's stream, one member after another.
+static int update_many_planes(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns,
+                              uint32_t count) {
+    sd_handle *d = hs[0];
+    std::vector<uint32_t> batch;
+    for (uint32_t i = 0; i < count; i++) {
+        if (hs[i]->T.mode == 6 && batch_member(d, hs[i], pairs[i], ns[i], hs, batch)) {
+            batch.push_back(i);
+        } else {
+            const int rc = sd_update(hs[i], pairs[i], ns[i]);
+            if (rc != SD_OK) return rc;
+        }
+    }
+    if (batch.empty()) return SD_OK;
+    const uint64_t round = 1ull << d->T.plane_round_log2;
+    int rc = ensure_plane_bins(d, plane_bin_words(d->G, round));
+    if (rc != SD_OK) return rc;
+    // each member's state (zeroed on its own stream when new) and earlier
+    // work come first
+    for (uint32_t q : batch) {
+        sd_handle *h = hs[q];
+        if ((rc = ensure_plane_state(h)) != SD_OK) return rc;
+        if (h == d || h->stream == d->stream) continue;
+        SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
+        SD_CK(d, cudaStreamWaitEvent(d->stream, h->ev_batch, 0));
+    }
+    for (uint32_t q : batch) {
+        rc = plane_rounds(hs[q], pairs[q], ns[q], -1, d->plane_bins, d->plane_bins_words, round, d->stream, d);
+        if (rc != SD_OK) return rc;
+    }
+    // later work on each member waits for the batch
+    SD_CK(d, cudaEventRecord(d->ev_batch, d->stream));
+    for (uint32_t q : batch) {
+        sd_handle *h = hs[q];
+        h->n_pairs += ns[q];
+        if (h == d || h->stream == d->stream) continue;
+        SD_CK(h, cudaStreamWaitEvent(h->stream, d->ev_batch, 0));
+    }
+    return SD_OK;
+}
+
 int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns, uint32_t count) {
     NvtxRange nvtx("sd_update_many");
     if (!count) return SD_OK;
@@ -868,6 +976,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
         if (!hs[i]) return SD_ERR_ARG;
     sd_handle *d = hs[0];
     DeviceGuard dg(d->p.device);
+    if (d->T.mode == 6) return update_many_planes(hs, pairs, ns, count);
     const sd_params &P = d->p;
     BatchLayout BL{};
     const bool binnable = batch_layout(d, &BL);
@@ -879,22 +988,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
     // the same DHLA shape, each handle once; the others update on their own
     std::vector<uint32_t> batch;
     for (uint32_t i = 0; i < count; i++) {
-        const sd_handle *h = hs[i];
-        bool ok = binnable && ns[i] > 0 && pairs[i] && !((uintptr_t)pairs[i] & 3u) && h->p.g == P.g &&
-                  h->p.r == P.r && h->p.k == P.k && h->p.alpha == P.alpha && h->p.dirs == P.dirs &&
-                  h->p.device == P.device;
-        for (uint32_t q : batch)
-            if (hs[q] == h) ok = false;
-        if (ok) {
-            cudaPointerAttributes attr;
-            if (cudaPointerGetAttributes(&attr, pairs[i]) != cudaSuccess) {
-                cudaGetLastError();
-                ok = false;
-            } else {
-                ok = attr.type == cudaMemoryTypeDevice && attr.device == P.device;
-            }
-        }
-        if (ok) {
+        if (binnable && batch_member(d, hs[i], pairs[i], ns[i], hs, batch)) {
             batch.push_back(i);
         } else {
             const int rc = sd_update(hs[i], pairs[i], ns[i]);
@@ -961,6 +1055,7 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
             const sd_handle *h = hs[i];
             const uint64_t take = std::min(budget, ns[i] - done[mem[m]]);
             LinkDesc &L = tab[m];
+            hs[i]->grid_clean = false;
             L.pairs = pairs[i] + 2 * done[mem[m]];
             L.n = take;
             L.grid = h->grid;
@@ -1215,6 +1310,7 @@ static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
     if (reset) {
         SD_CK(h, launch_reset(h->grid, (uint64_t)G.dirs * G.dir_words, h->st_d, h->num_sms, h->stream));
         launched(1);
+        h->grid_clean = !h->planes_dirty;
     }
 
     uint32_t flags = c.flags;
@@ -1311,6 +1407,9 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         cudaFreeHost(d->cb_hits_h);
         cudaFree(d->cb_base_d);
         cudaFreeHost(d->cb_base_h);
+        cudaFree(d->fj_d);
+        cudaFreeHost(d->fj_h);
+        d->fj_d = d->fj_h = nullptr;
         d->cj_d = d->cj_h = nullptr;
         d->cb_st_d = d->cb_st_h = nullptr;
         d->cb_hits_d = d->cb_hits_h = nullptr;
@@ -1325,6 +1424,8 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         // tile offsets (device + host) and candidate offsets (device), 2 count + 1 each
         SD_CK(d, cudaMalloc(&d->cb_base_d, (uint64_t)2 * (2 * count + 1) * 8));
         SD_CK(d, cudaMallocHost(&d->cb_base_h, (uint64_t)(2 * count + 1) * 8));
+        SD_CK(d, cudaMalloc(&d->fj_d, count * sizeof(FoldJob)));
+        SD_CK(d, cudaMallocHost(&d->fj_h, count * sizeof(FoldJob)));
         d->cj_cap = count;
     }
     // every member's queued work comes first, on the driver's stream
@@ -1335,15 +1436,23 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         SD_CK(d, cudaStreamWaitEvent(s, h->ev_batch, 0));
     }
     // phase A: row statistics and HE(0), HE(1) of every window (pending
-    // plane-binned updates folded into each DHLA first, on the driver's
-    // stream, which is ordered after every member's work)
+    // plane-binned updates folded into each DHLA first, all in one launch
+    // on the driver's stream, which is ordered after every member's work)
+    uint32_t nfold = 0;
     for (uint32_t i = 0; i < count; i++) {
         sd_handle *h = hs[i];
-        if (h->planes_dirty) {
-            SD_CK(d, launch_plane_fold(h->grid, h->planes, h->G, h->pa.ps, d->num_sms, s));
-            launched(1);
-            h->planes_dirty = false;
-        }
+        if (!h->planes_dirty) continue;
+        d->fj_h[nfold++] = FoldJob{h->grid, h->planes, h->grid_clean ? 1u : 0u, 0u};
+        h->planes_dirty = false;
+        h->grid_clean = false;
+    }
+    if (nfold) {
+        SD_CK(d, cudaMemcpyAsync(d->fj_d, d->fj_h, nfold * sizeof(FoldJob), cudaMemcpyHostToDevice, s));
+        SD_CK(d, launch_plane_fold(d->fj_h[0], d->fj_d, nfold, G, plane_words(G), d->num_sms, s));
+        launched(1);
+    }
+    for (uint32_t i = 0; i < count; i++) {
+        sd_handle *h = hs[i];
         std::memset(&outs[i], 0, sizeof outs[i]);
         std::memset(&h->cs, 0, sizeof h->cs);
         h->report.clear();
@@ -1415,6 +1524,7 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         if (rcs[i] == SD_OK) rcs[i] = close_phase_d(hs[i], &outs[i], false);
     SD_CK(d, launch_reset_many(d->cj_d, count, G, d->num_sms, s));
     launched(1);
+    for (uint32_t i = 0; i < count; i++) hs[i]->grid_clean = !hs[i]->planes_dirty;
     tr.mark(3);
     // each member's later work waits for the batch
     SD_CK(d, cudaEventRecord(d->ev_batch, s));
@@ -1540,6 +1650,7 @@ int sd_set_grid(sd_handle *h, uint32_t dir, const uint32_t *host_src) {
     DeviceGuard dg(h->p.device);
     const int frc = fold_planes(h);  // pending bits of the other direction stay
     if (frc != SD_OK) return frc;
+    h->grid_clean = false;
     SD_CK(h, cudaMemcpyAsync(h->grid + (uint64_t)dir * h->G.dir_words, host_src, h->G.dir_words * 4,
                              cudaMemcpyHostToDevice, h->stream));
     SD_CK(h, cudaStreamSynchronize(h->stream));
@@ -1582,6 +1693,7 @@ int sd_merge(sd_handle *dst, sd_handle *src) {
     int frc = fold_planes(src);
     if (frc == SD_OK) frc = fold_planes(dst);
     if (frc != SD_OK) return frc;
+    dst->grid_clean = false;
     cudaEvent_t ev;
     SD_CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     cudaError_t e = cudaEventRecord(ev, src->stream);
@@ -1630,6 +1742,7 @@ int sd_or_grid(sd_handle *h, const uint32_t *src) {
     DeviceGuard dg(h->p.device);
     const int frc = fold_planes(h);
     if (frc != SD_OK) return frc;
+    h->grid_clean = false;
     SD_CK(h, launch_merge(h->grid, src, (uint64_t)h->G.dirs * h->G.dir_words, h->num_sms, h->stream));
     launched(1);
     return SD_OK;

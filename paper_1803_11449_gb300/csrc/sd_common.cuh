@@ -56,6 +56,7 @@ struct Tuning {
 struct PlaneArgs {
     uint32_t *bins;        // the round's keys, plane by plane (each bin starts on 4 entries)
     uint32_t *cnt;         // [nbins] keys of each plane this round (zero between rounds)
+    uint32_t *prev;        // [nbins] keys of each plane in the previous round
     uint32_t *binoff;      // [nbins + 1] first slot of each plane's bin
     uint32_t *cap;         // [nbins] slots of each plane's bin; keys beyond them are set directly
     uint32_t *unit_start;  // [nbins + 1] first apply unit of each plane
@@ -242,8 +243,12 @@ size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);
 size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins);
 // one round of the plane-binned update over n pairs: an exact count first
 // when `count` (no usable layout from an earlier round), then bin and apply
+// How a plane round gets its bin layout: the one the previous round left
+// (its counts plus slack), that round's counts scaled by n / prev_pairs
+// (plus slack), or an exact count of this round's keys.
+enum PlaneLayout { kLayoutReuse = 0, kLayoutScale = 1, kLayoutCount = 2 };
 cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
-                               cudaStream_t s, bool count);
+                               cudaStream_t s, PlaneLayout layout, uint64_t prev_pairs);
 // dst = OR of `count` arrays of `words` words at src (words a multiple of 4)
 cudaError_t launch_or_words(uint32_t *dst, const uint32_t *src, uint64_t words, uint32_t count, int num_sms,
                             cudaStream_t s);
@@ -252,9 +257,17 @@ cudaError_t launch_or_words(uint32_t *dst, const uint32_t *src, uint64_t words, 
 cudaError_t launch_partition(const uint32_t *pairs, uint64_t n, uint32_t dir, uint32_t parts,
                              unsigned long long *counts, unsigned long long *cursor, uint32_t *out, int num_sms,
                              cudaStream_t s, bool scatter);
-// grid |= planes^T, planes = 0
-cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
-                              cudaStream_t s);
+// One handle's fold: grid |= planes^T (grid = planes^T where `clean`: the
+// DHLA is all zero), planes = 0.
+struct FoldJob {
+    uint32_t *grid;
+    uint32_t *planes;
+    uint32_t clean;
+    uint32_t pad;
+};
+// `one`'s fold, or (jobs != nullptr) the folds of njobs device-resident jobs
+cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
+                              int num_sms, cudaStream_t s);
 cudaError_t launch_binned_chunk(const uint32_t *pairs, uint64_t n, uint32_t *grid, const Geometry &G,
                                 const BinArgs &B, int num_sms, cudaStream_t s);
 cudaError_t launch_binned_links(const LinkDesc *links_dev, uint32_t nlinks, uint64_t ntiles_all,

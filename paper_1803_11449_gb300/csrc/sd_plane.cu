@@ -18,8 +18,11 @@
 //                  slack; keys beyond a bin's capacity (traffic that shifted
 //                  between rounds) set their bits directly with atomic ORs.
 //                  The last block cuts each plane's bin into apply units.
-//   k_plane_count  for a round without a usable layout (the first one, or
-//                  one larger than the round the layout came from): the
+//   k_plane_layout for a round of another size than the previous one (of
+//                  enough pairs to go by): that round's per-plane counts
+//                  scaled to this round's size, plus slack.
+//   k_plane_count  for a round with no usable history (the first one, one
+//                  over other directions, or one after a small round): the
 //                  exact keys of every plane, and a layout without slack.
 //   k_plane_apply  one unit (a plane and a range of its bin) per block step:
 //                  the plane in shared memory, DH_0 and Eq. 2 of every key,
@@ -104,19 +107,23 @@ __device__ __forceinline__ void block_scan(uint32_t N, Get get, Put put, uint32_
     __syncthreads();
 }
 
+// Capacity of a bin for an expected count c: c plus an eighth and 32 slots
+// of slack when `slack`, rounded up to 4 entries.
+__device__ __forceinline__ uint32_t bin_cap(uint32_t c, bool slack) {
+    return (c + (slack ? c / 8u + 32u : 0u) + 3u) & ~3u;
+}
+
 // One block: the bins of the next round from this round's per-plane counts
-// (cnt, then cleared): capacity = count rounded up to 4, plus an eighth and
-// 32 slots of slack when `slack`; bins back to back.  The caller has seen
-// every count (last-block pattern).
+// (cnt, then kept in prev and cleared), bins back to back.  The caller has
+// seen every count (last-block pattern).
 __device__ __forceinline__ void write_layout(const PlaneArgs &P, bool slack, uint32_t *s_warp) {
     const uint32_t NB = P.nbins;
-    auto cap_of = [&](uint32_t i) {
-        const uint32_t c = __ldcg(&P.cnt[i]);
-        return (c + (slack ? c / 8u + 32u : 0u) + 3u) & ~3u;
-    };
+    auto cap_of = [&](uint32_t i) { return bin_cap(__ldcg(&P.cnt[i]), slack); };
     block_scan(NB, cap_of, [&](uint32_t i, uint32_t v) { P.binoff[i] = v; }, s_warp);
     for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) {
-        P.cap[b] = cap_of(b);
+        const uint32_t c = __ldcg(&P.cnt[b]);
+        P.cap[b] = bin_cap(c, slack);
+        P.prev[b] = c;
         P.cnt[b] = 0;
     }
 }
@@ -200,6 +207,20 @@ k_plane_count(const uint32_t *__restrict__ pairs, uint64_t n, Geometry G, PlaneA
     // every count is in cnt: bins of exactly this round's sizes
     write_layout(P, false, s_warp);
     if (threadIdx.x == 0) P.ctl[0] = 0;
+}
+
+// ----------------------------------------------------------------- layout
+// One block: bins for a round of `num` pairs from the per-plane counts of a
+// previous round of `den` pairs (prev), each count scaled by num / den
+// (rounded up) and given slack.  Their total stays within the bins of a
+// round of num pairs: sum ceil(prev num / den) <= keys + nbins.
+__global__ void __launch_bounds__(1024) k_plane_layout(PlaneArgs P, uint64_t num, uint64_t den) {
+    __shared__ uint32_t s_warp[32];
+    auto cap_of = [&](uint32_t i) {
+        return bin_cap((uint32_t)(((uint64_t)P.prev[i] * num + den - 1) / den), true);
+    };
+    block_scan(P.nbins, cap_of, [&](uint32_t i, uint32_t v) { P.binoff[i] = v; }, s_warp);
+    for (uint32_t b = threadIdx.x; b < P.nbins; b += blockDim.x) P.cap[b] = cap_of(b);
 }
 
 // -------------------------------------------------------------------- bin
@@ -503,8 +524,12 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
     return x;
 }
 
-__global__ void __launch_bounds__(kFoldWarps * 32)
-k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometry G, uint32_t ps) {
+// Folds of several handles of one shape run as one launch (the batched
+// close): the items of job j follow those of job j - 1.  A job whose DHLA
+// is known to be all zero (every update since its last reset went through
+// the planes) stores the transposed words without reading the DHLA.
+__global__ void __launch_bounds__(kFoldWarps * 32, 3)
+k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geometry G, uint32_t ps) {
     extern __shared__ uint32_t stg[];  // [warps][256 estimators][kFoldTC + 1]
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     constexpr uint32_t SP = kFoldTC + 1;
@@ -515,9 +540,15 @@ k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometr
     const uint32_t rw = (1u << G.k) >> 5;      // plane words per row
     const uint32_t wq = rw < 8u ? rw : 8u;     // plane words per warp item
     const uint32_t groups = rw / wq;
-    const uint64_t items = (uint64_t)G.dirs * G.r * groups * nchunks;
+    const uint64_t per_job = (uint64_t)G.dirs * G.r * groups * nchunks;
+    const uint64_t items = per_job * njobs;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wid; it < items; it += nwarps) {
+    for (uint64_t it0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wid; it0 < items; it0 += nwarps) {
+        const uint32_t jn = (uint32_t)(it0 / per_job);
+        const FoldJob job = jobs ? jobs[jn] : one;
+        uint32_t *__restrict__ grid = job.grid;
+        uint32_t *__restrict__ planes = job.planes;
+        const uint64_t it = it0 - (uint64_t)jn * per_job;
         const uint32_t chunk = (uint32_t)(it % nchunks);
         const uint64_t rest = it / nchunks;
         const uint32_t grp = (uint32_t)(rest % groups);
@@ -571,7 +602,16 @@ k_plane_fold(uint32_t *__restrict__ grid, uint32_t *__restrict__ planes, Geometr
         // step, four steps' loads issued before their stores
         const uint32_t lt = tc == 8 ? 3u : tc == 4 ? 2u : tc == 2 ? 1u : 0u;  // log2 tc
         const uint32_t quads = (32u * wq * tc) / 4u;
-        if (tc >= 4) {
+        if (tc >= 4 && job.clean) {
+            // the DHLA words are zero: store the nonzero ones
+            for (uint32_t q = lane; q < quads; q += 32u) {
+                const uint32_t w = 4u * q, e = w >> lt, tt = w & (tc - 1u);
+                const uint32_t *m = my + e * SP + tt;
+                const uint4 v = make_uint4(m[0], m[1], m[2], m[3]);
+                if (v.x | v.y | v.z | v.w)
+                    *reinterpret_cast<uint4 *>(row + (uint64_t)(32u * w0 + e) * wpc + tc0 + tt) = v;
+            }
+        } else if (tc >= 4) {
             for (uint32_t q0 = lane; q0 < quads; q0 += 128u) {
                 uint4 cur[4];
                 uint4 *dst[4];
@@ -665,9 +705,14 @@ static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, uin
 }
 
 cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry &G, const PlaneArgs &P, int num_sms,
-                               cudaStream_t s, bool count) {
+                               cudaStream_t s, PlaneLayout layout, uint64_t prev_pairs) {
     if (n == 0) return cudaSuccess;
-    if (count) {
+    if (layout == kLayoutScale) {
+        if (prev_pairs == 0) return cudaErrorInvalidValue;
+        k_plane_layout<<<1, 1024, 0, s>>>(P, n, prev_pairs);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else if (layout == kLayoutCount) {
         auto kern = G.dirs == 2 ? k_plane_count<2> : k_plane_count<1>;
         const size_t smem = (size_t)P.nbins * 4;
         int per_sm = 0;
@@ -693,18 +738,19 @@ cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry
     }
 }
 
-cudaError_t launch_plane_fold(uint32_t *grid, uint32_t *planes, const Geometry &G, uint32_t ps, int num_sms,
-                              cudaStream_t s) {
+cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
+                              int num_sms, cudaStream_t s) {
+    if (njobs == 0) return cudaSuccess;
     const size_t smem = (size_t)kFoldWarps * 256 * (kFoldTC + 1) * 4;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldWarps * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t rw = ((uint64_t)1 << G.k) >> 5;
     const uint64_t tc = G.wpc < kFoldTC ? G.wpc : kFoldTC;
-    const uint64_t items = (uint64_t)G.dirs * G.r * (rw / (rw < 8 ? rw : 8)) * (G.wpc / tc);
+    const uint64_t items = (uint64_t)G.dirs * G.r * (rw / (rw < 8 ? rw : 8)) * (G.wpc / tc) * njobs;
     uint64_t blocks = (uint64_t)num_sms * per_sm;
     if ((items + kFoldWarps - 1) / kFoldWarps < blocks) blocks = (items + kFoldWarps - 1) / kFoldWarps;
-    k_plane_fold<<<(unsigned)blocks, kFoldWarps * 32, smem, s>>>(grid, planes, G, ps);
+    k_plane_fold<<<(unsigned)blocks, kFoldWarps * 32, smem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps);
     return cudaGetLastError();
 }
 

@@ -68,13 +68,16 @@ class _Link:
 class Server:
     """Serve links with per-link sketches of one shape (`workload`, a
     traffic.Workload or a dict of its sketch parameters).  hbm_budget is in
-    bytes; bin_chunk_log2 sets the most pairs a link gives one binned round,
-    bin_bytes the bins of a round (default: half the budget): a round takes
-    as many links as its bins hold at their actual shares."""
+    bytes; bin_chunk_log2 sets the most pairs a link gives one binned round.
+    The update is the library's default for the shape (mode 6, binned by
+    bit plane, where one plane fits; `mode=5` asks for the slice binning):
+    in mode 6 each link's rounds run in turn through the driver's bins of
+    one round; in mode 5 a round takes as many links as bin_bytes of bins
+    (default: half the budget) hold at their actual shares."""
 
     def __init__(self, workload, window_pairs: int, hbm_budget: int, device: int = 0,
                  bin_chunk_log2: int = 22, bin_bytes: int | None = None, cand_cap: int = 1 << 18,
-                 stream=None):
+                 stream=None, mode: int | None = None):
         import torch
         self.torch = torch
         self.workload = workload
@@ -96,8 +99,13 @@ class Server:
         self._closing = collections.deque()    # (future, link ids) in submission order
         self.bin_bytes = int(bin_bytes) if bin_bytes is not None else self.budget // 2
         self.driver = sd.sd_create(self._params(0, self.stream, cand_cap=1024))
-        sd.sd_set_tuning(self.driver, mode=5, bin_chunk_log2=bin_chunk_log2,
-                         bin_batch_mib=max(1, self.bin_bytes >> 20))
+        self.mode = sd.sd_get_tuning(self.driver).mode if mode is None else int(mode)
+        if self.mode not in (5, 6):
+            sd.sd_destroy(self.driver)
+            self.driver = None
+            self._closer.shutdown()
+            raise ValueError("the engine's batched update is binned: mode 5 or 6")
+        self._tune(self.driver, bin_batch_mib=max(1, self.bin_bytes >> 20))
         self.fixed = (sd.sd_device_bytes(self._params(0, self.stream, cand_cap=1024)) +
                       sd.sd_scratch_bytes(self.driver, 1 << 20))
         if self.fixed > self.budget:
@@ -116,6 +124,12 @@ class Server:
         return False
 
     # ---------------------------------------------------------- admission
+    def _tune(self, h, **extra):
+        if self.mode == 6:
+            sd.sd_set_tuning(h, mode=6, plane_round_log2=self.bin_chunk_log2)
+        else:
+            sd.sd_set_tuning(h, mode=5, bin_chunk_log2=self.bin_chunk_log2, **extra)
+
     def _params(self, seed, stream, cand_cap=None):
         return sd.params_for(self.workload, seed, device=self.device, cand_cap=cand_cap or self.cand_cap,
                              cuda_stream=stream.cuda_stream)
@@ -130,7 +144,7 @@ class Server:
         L = self.links[lid]
         L.stream = self.torch.cuda.Stream(device=self.device)
         L.h = sd.sd_create(self._params(L.seed, L.stream))
-        sd.sd_set_tuning(L.h, mode=5, bin_chunk_log2=self.bin_chunk_log2)
+        self._tune(L.h)
         self.admitted[lid] = L
         self.used += self.link_bytes()
 

@@ -42,7 +42,9 @@ def _same_report(rep, ref, dirs):
 
 
 @pytest.mark.parametrize("tuning", [dict(mode=5), dict(mode=5, bin_chunk_log2=17), dict(mode=1),
-                                    dict(mode=5, bin_batch_mib=1), dict(mode=5, bin_chunk_log2=14, bin_batch_mib=4)])
+                                    dict(mode=5, bin_batch_mib=1), dict(mode=5, bin_chunk_log2=14, bin_batch_mib=4),
+                                    dict(mode=6), dict(mode=6, plane_round_log2=14),
+                                    dict(mode=6, plane_round_log2=16, plane_tile_pairs=1024)])
 def test_batched_links_equal_each_link_alone(sd, O, tuning):
     """Seven links of uneven sizes (one of them much larger than a round's
     share), each with its own traffic and its own hash seed."""
@@ -61,6 +63,57 @@ def test_batched_links_equal_each_link_alone(sd, O, tuning):
         reps = sd.sd_close_many(hs)
     finally:
         for h in hs:
+            sd.sd_destroy(h)
+    for win, s, g, rep in zip(wins, seeds, grids, reps):
+        og, ref = _oracle(O, w, win.pairs, s)
+        assert np.array_equal(g, og)
+        _same_report(rep, ref, 2)
+        assert rep.n_pairs == len(win.pairs)
+
+
+def test_plane_batches_across_round_sizes(sd, O):
+    """Plane-mode members whose bin layouts come from rounds of other sizes:
+    each link first updates alone (one round of its whole part, through its
+    own bins), then in batches driven by a handle with 2^14-pair rounds
+    (layouts too large for the driver's bins are scaled down), then with
+    2^18-pair rounds (scaled up from the 2^14-pair rounds), then alone
+    again; a member in mode 5 takes its own update inside the batches.
+    Every DHLA and report equals the oracle's on the link's whole stream."""
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    sizes = [1 << 19, 300_001, 150_000, 1 << 17]
+    seeds = [3000 + i for i in range(len(sizes))]
+    wins = [T.make_window(w.with_(n=n, planted=4), s, n=n) for n, s in zip(sizes, seeds)]
+    drv = sd.sd_create(sd.params_for(w, 1))
+    hs = [sd.sd_create(sd.params_for(w, s)) for s in seeds]
+    try:
+        sd.sd_set_tuning(hs[3], mode=5)
+        cuts = [0, 0, 0, 0]
+        keep = []  # the device buffers stay alive until the handles' streams have read them
+
+        def feed(frac, batched):
+            parts = []
+            for i, win in enumerate(wins):
+                end = int(len(win.pairs) * frac)
+                parts.append(_dev(win.pairs[cuts[i]:end]))
+                cuts[i] = end
+            keep.append(parts)
+            if batched:
+                sd.sd_update_many([drv] + hs, [_dev(np.zeros((0, 2), np.uint32))] + parts)
+            else:
+                for h, p in zip(hs, parts):
+                    sd.sd_update(h, p)
+
+        feed(0.3, False)
+        sd.sd_set_tuning(drv, mode=6, plane_round_log2=14)
+        feed(0.5, True)
+        feed(0.6, True)
+        sd.sd_set_tuning(drv, mode=6, plane_round_log2=18)
+        feed(0.9, True)
+        feed(1.0, False)
+        grids = [np.concatenate([sd.sd_get_grid(h, d) for d in range(2)]) for h in hs]
+        reps = sd.sd_close_many(hs)
+    finally:
+        for h in hs + [drv]:
             sd.sd_destroy(h)
     for win, s, g, rep in zip(wins, seeds, grids, reps):
         og, ref = _oracle(O, w, win.pairs, s)

@@ -70,9 +70,9 @@ def _same(rep, ref):
     assert np.array_equal(rep.hits["dir"], ref["dir"]) and np.array_equal(rep.hits["est"], ref["est"])
 
 
-def _serve(mods, w, seeds, pairs, links, budget_links, rng, chunk_log2=21):
+def _serve(mods, w, seeds, pairs, links, budget_links, rng, chunk_log2=21, mode=None):
     sd, serving = mods
-    srv = serving.Server(w, WINDOW, hbm_budget=1 << 40, bin_chunk_log2=chunk_log2)
+    srv = serving.Server(w, WINDOW, hbm_budget=1 << 40, bin_chunk_log2=chunk_log2, mode=mode)
     srv.budget = srv.fixed + budget_links * srv.link_bytes()
     for i in links:
         srv.open_link(i, seeds[i])
@@ -99,11 +99,15 @@ def _serve(mods, w, seeds, pairs, links, budget_links, rng, chunk_log2=21):
     return srv, got
 
 
-def test_served_windows_equal_oracle_and_alone(mods, O):
+@pytest.mark.parametrize("mode,chunk_log2", [(6, 21), (6, 13), (5, 21)])
+def test_served_windows_equal_oracle_and_alone(mods, O, mode, chunk_log2):
+    """Plane rounds (mode 6; with 2^13-pair rounds a batch of a link takes
+    several) and slice-binned rounds (mode 5) of the batched update."""
     w, seeds, pairs = _streams()
     rng = np.random.default_rng(11)
     links = list(range(len(pairs)))
-    srv, got = _serve(mods, w, seeds, pairs, links, budget_links=3, rng=rng)
+    srv, got = _serve(mods, w, seeds, pairs, links, budget_links=3, rng=rng, chunk_log2=chunk_log2, mode=mode)
+    assert srv.mode == mode
     assert srv.pairs_done == sum(len(p) for p in pairs)
     n_hits = 0
     for i in links:
@@ -117,28 +121,34 @@ def test_served_windows_equal_oracle_and_alone(mods, O):
     assert n_hits > 0
     # the link with the most windows, served alone with other batch cuts,
     # reports the same windows
-    _, alone = _serve(mods, w, seeds, pairs, [4], budget_links=1, rng=np.random.default_rng(3))
+    _, alone = _serve(mods, w, seeds, pairs, [4], budget_links=1, rng=np.random.default_rng(3), mode=mode)
     for k, r in alone[4].items():
         assert np.array_equal(r.report.hits, got[4][k].report.hits)
         assert r.report.n_cand == got[4][k].report.n_cand
 
 
-def test_admission_respects_budget(mods):
+@pytest.mark.parametrize("mode", [5, 6])
+def test_admission_respects_budget(mods, mode):
     sd, serving = mods
     w = _workload()
     bins = 64 << 20
-    probe = serving.Server(w, WINDOW, hbm_budget=1 << 40, bin_bytes=bins)
+    probe = serving.Server(w, WINDOW, hbm_budget=1 << 40, bin_bytes=bins, mode=mode)
     fixed, lb = probe.fixed, probe.link_bytes()
-    assert fixed >= sd.sd_scratch_bytes(probe.driver, 1 << 20) >= bins
+    scratch = sd.sd_scratch_bytes(probe.driver, 1 << 20)
+    if mode == 5:
+        assert fixed >= scratch >= bins
+    else:  # the bins of one round of 2^22 pairs: at least 9/8 of its 2^23 keys
+        assert fixed >= scratch >= 4 * (9 << 20)
     probe.shutdown()
-    assert fixed > 0 and lb > 2 * 4 * sd.sd_grid_words(sd.params_for(w, 1))
+    grid = 2 * 4 * sd.sd_grid_words(sd.params_for(w, 1))
+    assert fixed > 0 and lb > 2 * grid  # the DHLA and its plane-major copy
     with pytest.raises(ValueError):
-        serving.Server(w, WINDOW, hbm_budget=fixed - 1, bin_bytes=bins)  # not even the engine fits
-    srv = serving.Server(w, WINDOW, hbm_budget=fixed + lb - 1, bin_bytes=bins)
+        serving.Server(w, WINDOW, hbm_budget=fixed - 1, bin_bytes=bins, mode=mode)  # not even the engine fits
+    srv = serving.Server(w, WINDOW, hbm_budget=fixed + lb - 1, bin_bytes=bins, mode=mode)
     with pytest.raises(ValueError):
         srv.open_link("a", 1)  # one link does not fit
     srv.shutdown()
-    srv = serving.Server(w, WINDOW, hbm_budget=fixed + 2 * lb, bin_bytes=bins)
+    srv = serving.Server(w, WINDOW, hbm_budget=fixed + 2 * lb, bin_bytes=bins, mode=mode)
     assert srv.open_link("a", 1) and srv.open_link("b", 2)
     assert not srv.open_link("c", 3)
     assert list(srv.waiting) == ["c"] and srv.used == fixed + 2 * lb

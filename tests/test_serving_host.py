@@ -25,6 +25,7 @@ class _FakeSd:
         self.scratch = scratch
         self.created = 0
         self.live = 0
+        self.tuned = []
 
     def params_for(self, workload, seed, **kw):
         return dict(seed=seed, **kw)
@@ -41,7 +42,13 @@ class _FakeSd:
         self.live -= 1
 
     def sd_set_tuning(self, h, **kw):
-        pass
+        assert kw["mode"] in (5, 6)
+        self.tuned.append(kw)
+
+    def sd_get_tuning(self, h):
+        class _T:
+            mode = 6
+        return _T()
 
     def sd_scratch_bytes(self, h, links):
         return self.scratch
