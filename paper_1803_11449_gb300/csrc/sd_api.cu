@@ -199,6 +199,9 @@ struct sd_handle {
     unsigned long long *hits_h = nullptr; // pinned [dirs][kSortSmall]
     uint64_t cand_cap = 0, hits_cap = 0, report_cap = 0, pair_cap = 0;
     unsigned long long *big_h = nullptr;  // pinned [2][hits_cap]: large sorted hit lists
+    void *ss_d = nullptr;                 // [2] sample-sort scratch (kSampleScratchBytes each)
+    uint32_t *ss_flag_h = nullptr;        // pinned [2]: a sample sort fell short
+    bool ss_check[2] = {false, false};    // ss_flag_h[d] is to be checked after the close's last sync
     HitBuf report;
     std::vector<double> est_tbl;
     uint64_t last_ncand[2] = {0, 0};
@@ -468,6 +471,8 @@ static void release(sd_handle *h) {
     cudaFreeHost(h->st_h);
     cudaFreeHost(h->hits_h);
     cudaFreeHost(h->big_h);
+    cudaFree(h->ss_d);
+    cudaFreeHost(h->ss_flag_h);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->dstage[b]);
         cudaFreeHost(h->hstage[b]);
@@ -1243,6 +1248,7 @@ static int close_phase_b(sd_handle *h, sd_report *out) {
 static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
     CloseState &c = h->cs;
     *need_sync = false;
+    h->ss_check[0] = h->ss_check[1] = false;
     for (uint32_t d = 0; d < h->G.dirs; d++) {
         if (!c.A.run[d]) continue;
         const uint64_t nk = h->st_h->ncand[d];
@@ -1263,15 +1269,46 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
         c.keys[d] = h->hits_h + (uint64_t)d * kSortSmall;
         if (!h->st_h->big_sort[d]) continue;
         unsigned long long *sorted = nullptr;
+        uint32_t *overflow = nullptr;
         int nl = 0;
+        if (!h->ss_d) {
+            SD_CK(h, cudaMalloc(&h->ss_d, 2 * kSampleScratchBytes));
+            SD_CK(h, cudaMallocHost(&h->ss_flag_h, 2 * sizeof(uint32_t)));
+        }
         SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp + (uint64_t)d * h->hits_cap,
-                                 c.nh[d], h->num_sms, h->stream, &sorted, &nl));
+                                 c.nh[d], static_cast<char *>(h->ss_d) + d * kSampleScratchBytes, h->num_sms,
+                                 h->stream, &sorted, &nl, &overflow));
         launched(nl);
         if (!h->big_h) SD_CK(h, cudaMallocHost(&h->big_h, (uint64_t)2 * h->hits_cap * 8));
         unsigned long long *dst = h->big_h + (uint64_t)d * h->hits_cap;
         SD_CK(h, cudaMemcpyAsync(dst, sorted, c.nh[d] * 8, cudaMemcpyDeviceToHost, h->stream));
+        h->ss_check[d] = overflow != nullptr;
+        if (overflow)
+            SD_CK(h, cudaMemcpyAsync(h->ss_flag_h + d, overflow, 4, cudaMemcpyDeviceToHost, h->stream));
         c.keys[d] = dst;
         *need_sync = true;
+    }
+    return SD_OK;
+}
+
+// A sample sort of phase C that fell short (a bucket beyond one block's
+// shared memory): the list, still a permutation of the hits on the device,
+// is sorted again by the merge path and read back (after phase C's sync).
+static int redo_short_sorts(sd_handle *h) {
+    CloseState &c = h->cs;
+    for (uint32_t d = 0; d < h->G.dirs; d++) {
+        if (!h->ss_check[d]) continue;
+        h->ss_check[d] = false;
+        if (!h->ss_flag_h[d]) continue;
+        unsigned long long *sorted = nullptr;
+        uint32_t *overflow = nullptr;
+        int nl = 0;
+        SD_CK(h, launch_sort_big(h->hits + (uint64_t)d * h->hits_cap, h->hits_tmp + (uint64_t)d * h->hits_cap,
+                                 c.nh[d], nullptr, h->num_sms, h->stream, &sorted, &nl, &overflow));
+        launched(nl);
+        SD_CK(h, cudaMemcpyAsync(h->big_h + (uint64_t)d * h->hits_cap, sorted, c.nh[d] * 8, cudaMemcpyDeviceToHost,
+                                 h->stream));
+        SD_CK(h, cudaStreamSynchronize(h->stream));
     }
     return SD_OK;
 }
@@ -1279,6 +1316,8 @@ static int close_phase_c(sd_handle *h, sd_report *out, bool *need_sync) {
 static int close_phase_d(sd_handle *h, sd_report *out, bool reset = true) {
     const Geometry &G = h->G;
     CloseState &c = h->cs;
+    const int src = redo_short_sorts(h);
+    if (src != SD_OK) return src;
     for (uint32_t d = 0; d < G.dirs; d++) {
         if (!c.A.run[d] || !c.keys[d]) continue;
         // Eq. 4 depends on SZ alone within a window: one evaluation per
@@ -1483,7 +1522,7 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         const bool run = close_decide(h, &outs[i]);
         CloseJob &j = d->cj_h[i];
         j.A = h->cs.A;
-        if (run) prepare_restore(G, j.A, d->num_sms);
+        if (run) prepare_restore(G, j.A, d->num_sms, 1);
         h->cs.A = j.A;
         any = any || run;
     }

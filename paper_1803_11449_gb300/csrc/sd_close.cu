@@ -207,6 +207,12 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     const uint32_t *he0 = A.he + (uint64_t)dir * 2 * (1ull << k);
     const uint32_t *he1 = he0 + (1ull << k);
     const uint32_t *bm_dir = A.hotmap + (uint64_t)dir * G.r * nw;  // row i at bm_dir + i*nw
+    const uint64_t J = (uint64_t)n1 << A.ulog;
+    const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
+    const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
+    const uint64_t ntiles = (uint64_t)ntile0 * nchunk;
+    const uint64_t t_stop = t_end < ntiles ? t_end : ntiles;
+    if (t_begin >= t_stop) return;  // no tile of this direction for the block
 
     // rows 2..r-1 of the hot bitmap; row i is at hot2 + (i-2)*nw
     const uint32_t *hot2 = bm_dir + 2 * nw;
@@ -221,15 +227,10 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *cbuf = s_cbuf[threadIdx.x >> 5];
     uint32_t ccount = 0;  // warp-uniform
-    const uint64_t J = (uint64_t)n1 << A.ulog;
-    const uint32_t ntile0 = (n0 + A.tile0 - 1) / A.tile0;
-    const uint64_t nchunk = (J + A.jchunk - 1) / A.jchunk;
-    const uint64_t ntiles = (uint64_t)ntile0 * nchunk;
     const uint32_t lowbits = (k >= 16u) ? (2u * k - 32u) : 0u;
     const uint32_t lowmask = (1u << lowbits) - 1u;
     const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
 
-    const uint64_t t_stop = t_end < ntiles ? t_end : ntiles;
     for (uint64_t t = t_begin; t < t_stop; t += t_step) {
         const uint32_t t0 = (uint32_t)(t / nchunk);
         const uint64_t jc = t % nchunk;
@@ -281,9 +282,15 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     flush_cands(A, dir, cbuf, ccount, lane);
 }
 
+// The tiles of direction 0 (tiles0 of them), then those of direction 1,
+// dealt round-robin to the blocks of a 1-D grid.
 __global__ void __launch_bounds__(256)
-k_restore(Geometry G, RestoreArgs A) {
-    restore_body(G, A, blockIdx.y, blockIdx.x, ~0ull, gridDim.x);
+k_restore(Geometry G, RestoreArgs A, uint64_t tiles0) {
+    restore_body(G, A, 0, blockIdx.x, ~0ull, gridDim.x);
+    if (G.dirs > 1) {
+        const uint64_t first = ((uint64_t)blockIdx.x + gridDim.x - tiles0 % gridDim.x) % gridDim.x;
+        restore_body(G, A, 1, first, ~0ull, gridDim.x);
+    }
 }
 
 // k_estimate: SZ(a) = zero bits of ULE(a), the AND of a's r estimators, for
@@ -463,6 +470,135 @@ __global__ void k_merge_all(const unsigned long long *__restrict__ src, unsigned
         }
         dst[pos] = key;
     }
+}
+
+// ----------------------------------------------------- sample sort (big)
+// Hit lists longer than kSortSmall: nb buckets (a power of two, about 512
+// keys each) split by nb - 1 splitters taken from a sorted sample of
+// kSampleOver keys per bucket (evenly spaced positions); every key goes to
+// the bucket of the splitters around it, and each bucket is sorted by one
+// block in shared memory.  A bucket beyond kSortSmall keys (a sample that
+// did not represent the keys) raises *overflow, and the host sorts the
+// list again by the merge path.  Keys are distinct.
+constexpr uint32_t kSampleOver = 8;
+
+// bucket of `key`: the number of splitters below it
+__device__ __forceinline__ uint32_t bucket_of(const unsigned long long *spl, uint32_t nb, unsigned long long key) {
+    uint32_t lo = 0, hi = nb - 1;  // splitters spl[0 .. nb-2]
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (spl[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One block: sort the sample, write the splitters, clear the counters.
+__global__ void __launch_bounds__(1024)
+k_ss_splitters(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t nb, SampleSortArgs S) {
+    extern __shared__ unsigned long long smp[];  // nb * kSampleOver keys
+    const uint32_t m = nb * kSampleOver;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) smp[i] = keys[((uint64_t)i * n) / m];
+    for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) {
+        S.count[i] = 0;
+        S.cursor[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        S.ctl[0] = 0;  // count blocks done
+        S.ctl[1] = 0;  // overflow
+    }
+    __syncthreads();
+    bitonic_smem(smp, m);
+    for (uint32_t j = threadIdx.x; j + 1 < nb; j += blockDim.x) S.spl[j] = smp[(j + 1) * kSampleOver - 1];
+}
+
+// Keys per bucket; the last block turns the counts into bucket offsets.
+__global__ void __launch_bounds__(256)
+k_ss_count(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t nb, SampleSortArgs S) {
+    __shared__ unsigned long long s_spl[kSampleMaxBuckets];
+    __shared__ uint32_t s_hist[kSampleMaxBuckets];
+    __shared__ bool s_last;
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+        if (j + 1 < nb) s_spl[j] = S.spl[j];
+        s_hist[j] = 0;
+    }
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        atomicAdd(&s_hist[bucket_of(s_spl, nb, keys[i])], 1u);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
+        if (s_hist[j]) atomicAdd(&S.count[j], s_hist[j]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&S.ctl[0], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // exclusive scan of the nb <= 1024 counts, 4 consecutive ones per thread
+    __shared__ uint32_t s_w[8];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t j0 = threadIdx.x * 4;
+    uint32_t c[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        c[q] = j0 + q < nb ? __ldcg(&S.count[j0 + q]) : 0u;
+        sum += c[q];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    uint32_t run = incl - sum;
+    for (uint32_t w = 0; w < wid; w++) run += s_w[w];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (j0 + q < nb) {
+            S.off[j0 + q] = run;
+            S.cursor[j0 + q] = run;
+        }
+        run += c[q];
+    }
+    if (j0 < nb && j0 + 4 >= nb) S.off[nb] = run;
+}
+
+// Every key to a free slot of its bucket in `out`.
+__global__ void __launch_bounds__(256)
+k_ss_scatter(const unsigned long long *__restrict__ keys, unsigned long long *__restrict__ out, uint64_t n, uint32_t nb,
+             SampleSortArgs S) {
+    __shared__ unsigned long long s_spl[kSampleMaxBuckets];
+    for (uint32_t j = threadIdx.x; j + 1 < nb; j += blockDim.x) s_spl[j] = S.spl[j];
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long key = keys[i];
+        out[atomicAdd(&S.cursor[bucket_of(s_spl, nb, key)], 1u)] = key;
+    }
+}
+
+// One block per bucket: its keys of `in` sorted into the same places of `out`.
+__global__ void __launch_bounds__(1024)
+k_ss_buckets(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out, SampleSortArgs S) {
+    extern __shared__ unsigned long long s[];  // kSortSmall keys
+    const uint32_t b = blockIdx.x;
+    const uint32_t lo = S.off[b], len = S.off[b + 1] - lo;
+    if (len > (uint32_t)kSortSmall) {
+        if (threadIdx.x == 0) atomicOr(&S.ctl[1], 1u);
+        return;
+    }
+    if (len == 0) return;
+    unsigned P = 1;
+    while (P < len) P <<= 1;
+    for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? in[lo + i] : ~0ull;
+    __syncthreads();
+    bitonic_smem(s, P);
+    for (unsigned i = threadIdx.x; i < len; i += blockDim.x) out[lo + i] = s[i];
 }
 
 // ------------------------------------------------------------ reset/merge
@@ -650,14 +786,16 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
 // Tile shape of k_restore for A's sizes: preimages per (c0, c1), (c1, t)
 // items per tile, and c0 values per tile -- enough work per tile to amortise
 // its set-up while still giving every resident block about one tile.
-void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms) {
+void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms, uint32_t tiles_per_block) {
     const unsigned threads = 256;
     A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
     A.jchunk = threads;
     uint64_t tests = 0;
     for (uint32_t d = 0; d < G.dirs; d++)
         if (A.run[d]) tests += (uint64_t)A.n0[d] * ((uint64_t)A.n1[d] << A.ulog);
-    const uint64_t per_block = tests / ((uint64_t)num_sms * 8 * threads) + 1;
+    // c0 values per tile: about tiles_per_block tiles for each of the
+    // (up to) 8 blocks per SM, so that the last wave of tiles is short
+    const uint64_t per_block = tests / ((uint64_t)num_sms * 8 * threads * tiles_per_block) + 1;
     A.tile0 = (uint32_t)(per_block < kRestoreTileMax ? per_block : kRestoreTileMax);
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
     A.smem_hot = hot_bytes <= (size_t)200 * 1024;
@@ -671,26 +809,20 @@ static uint64_t restore_tiles_dir(const Geometry &G, const RestoreArgs &A, uint3
     return t0 * nc;
 }
 
-static uint64_t restore_tiles(const Geometry &G, const RestoreArgs &A) {
-    uint64_t most = 0;
-    for (uint32_t d = 0; d < G.dirs; d++) most = std::max(most, restore_tiles_dir(G, A, d));
-    return most;
-}
-
 cudaError_t launch_restore(const Geometry &G, RestoreArgs A, int num_sms, cudaStream_t s) {
     const unsigned threads = 256;
-    prepare_restore(G, A, num_sms);
+    prepare_restore(G, A, num_sms, 4);
     const size_t hot_bytes = (size_t)(G.r - 2) * ((1u << G.k) >> 5) * 4;
     const size_t smem = A.smem_hot ? hot_bytes : 16;
-    const uint64_t most = restore_tiles(G, A);
-    if (most == 0) return cudaSuccess;
+    const uint64_t tiles0 = restore_tiles_dir(G, A, 0);
+    const uint64_t total = tiles0 + restore_tiles_dir(G, A, 1);
+    if (total == 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_restore), (int)threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (uint64_t)num_sms * per_sm;
-    if (most < blocks) blocks = most;
-    dim3 grid((unsigned)blocks, G.dirs);
-    k_restore<<<grid, threads, smem, s>>>(G, A);
+    if (total < blocks) blocks = total;
+    k_restore<<<(unsigned)blocks, threads, smem, s>>>(G, A, tiles0);
     return cudaGetLastError();
 }
 
@@ -710,13 +842,37 @@ cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatB
     return cudaGetLastError();
 }
 
-// Sort keys[0, n) ascending (distinct keys) with `tmp` as scratch of the
-// same size; *out points at whichever of the two holds the result.
-cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
-                            cudaStream_t s, unsigned long long **out, int *launches) {
+cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, void *scratch, int num_sms,
+                            cudaStream_t s, unsigned long long **out, int *launches, uint32_t **overflow) {
     const int smem = kSortSmall * (int)sizeof(unsigned long long);
     int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_sort_segments), 1024, smem, &per_sm);
+    cudaError_t e;
+    *overflow = nullptr;
+    if (scratch && n <= kSampleMaxKeys) {
+        uint32_t nb = 2;
+        while ((uint64_t)nb * 512 < n) nb <<= 1;
+        SampleSortArgs S;
+        S.spl = static_cast<unsigned long long *>(scratch);
+        S.count = reinterpret_cast<uint32_t *>(S.spl + kSampleMaxBuckets);
+        S.off = S.count + kSampleMaxBuckets + 1;
+        S.cursor = S.off + kSampleMaxBuckets + 1;
+        S.ctl = S.cursor + kSampleMaxBuckets + 1;
+        const int ssmem = (int)(nb * kSampleOver * sizeof(unsigned long long));
+        if ((e = prepare_launch(reinterpret_cast<const void *>(k_ss_splitters), 1024, ssmem, &per_sm)) != cudaSuccess)
+            return e;
+        if ((e = prepare_launch(reinterpret_cast<const void *>(k_ss_buckets), 1024, smem, &per_sm)) != cudaSuccess)
+            return e;
+        const unsigned blocks = grid_for(n, 256, num_sms, 4);
+        k_ss_splitters<<<1, 1024, ssmem, s>>>(keys, n, nb, S);
+        k_ss_count<<<blocks, 256, 0, s>>>(keys, n, nb, S);
+        k_ss_scatter<<<blocks, 256, 0, s>>>(keys, tmp, n, nb, S);
+        k_ss_buckets<<<nb, 1024, smem, s>>>(tmp, keys, S);
+        *launches = 4;
+        *out = keys;
+        *overflow = S.ctl + 1;
+        return cudaGetLastError();
+    }
+    e = prepare_launch(reinterpret_cast<const void *>(k_sort_segments), 1024, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t segs = (n + kSortSmall - 1) / kSortSmall;
     k_sort_segments<<<(unsigned)segs, 1024, smem, s>>>(keys, n);

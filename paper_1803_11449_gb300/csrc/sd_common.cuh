@@ -92,6 +92,20 @@ struct BinArgs {
 
 
 constexpr int kSortSmall = 2048;  // keys sorted by one block in shared memory
+// Sample sort of hit lists beyond kSortSmall keys (up to kSampleMaxBuckets
+// buckets of about 512 keys; longer lists take the merge path): splitters,
+// per-bucket counts, offsets and cursors, and two control words (blocks
+// done, overflow) in a scratch of kSampleScratchBytes per direction.
+constexpr uint32_t kSampleMaxBuckets = 1024;
+constexpr uint64_t kSampleMaxKeys = (uint64_t)kSampleMaxBuckets * 512;
+constexpr size_t kSampleScratchBytes = 24 * 1024;
+struct SampleSortArgs {
+    unsigned long long *spl;  // [nb - 1] splitters, ascending
+    uint32_t *count;          // [nb] keys per bucket
+    uint32_t *off;            // [nb + 1] first slot of each bucket
+    uint32_t *cursor;         // [nb] next free slot of each bucket
+    uint32_t *ctl;            // [0] count blocks done, [1] a bucket overflowed
+};
 
 // Per-window counters, copied to the host in one transfer.
 struct StatBlock {
@@ -222,7 +236,7 @@ void geometry_of(const sd_params *p, Geometry *out);
 // kSortSmall hits per direction into st_out[count] / hits_out[count][2]
 // [kSortSmall]; the reset of every job's DHLA and counters.
 cudaError_t launch_stats_many(const CloseJob *J, uint32_t count, const Geometry &G, int num_sms, cudaStream_t s);
-void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms);
+void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms, uint32_t tiles_per_block);
 // (restore and estimate spread all jobs' tiles / candidates over the whole
 // grid: tile_base_* and cand_base_d hold 2 count + 1 offsets)
 cudaError_t launch_restore_many(const CloseJob *J, const CloseJob *Jh, uint32_t count, unsigned long long *tile_base_d,
@@ -235,8 +249,14 @@ cudaError_t launch_reset_many(const CloseJob *J, uint32_t count, const Geometry 
 cudaError_t launch_join(const Geometry &G, const JoinArgs &J, int num_sms, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *hits, uint64_t hits_cap, StatBlock *st,
                               const uint32_t run[2], uint32_t dirs, cudaStream_t s);
-cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, int num_sms,
-                            cudaStream_t s, unsigned long long **out, int *launches);
+// Sort keys[0, n) ascending (distinct keys, n > kSortSmall) with tmp as
+// scratch of the same size; *out gets the array holding the result.  With
+// `scratch` (kSampleScratchBytes of device memory) and n <= kSampleMaxKeys
+// the sample sort runs and *overflow points at a device word that is
+// nonzero if it fell short (the caller then sorts again with scratch =
+// nullptr: the merge path); otherwise *overflow is nullptr.
+cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, uint64_t n, void *scratch, int num_sms,
+                            cudaStream_t s, unsigned long long **out, int *launches, uint32_t **overflow);
 cudaError_t launch_reset(uint32_t *grid, uint64_t words, StatBlock *st, int num_sms, cudaStream_t s);
 cudaError_t launch_merge(uint32_t *dst, const uint32_t *src, uint64_t words, int num_sms, cudaStream_t s);
 size_t bin_smem_bytes(uint32_t tile_pairs, uint32_t upd_per_pair, uint32_t S);

@@ -470,12 +470,13 @@ def test_report_cap_truncates_in_order(sd, O, torch_mod):
     assert np.array_equal(rep.hits["est"], ref["est"][:17])
 
 
-@pytest.mark.parametrize("p_full,least", [(0.0465, 8192), (0.066, 65536)])
+@pytest.mark.parametrize("p_full,least", [(0.0465, 8192), (0.066, 65536), (0.11, 1 << 19)])
 def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod, p_full, least):
     """A DHLA where a fraction p of the estimators of each row are full: |K|
     is about p^4 2^32, every candidate has SZ = 0 and is reported, and more
-    than one block sorts: up to 32 sorted segments merge in one pass, more
-    in pairwise passes."""
+    than one block sorts: up to 2^19 hits by the sample sort (buckets split
+    at sampled keys, each sorted by one block), more by sorted segments
+    merged in pairwise passes."""
     w = T.WORKLOADS["core"].with_(dirs=1, g=256)
     rng = np.random.default_rng(12)
     cells = rng.random((w.r, 1 << w.k)) < p_full
@@ -483,7 +484,8 @@ def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod, p_full, least):
     grid[cells] = 0xFFFFFFFF
     grid[~cells, 0] = 1   # every other estimator keeps g-1 zero bits
     grid = grid.reshape(-1)
-    p = sd.params_for(w, SEED, cand_cap=1 << 17,
+    cap = 1 << 17 if least < (1 << 19) else 1 << 20
+    p = sd.params_for(w, SEED, cand_cap=cap,
                       cuda_stream=torch_mod.cuda.current_stream().cuda_stream)
     h = sd.sd_create(p)
     try:
@@ -491,7 +493,7 @@ def test_many_hits_take_the_multi_block_sort(sd, O, torch_mod, p_full, least):
         rep = sd.sd_close_window(h)
     finally:
         sd.sd_destroy(h)
-    op = O.params_from(w.sketch(), seed=SEED, cand_cap=1 << 17)
+    op = O.params_from(w.sketch(), seed=SEED, cand_cap=cap)
     ref = O.close_window(op, grid)
     assert ref["n_hits"] > least
     _assert_report_equal(O, rep, ref, p)
