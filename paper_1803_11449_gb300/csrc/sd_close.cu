@@ -7,11 +7,15 @@
 //   k_compact     sorted lists HE(0) and HE(1) (all HE(i) for the staged
 //                 join of sd_join.cu) from their bitmaps.
 //   k_restore     the candidate set K = {a : DH_i(a) in HE(i) for all i}.
-//   k_estimate    SZ(a) from ULE(a) = AND of a's r estimators, one warp per
-//                 candidate, keeping (a, SZ) when SZ <= szmax.
+//   k_estimate    SZ(a) from ULE(a) = AND of a's r estimators (16-byte
+//                 chunks, several candidates per warp), keeping (a, SZ) when
+//                 SZ <= szmax.
 //   k_sort_small  orders each direction's hits by address (bitonic, smem).
-//   k_sort_segments + k_merge_rank  the same for hit lists too large for one
-//                 block: sorted 2048-key segments, then pairwise merges.
+//   k_ss_*        the same for up to 2^19 hits: a sample sort (splitters
+//                 from a sorted sample, keys scattered to buckets, each
+//                 bucket sorted by one block).
+//   k_sort_segments + k_merge_rank  longer lists, or a sample sort that fell
+//                 short: sorted 2048-key segments, then pairwise merges.
 //   k_reset       clears the DHLA and the per-window counters.
 //   k_merge_or    dst |= src over whole DHLAs (multi-monitor merge).
 //   k_*_many      the same kernels over an array of windows of one shape
@@ -185,6 +189,41 @@ __device__ __forceinline__ void flush_hits(const RestoreArgs &A, uint32_t dir, u
     __syncwarp();
 }
 
+// The (c0, c1) tests of one c1 against the tile's c0 values for k >= 16 and
+// R rows (the inner loop of restore_body, specialised): a's low k bits are
+// L = c0 ^ c1; its high 32 - k bits are A0^-1 (c0 >> (2k - 32) - (A0 L >> k))
+// mod 2^(32-k), computed as one multiply by A0^-1 2^k; the low 2k - 32 bits
+// of c0 must match the top bits of A0 L mod 2^k; rows 2..R-1 are looked up
+// in the hot bitmap.  Candidates go to the warp's buffer.
+template <int R>
+__device__ __forceinline__ void restore_c1_k16(const Geometry &G, const RestoreArgs &A, uint32_t dir,
+                                               const uint32_t *s_c0, uint32_t nc0, const uint32_t *hot2, uint32_t nw,
+                                               uint32_t c1, bool jvalid, uint32_t A0, uint32_t A0inv,
+                                               uint32_t *cbuf, uint32_t &ccount, uint32_t lane) {
+    const uint32_t k = G.k, kmask = (1u << k) - 1u;
+    const uint32_t lowbits = 2u * k - 32u, lowmask = (1u << lowbits) - 1u;
+    const uint32_t A0inv_k = A0inv << k;
+    uint32_t sh[R > 2 ? R - 2 : 1];
+#pragma unroll
+    for (int i = 2; i < R; i++) sh[i - 2] = (uint32_t)(i - 1) * G.alpha;
+    for (uint32_t q = 0; q < nc0; q++) {
+        const uint32_t c0 = s_c0[q];  // same for the whole block
+        const uint32_t L = c0 ^ c1;
+        const uint32_t Q = A0 * L;
+        const uint32_t a = A0inv_k * ((c0 >> lowbits) - (Q >> k)) + L;
+        bool found = jvalid && (((Q & kmask) >> (32u - k)) == (c0 & lowmask));
+#pragma unroll
+        for (int i = 2; i < R; i++)
+            found = found & hot_at(hot2 + (uint32_t)(i - 2) * nw, (shr_clamp(a, sh[i - 2]) & kmask) ^ c0);
+        const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
+        if (!fb) continue;
+        if (found) cbuf[ccount + __popc(fb & ((1u << lane) - 1u))] = a;
+        ccount += __popc(fb);
+        __syncwarp();
+        if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane);
+    }
+}
+
 // Tiles t_begin, t_begin + t_step, ... below t_end of direction `dir`.
 __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArgs &A, uint32_t dir, uint64_t t_begin,
                                              uint64_t t_end, uint64_t t_step) {
@@ -251,6 +290,17 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
             const uint32_t i1 = (uint32_t)(j >> A.ulog);
             const uint32_t tt = (uint32_t)(j & ((1ull << A.ulog) - 1ull));
             const uint32_t c1 = jvalid ? he1[i1] : 0u;
+            if (k >= 16u && G.r <= 8u) {
+                switch (G.r) {
+                    case 3: restore_c1_k16<3>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                    case 4: restore_c1_k16<4>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                    case 5: restore_c1_k16<5>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                    case 6: restore_c1_k16<6>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                    case 7: restore_c1_k16<7>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                    default: restore_c1_k16<8>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
+                }
+                continue;
+            }
             for (uint32_t q = 0; q < nc0; q++) {
                 const uint32_t c0 = s_c0[q];  // same for the whole block
                 const uint32_t L = c0 ^ c1;                 // BL(1): the low k bits of a
@@ -313,6 +363,46 @@ __device__ __forceinline__ void estimate_body(const Geometry &G, const RestoreAr
     const uint32_t *gdir = A.grid + (uint64_t)dir * G.dir_words;
     const uint32_t *cand = A.cand + (uint64_t)dir * A.cand_cap;
     const uint64_t q_stop = q_end < nk ? q_end : nk;
+    if (G.wpc >= 4) {
+        // lpc lanes per candidate, each ANDing 16-byte chunks of the r
+        // estimators; the warp's 32 / lpc candidates are q, q + q_step, ...
+        const uint32_t chunks = G.wpc >> 2;
+        const uint32_t lpc = chunks < 32u ? chunks : 32u;
+        const uint32_t cpw = 32u / lpc, sub = lane / lpc, sl = lane % lpc;
+        const uint32_t kmask = (1u << G.k) - 1u;
+        for (uint64_t q0 = q_begin; q0 < q_stop; q0 += (uint64_t)cpw * q_step) {
+            const uint64_t q = q0 + (uint64_t)sub * q_step;
+            const bool ok = q < q_stop;
+            const uint32_t x = ok ? cand[q] : 0u;
+            const uint32_t c0 = dh0(A0, G.k, x);
+            uint32_t ones = 0;
+            if (ok) {
+                for (uint32_t c = sl; c < chunks; c += lpc) {
+                    uint4 ule = make_uint4(~0u, ~0u, ~0u, ~0u);
+#pragma unroll
+                    for (uint32_t i = 0; i < 8; i++) {
+                        if (i >= G.r) break;
+                        const uint32_t ci = i == 0 ? c0 : ((shr_clamp(x, (i - 1u) * G.alpha) & kmask) ^ c0);
+                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(gdir + (uint64_t)i * G.row_words +
+                                                                              (uint64_t)ci * G.wpc) + c);
+                        ule.x &= v.x; ule.y &= v.y; ule.z &= v.z; ule.w &= v.w;
+                    }
+                    ones += __popc(ule.x) + __popc(ule.y) + __popc(ule.z) + __popc(ule.w);
+                }
+            }
+            for (uint32_t o = lpc >> 1; o > 0; o >>= 1) ones += __shfl_xor_sync(0xFFFFFFFFu, ones, o);
+            const bool hit = ok && sl == 0 && (int)(G.g - ones) <= szmax;
+            const unsigned hb = __ballot_sync(0xFFFFFFFFu, hit);
+            if (!hb) continue;
+            if (hit) hbuf[hcount + __popc(hb & ((1u << lane) - 1u))] = ((unsigned long long)x << 32) | (G.g - ones);
+            hcount += __popc(hb);
+            __syncwarp();
+            if (hcount >= 32) flush_hits(A, dir, hbuf, hcount, lane);
+        }
+        __syncwarp();
+        flush_hits(A, dir, hbuf, hcount, lane);
+        return;
+    }
     for (uint64_t q = q_begin; q < q_stop; q += q_step) {
         const uint32_t x = cand[q];
         const uint32_t c0 = dh0(A0, G.k, x);
@@ -473,14 +563,14 @@ __global__ void k_merge_all(const unsigned long long *__restrict__ src, unsigned
 }
 
 // ----------------------------------------------------- sample sort (big)
-// Hit lists longer than kSortSmall: nb buckets (a power of two, about 512
-// keys each) split by nb - 1 splitters taken from a sorted sample of
-// kSampleOver keys per bucket (evenly spaced positions); every key goes to
-// the bucket of the splitters around it, and each bucket is sorted by one
-// block in shared memory.  A bucket beyond kSortSmall keys (a sample that
-// did not represent the keys) raises *overflow, and the host sorts the
-// list again by the merge path.  Keys are distinct.
-constexpr uint32_t kSampleOver = 8;
+// Hit lists longer than kSortSmall: nb buckets (a power of two, about 128
+// keys each, up to 1024 buckets) split by nb - 1 splitters taken from a
+// sorted sample of `over` keys per bucket (evenly spaced positions: 2 per
+// bucket of 128, 8 for larger buckets); every key goes to the bucket of the
+// splitters around it, and each bucket is sorted by one block in shared
+// memory.  A bucket beyond kSortSmall keys (a sample that did not represent
+// the keys) raises *overflow, and the host sorts the list again by the
+// merge path.  Keys are distinct.
 
 // bucket of `key`: the number of splitters below it
 __device__ __forceinline__ uint32_t bucket_of(const unsigned long long *spl, uint32_t nb, unsigned long long key) {
@@ -495,9 +585,9 @@ __device__ __forceinline__ uint32_t bucket_of(const unsigned long long *spl, uin
 
 // One block: sort the sample, write the splitters, clear the counters.
 __global__ void __launch_bounds__(1024)
-k_ss_splitters(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t nb, SampleSortArgs S) {
-    extern __shared__ unsigned long long smp[];  // nb * kSampleOver keys
-    const uint32_t m = nb * kSampleOver;
+k_ss_splitters(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t nb, uint32_t over, SampleSortArgs S) {
+    extern __shared__ unsigned long long smp[];  // nb * over keys
+    const uint32_t m = nb * over;
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) smp[i] = keys[((uint64_t)i * n) / m];
     for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) {
         S.count[i] = 0;
@@ -508,8 +598,22 @@ k_ss_splitters(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t
         S.ctl[1] = 0;  // overflow
     }
     __syncthreads();
-    bitonic_smem(smp, m);
-    for (uint32_t j = threadIdx.x; j + 1 < nb; j += blockDim.x) S.spl[j] = smp[(j + 1) * kSampleOver - 1];
+    if (m <= blockDim.x) {
+        // a small sample: each thread places its key by counting the keys
+        // below it (sample keys are distinct keys of the list)
+        unsigned long long key = 0;
+        uint32_t rank = 0;
+        if (threadIdx.x < m) {
+            key = smp[threadIdx.x];
+            for (uint32_t j = 0; j < m; j++) rank += smp[j] < key;
+        }
+        __syncthreads();
+        if (threadIdx.x < m) smp[rank] = key;
+        __syncthreads();
+    } else {
+        bitonic_smem(smp, m);
+    }
+    for (uint32_t j = threadIdx.x; j + 1 < nb; j += blockDim.x) S.spl[j] = smp[(j + 1) * over - 1];
 }
 
 // Keys per bucket; the last block turns the counts into bucket offsets.
@@ -568,22 +672,53 @@ k_ss_count(const unsigned long long *__restrict__ keys, uint64_t n, uint32_t nb,
     if (j0 < nb && j0 + 4 >= nb) S.off[nb] = run;
 }
 
-// Every key to a free slot of its bucket in `out`.
+// Every key to a free slot of its bucket in `out`: a block takes
+// kScatterKeys keys per thread, ranks them per bucket in shared memory and
+// reserves each bucket's run with one atomic.
+constexpr uint32_t kScatterKeys = 4;
 __global__ void __launch_bounds__(256)
 k_ss_scatter(const unsigned long long *__restrict__ keys, unsigned long long *__restrict__ out, uint64_t n, uint32_t nb,
              SampleSortArgs S) {
     __shared__ unsigned long long s_spl[kSampleMaxBuckets];
-    for (uint32_t j = threadIdx.x; j + 1 < nb; j += blockDim.x) s_spl[j] = S.spl[j];
+    __shared__ uint32_t s_cnt[kSampleMaxBuckets];
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+        if (j + 1 < nb) s_spl[j] = S.spl[j];
+        s_cnt[j] = 0;
+    }
     __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long key = keys[i];
-        out[atomicAdd(&S.cursor[bucket_of(s_spl, nb, key)], 1u)] = key;
+    const uint64_t per_block = (uint64_t)blockDim.x * kScatterKeys;
+    for (uint64_t base = (uint64_t)blockIdx.x * per_block; base < n; base += (uint64_t)gridDim.x * per_block) {
+        unsigned long long key[kScatterKeys];
+        uint32_t b[kScatterKeys], rank[kScatterKeys];
+#pragma unroll
+        for (uint32_t u = 0; u < kScatterKeys; u++) {
+            const uint64_t i = base + (uint64_t)u * blockDim.x + threadIdx.x;
+            b[u] = 0xFFFFFFFFu;
+            if (i < n) {
+                key[u] = keys[i];
+                b[u] = bucket_of(s_spl, nb, key[u]);
+                rank[u] = atomicAdd(&s_cnt[b[u]], 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+            const uint32_t c = s_cnt[j];
+            s_cnt[j] = c ? atomicAdd(&S.cursor[j], c) : 0u;  // the run's first slot
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t u = 0; u < kScatterKeys; u++)
+            if (b[u] != 0xFFFFFFFFu) out[s_cnt[b[u]] + rank[u]] = key[u];
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) s_cnt[j] = 0;
+        __syncthreads();
     }
 }
 
-// One block per bucket: its keys of `in` sorted into the same places of `out`.
-__global__ void __launch_bounds__(1024)
+// One block per bucket: its keys of `in` sorted into the same places of
+// `out` (up to 512 keys: each key placed by counting the keys below it;
+// more: bitonic).
+__global__ void __launch_bounds__(256)
 k_ss_buckets(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out, SampleSortArgs S) {
     extern __shared__ unsigned long long s[];  // kSortSmall keys
     const uint32_t b = blockIdx.x;
@@ -593,6 +728,17 @@ k_ss_buckets(const unsigned long long *__restrict__ in, unsigned long long *__re
         return;
     }
     if (len == 0) return;
+    if (len <= 512) {
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) s[i] = in[lo + i];
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
+            const unsigned long long key = s[i];
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < len; j++) rank += s[j] < key;
+            out[lo + rank] = key;
+        }
+        return;
+    }
     unsigned P = 1;
     while (P < len) P <<= 1;
     for (unsigned i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? in[lo + i] : ~0ull;
@@ -850,23 +996,24 @@ cudaError_t launch_sort_big(unsigned long long *keys, unsigned long long *tmp, u
     *overflow = nullptr;
     if (scratch && n <= kSampleMaxKeys) {
         uint32_t nb = 2;
-        while ((uint64_t)nb * 512 < n) nb <<= 1;
+        while ((uint64_t)nb * 128 < n && nb < kSampleMaxBuckets) nb <<= 1;
+        const uint32_t over = (uint64_t)nb * 256 >= n ? 2u : 8u;
         SampleSortArgs S;
         S.spl = static_cast<unsigned long long *>(scratch);
         S.count = reinterpret_cast<uint32_t *>(S.spl + kSampleMaxBuckets);
         S.off = S.count + kSampleMaxBuckets + 1;
         S.cursor = S.off + kSampleMaxBuckets + 1;
         S.ctl = S.cursor + kSampleMaxBuckets + 1;
-        const int ssmem = (int)(nb * kSampleOver * sizeof(unsigned long long));
+        const int ssmem = (int)(nb * over * sizeof(unsigned long long));
         if ((e = prepare_launch(reinterpret_cast<const void *>(k_ss_splitters), 1024, ssmem, &per_sm)) != cudaSuccess)
             return e;
-        if ((e = prepare_launch(reinterpret_cast<const void *>(k_ss_buckets), 1024, smem, &per_sm)) != cudaSuccess)
+        if ((e = prepare_launch(reinterpret_cast<const void *>(k_ss_buckets), 256, smem, &per_sm)) != cudaSuccess)
             return e;
         const unsigned blocks = grid_for(n, 256, num_sms, 4);
-        k_ss_splitters<<<1, 1024, ssmem, s>>>(keys, n, nb, S);
+        k_ss_splitters<<<1, 1024, ssmem, s>>>(keys, n, nb, over, S);
         k_ss_count<<<blocks, 256, 0, s>>>(keys, n, nb, S);
-        k_ss_scatter<<<blocks, 256, 0, s>>>(keys, tmp, n, nb, S);
-        k_ss_buckets<<<nb, 1024, smem, s>>>(tmp, keys, S);
+        k_ss_scatter<<<grid_for(n, 256 * kScatterKeys, num_sms, 4), 256, 0, s>>>(keys, tmp, n, nb, S);
+        k_ss_buckets<<<nb, 256, smem, s>>>(tmp, keys, S);
         *launches = 4;
         *out = keys;
         *overflow = S.ctl + 1;
