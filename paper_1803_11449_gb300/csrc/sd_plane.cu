@@ -33,8 +33,8 @@
 //                  next round's bins from this round's counts.
 //   k_plane_fold   (window close, sd_get_grid, sd_merge) transposes the
 //                  plane-major copy into the estimator-major DHLA
-//                  (grid |= planes^T, 32 x 32 bit blocks by warp shuffles)
-//                  and clears it.
+//                  (grid |= planes^T: tiles read with coalesced loads, 32 x
+//                  32 bit blocks transposed in registers) and clears it.
 //
 // Per pair this moves dirs keys (4 bytes each) through the bins instead of
 // r * dirs bit positions, and the plane copy is swept once per round by
@@ -502,147 +502,110 @@ k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf, uint32_t per_block) {
 }
 
 // ------------------------------------------------------------------- fold
-// One warp per (direction, row, group of 32 WQ estimators, TC of their bit
-// words), WQ = 8 plane words (256 estimators) where rows are that long.  For
-// each bit word t, lane j reads the group's WQ words of plane 32t + j (one
-// 32-byte sector) and clears them, four words t in flight; a 32 x 32 bit
-// transpose by shuffles turns each into word t of 32 estimators (lane l:
-// estimator 32q + l); the TC words of every estimator are staged in shared
-// memory and ORed into the DHLA, where they are contiguous.
-constexpr uint32_t kFoldWarps = 8;
-constexpr uint32_t kFoldTC = 8;    // estimator words per warp item
-constexpr uint32_t kFoldBatch = 4; // plane words t loaded before transposing
+// One block per tile: TC groups of 32 planes (32 TC consecutive bits of
+// every estimator of a row) times W consecutive words of one row of those
+// planes (32 W estimators).  The tile is read with coalesced 16-byte loads
+// into shared memory (and its plane words cleared); each thread (t, w)
+// transposes the 32 x 32 bit block of plane group t at word w in registers
+// (32 words of 32 planes -> word t of 32 estimators); the results are
+// staged by (t, estimator) and each estimator's TC words are written to the
+// DHLA with one or two vector stores.  A DHLA known to be all zero ("clean")
+// is written without being read.
+constexpr uint32_t kFoldThreads = 256;
+constexpr uint32_t kFoldTC = 8;   // estimator words (groups of 32 planes) per tile
+constexpr uint32_t kFoldW = 32;   // plane words per tile
+constexpr size_t kFoldSmem = (size_t)2 * 32 * kFoldTC * kFoldW * 4;  // input and output stages
 
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
+// 32 x 32 bit transpose in registers: afterwards bit j of x[b] is what was
+// bit b of x[j] (block swaps of 16, 8, 4, 2 and 1 bits).
+__device__ __forceinline__ void transpose32_regs(uint32_t (&x)[32]) {
 #pragma unroll
-    for (uint32_t j = 16; j > 0; j >>= 1) {
-        const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
-                         : j == 2 ? 0x33333333u : 0x55555555u;
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+    for (int s = 0; s < 5; s++) {
+        const uint32_t j = 16u >> s;
+        const uint32_t m = s == 0 ? 0x0000FFFFu : s == 1 ? 0x00FF00FFu : s == 2 ? 0x0F0F0F0Fu
+                         : s == 3 ? 0x33333333u : 0x55555555u;
+#pragma unroll
+        for (uint32_t r = 0; r < 32; r++) {
+            if (r & j) continue;
+            const uint32_t t = ((x[r] >> j) ^ x[r + j]) & m;
+            x[r] ^= t << j;
+            x[r + j] ^= t;
+        }
     }
-    return x;
 }
 
 // Folds of several handles of one shape run as one launch (the batched
-// close): the items of job j follow those of job j - 1.  A job whose DHLA
-// is known to be all zero (every update since its last reset went through
-// the planes) stores the transposed words without reading the DHLA.
-__global__ void __launch_bounds__(kFoldWarps * 32, 3)
+// close): the tiles of job j follow those of job j - 1.
+__global__ void __launch_bounds__(kFoldThreads)
 k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geometry G, uint32_t ps) {
-    extern __shared__ uint32_t stg[];  // [warps][256 estimators][kFoldTC + 1]
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    constexpr uint32_t SP = kFoldTC + 1;
-    uint32_t *my = stg + (size_t)wid * 256 * SP;
+    extern __shared__ uint4 fold_smem[];
+    uint32_t *in = reinterpret_cast<uint32_t *>(fold_smem);  // [32 TC planes][W words]
+    uint32_t *out = in + 32 * kFoldTC * kFoldW;              // [TC][32 bits][W words]
     const uint32_t wpc = G.wpc;
-    const uint32_t tc = wpc < kFoldTC ? wpc : kFoldTC;
-    const uint32_t nchunks = wpc / tc;
-    const uint32_t rw = (1u << G.k) >> 5;      // plane words per row
-    const uint32_t wq = rw < 8u ? rw : 8u;     // plane words per warp item
-    const uint32_t groups = rw / wq;
-    const uint64_t per_job = (uint64_t)G.dirs * G.r * groups * nchunks;
-    const uint64_t items = per_job * njobs;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t it0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wid; it0 < items; it0 += nwarps) {
-        const uint32_t jn = (uint32_t)(it0 / per_job);
+    const uint32_t TC = wpc < kFoldTC ? wpc : kFoldTC;
+    const uint32_t rw = (1u << G.k) >> 5;  // plane words per row
+    const uint32_t W = rw < kFoldW ? rw : kFoldW;
+    const uint32_t wgroups = rw / W, tgroups = wpc / TC;
+    const uint64_t per_job = (uint64_t)G.dirs * G.r * wgroups * tgroups;
+    const uint64_t tiles = per_job * njobs;
+    const uint32_t W4 = W / 4, rows = 32u * TC;
+    const uint32_t tt = threadIdx.x >> 5, w = threadIdx.x & 31u;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint32_t jn = (uint32_t)(tile / per_job);
         const FoldJob job = jobs ? jobs[jn] : one;
-        uint32_t *__restrict__ grid = job.grid;
-        uint32_t *__restrict__ planes = job.planes;
-        const uint64_t it = it0 - (uint64_t)jn * per_job;
-        const uint32_t chunk = (uint32_t)(it % nchunks);
-        const uint64_t rest = it / nchunks;
-        const uint32_t grp = (uint32_t)(rest % groups);
-        const uint32_t di = (uint32_t)(rest / groups);
-        const uint32_t d = di / G.r, i = di - d * G.r;
-        const uint32_t w0 = grp * wq, tc0 = chunk * tc;
-        uint32_t *row = grid + (uint64_t)d * G.dir_words + (uint64_t)i * G.row_words;
-        for (uint32_t t0 = 0; t0 < tc; t0 += kFoldBatch) {
-            uint32_t x[kFoldBatch][8];
-#pragma unroll
-            for (uint32_t bt = 0; bt < kFoldBatch; bt++) {
-                const uint32_t tt = t0 + bt;
-                uint32_t *src = planes + (uint64_t)(d * G.g + 32u * (tc0 + tt) + lane) * ps + (uint64_t)i * rw + w0;
-                if (tt >= tc) {
-#pragma unroll
-                    for (uint32_t q = 0; q < 8; q++) x[bt][q] = 0u;
-                } else if (wq == 8) {
-                    uint4 *s4 = reinterpret_cast<uint4 *>(src);
-                    const uint4 a = s4[0], b = s4[1];
-                    x[bt][0] = a.x; x[bt][1] = a.y; x[bt][2] = a.z; x[bt][3] = a.w;
-                    x[bt][4] = b.x; x[bt][5] = b.y; x[bt][6] = b.z; x[bt][7] = b.w;
-                } else {
-#pragma unroll
-                    for (uint32_t q = 0; q < 8; q++) x[bt][q] = q < wq ? src[q] : 0u;
-                }
-            }
-#pragma unroll
-            for (uint32_t bt = 0; bt < kFoldBatch; bt++) {
-                const uint32_t tt = t0 + bt;
-                if (tt >= tc) continue;  // warp-uniform
-                uint32_t *src = planes + (uint64_t)(d * G.g + 32u * (tc0 + tt) + lane) * ps + (uint64_t)i * rw + w0;
-                if (wq == 8) {  // clear the plane words just read
-                    uint4 *s4 = reinterpret_cast<uint4 *>(src);
-                    if (x[bt][0] | x[bt][1] | x[bt][2] | x[bt][3]) s4[0] = make_uint4(0, 0, 0, 0);
-                    if (x[bt][4] | x[bt][5] | x[bt][6] | x[bt][7]) s4[1] = make_uint4(0, 0, 0, 0);
-                } else {
-#pragma unroll
-                    for (uint32_t q = 0; q < 8; q++)
-                        if (q < wq && x[bt][q]) src[q] = 0u;
-                }
-#pragma unroll
-                for (uint32_t q = 0; q < 8; q++) {
-                    if (q >= wq) continue;
-                    my[(32u * q + lane) * SP + tt] = transpose32(x[bt][q], lane);
-                }
-            }
+        uint64_t rest = tile - (uint64_t)jn * per_job;
+        const uint32_t tg = (uint32_t)(rest % tgroups);
+        rest /= tgroups;
+        const uint32_t wg = (uint32_t)(rest % wgroups);
+        rest /= wgroups;
+        const uint32_t i = (uint32_t)(rest % G.r), d = (uint32_t)(rest / G.r);
+        const uint32_t tc0 = tg * TC, w0 = wg * W;
+        // the tile's plane words into shared memory; the planes cleared
+        uint32_t *pbase = job.planes + ((uint64_t)d * G.g + 32u * tc0) * ps + (uint64_t)i * rw + w0;
+        for (uint32_t q = threadIdx.x; q < rows * W4; q += blockDim.x) {
+            const uint32_t row = q / W4, c = q - row * W4;
+            uint4 *src = reinterpret_cast<uint4 *>(pbase + (uint64_t)row * ps) + c;
+            const uint4 v = *src;
+            if (v.x | v.y | v.z | v.w) *src = make_uint4(0, 0, 0, 0);
+            reinterpret_cast<uint4 *>(in)[q] = v;  // row * W4 + c
         }
-        __syncwarp();
-        // OR the staged words into the estimators (32 wq of them, tc words
-        // each, contiguous in the DHLA when tc = wpc): four words per lane and
-        // step, four steps' loads issued before their stores
-        const uint32_t lt = tc == 8 ? 3u : tc == 4 ? 2u : tc == 2 ? 1u : 0u;  // log2 tc
-        const uint32_t quads = (32u * wq * tc) / 4u;
-        if (tc >= 4 && job.clean) {
-            // the DHLA words are zero: store the nonzero ones
-            for (uint32_t q = lane; q < quads; q += 32u) {
-                const uint32_t w = 4u * q, e = w >> lt, tt = w & (tc - 1u);
-                const uint32_t *m = my + e * SP + tt;
-                const uint4 v = make_uint4(m[0], m[1], m[2], m[3]);
-                if (v.x | v.y | v.z | v.w)
-                    *reinterpret_cast<uint4 *>(row + (uint64_t)(32u * w0 + e) * wpc + tc0 + tt) = v;
-            }
-        } else if (tc >= 4) {
-            for (uint32_t q0 = lane; q0 < quads; q0 += 128u) {
-                uint4 cur[4];
-                uint4 *dst[4];
+        __syncthreads();
+        if (tt < TC && w < W) {
+            uint32_t x[32];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t q = q0 + 32u * u;
-                    dst[u] = nullptr;
-                    if (q < quads) {
-                        const uint32_t w = 4u * q, e = w >> lt, tt = w & (tc - 1u);
-                        dst[u] = reinterpret_cast<uint4 *>(row + (uint64_t)(32u * w0 + e) * wpc + tc0 + tt);
-                        cur[u] = *dst[u];
+            for (uint32_t j = 0; j < 32; j++) x[j] = in[(32u * tt + j) * W + w];
+            transpose32_regs(x);
+#pragma unroll
+            for (uint32_t b = 0; b < 32; b++) out[(tt * 32u + b) * W + w] = x[b];
+        }
+        __syncthreads();
+        // estimator 32 (w0 + w) + b of row i gets words tc0 .. tc0 + TC - 1
+        uint32_t *row = job.grid + (uint64_t)d * G.dir_words + (uint64_t)i * G.row_words;
+        for (uint32_t e = threadIdx.x; e < 32u * W; e += blockDim.x) {
+            const uint32_t b = e / W, ww = e - b * W;
+            uint32_t v[kFoldTC];
+#pragma unroll
+            for (uint32_t t = 0; t < kFoldTC; t++) v[t] = t < TC ? out[(t * 32u + b) * W + ww] : 0u;
+            uint32_t *dst = row + (uint64_t)(32u * (w0 + ww) + b) * wpc + tc0;
+            if (TC == 8) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+                for (uint32_t h = 0; h < 2; h++) {
+                    uint4 nv = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+                    if (job.clean) {
+                        if (nv.x | nv.y | nv.z | nv.w) d4[h] = nv;
+                    } else if (nv.x | nv.y | nv.z | nv.w) {
+                        const uint4 c = d4[h];
+                        nv.x |= c.x; nv.y |= c.y; nv.z |= c.z; nv.w |= c.w;
+                        d4[h] = nv;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    if (!dst[u]) continue;
-                    const uint32_t w = 4u * (q0 + 32u * u), e = w >> lt, tt = w & (tc - 1u);
-                    const uint32_t *m = my + e * SP + tt;
-                    const uint4 v = make_uint4(cur[u].x | m[0], cur[u].y | m[1], cur[u].z | m[2], cur[u].w | m[3]);
-                    if (v.x != cur[u].x || v.y != cur[u].y || v.z != cur[u].z || v.w != cur[u].w) *dst[u] = v;
-                }
-            }
-        } else {
-            const uint32_t total = 32u * wq * tc;
-            for (uint32_t q = lane; q < total; q += 32u) {
-                const uint32_t e = q >> lt, tt = q & (tc - 1u);
-                const uint32_t v = my[e * SP + tt];
-                if (v) row[(uint64_t)(32u * w0 + e) * wpc + tc0 + tt] |= v;
+            } else {
+                for (uint32_t t = 0; t < TC; t++)
+                    if (v[t]) dst[t] = job.clean ? v[t] : (dst[t] | v[t]);
             }
         }
-        __syncwarp();
+        __syncthreads();  // the stages are rewritten by the next tile
     }
 }
 
@@ -741,16 +704,16 @@ cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry
 cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
                               int num_sms, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const size_t smem = (size_t)kFoldWarps * 256 * (kFoldTC + 1) * 4;
     int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldWarps * 32, smem, &per_sm);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldThreads, kFoldSmem, &per_sm);
     if (e != cudaSuccess) return e;
     const uint64_t rw = ((uint64_t)1 << G.k) >> 5;
-    const uint64_t tc = G.wpc < kFoldTC ? G.wpc : kFoldTC;
-    const uint64_t items = (uint64_t)G.dirs * G.r * (rw / (rw < 8 ? rw : 8)) * (G.wpc / tc) * njobs;
+    const uint64_t W = rw < kFoldW ? rw : kFoldW;
+    const uint64_t TC = G.wpc < kFoldTC ? G.wpc : kFoldTC;
+    const uint64_t tiles = (uint64_t)G.dirs * G.r * (rw / W) * (G.wpc / TC) * (jobs ? njobs : 1u);
     uint64_t blocks = (uint64_t)num_sms * per_sm;
-    if ((items + kFoldWarps - 1) / kFoldWarps < blocks) blocks = (items + kFoldWarps - 1) / kFoldWarps;
-    k_plane_fold<<<(unsigned)blocks, kFoldWarps * 32, smem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps);
+    if (tiles < blocks) blocks = tiles;
+    k_plane_fold<<<(unsigned)blocks, kFoldThreads, kFoldSmem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps);
     return cudaGetLastError();
 }
 
