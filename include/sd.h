@@ -163,8 +163,10 @@ typedef struct {
                                    direction SD_FLAG_OVERLOAD_CANDS, and a first
                                    stage above pair_cap tuples SD_FLAG_OVERLOAD_PAIRS.
                                 Both give the same K and the same report. */
-    uint32_t bin_batch_mib;  /* mode 5, sd_update_many: MiB of bins one batched round
-                                may use (bounds the links per round); default 8192 */
+    uint32_t bin_batch_mib;  /* sd_update_many driven by the handle: MiB of bins one
+                                batched round may use (mode 5: bounds the links per
+                                round; mode 6: bounds the lanes, bins of one plane
+                                round each, at most 4); default 8192 */
     uint32_t plane_tile_pairs; /* mode 6: pairs per binning tile: 1024, 2048, 4096 or 8192
                                   (within 200 KiB of shared memory: 8 dirs bytes per pair
                                   plus 16 bytes per plane) */
@@ -242,8 +244,11 @@ int sd_close_many(sd_handle *const *hs, uint32_t count, sd_report *outs, int *rc
  * take sd_update.
  *   hs[0] in mode 6: each member in mode 6 runs its plane rounds (of up to
  *   2^plane_round_log2 pairs of hs[0]'s tuning, with its own tile and unit)
- *   through hs[0]'s bins, one member after another; members in other modes
- *   take sd_update.
+ *   through the bins of one of hs[0]'s lanes: hs[0]'s stream and up to three
+ *   side streams of hs[0], each with bins of one round (as many lanes as
+ *   bin_batch_mib holds); members go to lanes largest first, each to the
+ *   lane with the fewest pairs so far, and a lane takes its members one
+ *   after another.  Members in other modes take sd_update.
  *   hs[0] in mode 5: rounds take members round-robin, each contributing up
  *   to 2^bin_chunk_log2 pairs, as many as hs[0]'s bin_batch_mib of bins
  *   holds at the round's largest share (and at most 4096 slices in all),
@@ -254,8 +259,8 @@ int sd_update_many(sd_handle *const *hs, const uint32_t *const *pairs, const uin
 
 /* Device bytes of the binned update's bins that h allocates, with its
  * current tuning: mode 6, the bins of one plane round (of
- * 2^plane_round_log2 pairs), for its own rounds and for every member's
- * rounds of a batch it drives (the plane copy is in sd_device_bytes); mode
+ * 2^plane_round_log2 pairs) for its own rounds, times the lanes of a batch
+ * of `links` members it drives (the plane copy is in sd_device_bytes); mode
  * 5, the slice bins of its own chunks (links <= 1) or of batched rounds
  * over `links` members (at most about bin_batch_mib MiB).  The bins grow to
  * the largest such need and are kept until sd_destroy.  0 when h does not

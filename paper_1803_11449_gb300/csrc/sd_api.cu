@@ -177,6 +177,8 @@ class HitBuf {
     size_t n_ = 0, cap_ = 0;
 };
 
+constexpr uint32_t kBatchLanes = 4;  // concurrent member lanes of a plane-mode sd_update_many
+
 struct sd_handle {
     sd_params p{};
     Geometry G{};
@@ -237,6 +239,12 @@ struct sd_handle {
     uint32_t *plane_ctr = nullptr;     // cnt, prev, binoff, cap, unit_start, ctl
     uint32_t *plane_bins = nullptr;
     uint64_t plane_bins_words = 0;
+    // a plane batch it drives: side streams, their bins and events (lane 0
+    // is the handle's own stream and bins)
+    cudaStream_t lane_stream[kBatchLanes - 1] = {};
+    uint32_t *lane_bins[kBatchLanes - 1] = {};
+    uint64_t lane_bins_words[kBatchLanes - 1] = {};
+    cudaEvent_t lane_ev[kBatchLanes] = {};
     PlaneArgs pa{};                    // counters and plane copy (bins, tile, unit set per round)
     bool planes_dirty = false;
     bool grid_clean = false;           // the DHLA is all zero (reset, then plane updates only)
@@ -454,6 +462,13 @@ static void release(sd_handle *h) {
     cudaFree(h->planes);
     cudaFree(h->plane_ctr);
     cudaFree(h->plane_bins);
+    for (uint32_t l = 0; l + 1 < kBatchLanes; l++) {
+        if (h->lane_stream[l]) cudaStreamSynchronize(h->lane_stream[l]);
+        cudaFree(h->lane_bins[l]);
+        if (h->lane_stream[l]) cudaStreamDestroy(h->lane_stream[l]);
+    }
+    for (uint32_t l = 0; l < kBatchLanes; l++)
+        if (h->lane_ev[l]) cudaEventDestroy(h->lane_ev[l]);
     cudaFree(h->part_d);
     cudaFreeHost(h->part_h);
     cudaFree(h->he_all);
@@ -891,13 +906,25 @@ static bool batch_layout(const sd_handle *h, BatchLayout *L) {
     return true;
 }
 
+// Lanes of a plane batch driven by d over `members` members: as many bin
+// buffers of one round as bin_batch_mib holds, at most kBatchLanes and one
+// per member.
+static uint32_t plane_batch_lanes(const sd_handle *d, uint64_t members) {
+    const uint64_t bytes = plane_bin_words(d->G, 1ull << d->T.plane_round_log2) * 4;
+    const uint64_t budget = (uint64_t)d->T.bin_batch_mib << 20;
+    uint64_t lanes = budget / std::max<uint64_t>(1, bytes);
+    lanes = std::min<uint64_t>(std::min<uint64_t>(lanes, kBatchLanes), members);
+    return (uint32_t)std::max<uint64_t>(1, lanes);
+}
+
 uint64_t sd_scratch_bytes(const sd_handle *h, uint32_t links) {
     if (!h) return 0;
     BinArgs B;
     uint64_t words = 0;
     // plane mode: the bins of one round, for the handle's own rounds and for
     // every member's rounds of a batch it drives
-    if (h->T.mode == 6) return plane_bin_words(h->G, 1ull << h->T.plane_round_log2) * 4;
+    if (h->T.mode == 6)
+        return plane_bin_words(h->G, 1ull << h->T.plane_round_log2) * 4 * (links <= 1 ? 1 : plane_batch_lanes(h, links));
     if ((h->T.mode != 5 && h->T.mode != 6) || !bin_layout(h, &B, &words)) return 0;
     if (links <= 1) return words * 4;
     BatchLayout L;
@@ -931,8 +958,30 @@ static bool batch_member(const sd_handle *d, const sd_handle *h, const uint32_t 
     return ok;
 }
 
+// Side lanes 1 .. lanes - 1 of d: a stream, an event and `words` of bins each.
+static int ensure_lanes(sd_handle *d, uint32_t lanes, uint64_t words) {
+    if (!d->lane_ev[0]) SD_CK(d, cudaEventCreateWithFlags(&d->lane_ev[0], cudaEventDisableTiming));
+    for (uint32_t l = 1; l < lanes; l++) {
+        if (!d->lane_stream[l - 1]) {
+            SD_CK(d, cudaStreamCreateWithFlags(&d->lane_stream[l - 1], cudaStreamNonBlocking));
+            SD_CK(d, cudaEventCreateWithFlags(&d->lane_ev[l], cudaEventDisableTiming));
+        }
+        if (d->lane_bins_words[l - 1] < words) {
+            SD_CK(d, cudaStreamSynchronize(d->lane_stream[l - 1]));
+            cudaFree(d->lane_bins[l - 1]);
+            d->lane_bins[l - 1] = nullptr;
+            d->lane_bins_words[l - 1] = 0;
+            SD_CK(d, cudaMalloc(&d->lane_bins[l - 1], words * 4));
+            d->lane_bins_words[l - 1] = words;
+        }
+    }
+    return SD_OK;
+}
+
 // sd_update_many with d in mode 6: each member in mode 6 runs its plane
-// rounds through d's bins on d's stream, one member after another.
+// rounds through one lane's bins on that lane's stream; the members are
+// dealt to the lanes largest first, each to the lane with the fewest pairs
+// so far, and each lane takes its members one after another.
 static int update_many_planes(sd_handle *const *hs, const uint32_t *const *pairs, const uint64_t *ns,
                               uint32_t count) {
     sd_handle *d = hs[0];
@@ -947,7 +996,10 @@ static int update_many_planes(sd_handle *const *hs, const uint32_t *const *pairs
     }
     if (batch.empty()) return SD_OK;
     const uint64_t round = 1ull << d->T.plane_round_log2;
-    int rc = ensure_plane_bins(d, plane_bin_words(d->G, round));
+    const uint64_t words = plane_bin_words(d->G, round);
+    const uint32_t lanes = plane_batch_lanes(d, batch.size());
+    int rc = ensure_plane_bins(d, words);
+    if (rc == SD_OK) rc = ensure_lanes(d, lanes, words);
     if (rc != SD_OK) return rc;
     // each member's state (zeroed on its own stream when new) and earlier
     // work come first
@@ -958,9 +1010,30 @@ static int update_many_planes(sd_handle *const *hs, const uint32_t *const *pairs
         SD_CK(h, cudaEventRecord(h->ev_batch, h->stream));
         SD_CK(d, cudaStreamWaitEvent(d->stream, h->ev_batch, 0));
     }
-    for (uint32_t q : batch) {
-        rc = plane_rounds(hs[q], pairs[q], ns[q], -1, d->plane_bins, d->plane_bins_words, round, d->stream, d);
+    std::vector<uint32_t> order(batch);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return ns[x] > ns[y]; });
+    std::vector<uint64_t> load(lanes, 0);
+    std::vector<uint32_t> lane_of(count, 0);
+    for (uint32_t q : order) {
+        const uint32_t l = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane_of[q] = l;
+        load[l] += ns[q];
+    }
+    if (lanes > 1) {
+        SD_CK(d, cudaEventRecord(d->lane_ev[0], d->stream));
+        for (uint32_t l = 1; l < lanes; l++) SD_CK(d, cudaStreamWaitEvent(d->lane_stream[l - 1], d->lane_ev[0], 0));
+    }
+    for (uint32_t q : order) {
+        const uint32_t l = lane_of[q];
+        cudaStream_t st = l ? d->lane_stream[l - 1] : d->stream;
+        uint32_t *bins = l ? d->lane_bins[l - 1] : d->plane_bins;
+        const uint64_t bw = l ? d->lane_bins_words[l - 1] : d->plane_bins_words;
+        rc = plane_rounds(hs[q], pairs[q], ns[q], -1, bins, bw, round, st, d);
         if (rc != SD_OK) return rc;
+    }
+    for (uint32_t l = 1; l < lanes; l++) {
+        SD_CK(d, cudaEventRecord(d->lane_ev[l], d->lane_stream[l - 1]));
+        SD_CK(d, cudaStreamWaitEvent(d->stream, d->lane_ev[l], 0));
     }
     // later work on each member waits for the batch
     SD_CK(d, cudaEventRecord(d->ev_batch, d->stream));

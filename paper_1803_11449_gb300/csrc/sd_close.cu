@@ -189,36 +189,67 @@ __device__ __forceinline__ void flush_hits(const RestoreArgs &A, uint32_t dir, u
     __syncwarp();
 }
 
-// The (c0, c1) tests of one c1 against the tile's c0 values for k >= 16 and
-// R rows (the inner loop of restore_body, specialised): a's low k bits are
-// L = c0 ^ c1; its high 32 - k bits are A0^-1 (c0 >> (2k - 32) - (A0 L >> k))
-// mod 2^(32-k), computed as one multiply by A0^-1 2^k; the low 2k - 32 bits
-// of c0 must match the top bits of A0 L mod 2^k; rows 2..R-1 are looked up
-// in the hot bitmap.  Candidates go to the warp's buffer.
-template <int R>
-__device__ __forceinline__ void restore_c1_k16(const Geometry &G, const RestoreArgs &A, uint32_t dir,
-                                               const uint32_t *s_c0, uint32_t nc0, const uint32_t *hot2, uint32_t nw,
-                                               uint32_t c1, bool jvalid, uint32_t A0, uint32_t A0inv,
-                                               uint32_t *cbuf, uint32_t &ccount, uint32_t lane) {
+// 32-bit load from shared memory at byte address `addr`.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// One (c0, c1) test for k >= 16 and R rows, the hot bitmap rows 2..R-1 in
+// shared memory at byte address hot2s (row i - 2 at + (i - 2) nw 4): a's low
+// k bits are L = c0 ^ c1; its high 32 - k bits are A0^-1 (c0 >> (2k - 32) -
+// (A0 L >> k)) mod 2^(32-k), computed as one multiply by A0^-1 2^k; unless
+// k = 16, the low 2k - 32 bits of c0 must also match the top bits of A0 L
+// mod 2^k.  Returns whether a is in K; a is set.
+template <int R, bool K16>
+__device__ __forceinline__ bool restore_test(uint32_t c0, uint32_t c1, uint32_t k, uint32_t kmask, uint32_t lowbits,
+                                             uint32_t lowmask, uint32_t A0, uint32_t A0inv_k, uint32_t hot2s,
+                                             uint32_t nw4, const uint32_t (&sh)[R > 2 ? R - 2 : 1], uint32_t &a) {
+    const uint32_t L = c0 ^ c1;
+    const uint32_t Q = A0 * L;
+    bool found = true;
+    if (K16) {
+        a = A0inv_k * (c0 - (Q >> 16)) + L;
+    } else {
+        a = A0inv_k * ((c0 >> lowbits) - (Q >> k)) + L;
+        found = ((Q & kmask) >> (32u - k)) == (c0 & lowmask);
+    }
+#pragma unroll
+    for (int i = 2; i < R; i++) {
+        const uint32_t ci = (shr_clamp(a, sh[i - 2]) & kmask) ^ c0;
+        const uint32_t word = lds_u32(hot2s + (uint32_t)(i - 2) * nw4 + ((ci >> 5) << 2));
+        found = found & ((word >> (ci & 31u)) & 1u);
+    }
+    return found;
+}
+
+// The tests of two c1 values per thread against the tile's c0 values, for
+// k >= 16 with the hot bitmap in shared memory; candidates go to the warp's
+// buffer.
+template <int R, bool K16>
+__device__ __forceinline__ void restore_c1x2(const Geometry &G, const RestoreArgs &A, uint32_t dir,
+                                             const uint32_t *s_c0, uint32_t nc0, uint32_t hot2s, uint32_t nw,
+                                             uint32_t c1a, bool va, uint32_t c1b, bool vb, uint32_t A0,
+                                             uint32_t A0inv, uint32_t *cbuf, uint32_t &ccount, uint32_t lane) {
     const uint32_t k = G.k, kmask = (1u << k) - 1u;
     const uint32_t lowbits = 2u * k - 32u, lowmask = (1u << lowbits) - 1u;
-    const uint32_t A0inv_k = A0inv << k;
+    const uint32_t A0inv_k = A0inv << k, nw4 = nw * 4u;
     uint32_t sh[R > 2 ? R - 2 : 1];
 #pragma unroll
     for (int i = 2; i < R; i++) sh[i - 2] = (uint32_t)(i - 1) * G.alpha;
+    const unsigned below = (1u << lane) - 1u;
     for (uint32_t q = 0; q < nc0; q++) {
         const uint32_t c0 = s_c0[q];  // same for the whole block
-        const uint32_t L = c0 ^ c1;
-        const uint32_t Q = A0 * L;
-        const uint32_t a = A0inv_k * ((c0 >> lowbits) - (Q >> k)) + L;
-        bool found = jvalid && (((Q & kmask) >> (32u - k)) == (c0 & lowmask));
-#pragma unroll
-        for (int i = 2; i < R; i++)
-            found = found & hot_at(hot2 + (uint32_t)(i - 2) * nw, (shr_clamp(a, sh[i - 2]) & kmask) ^ c0);
-        const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
-        if (!fb) continue;
-        if (found) cbuf[ccount + __popc(fb & ((1u << lane) - 1u))] = a;
-        ccount += __popc(fb);
+        uint32_t aa, ab;
+        const bool fa = va && restore_test<R, K16>(c0, c1a, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4, sh, aa);
+        const bool fb = vb && restore_test<R, K16>(c0, c1b, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4, sh, ab);
+        const unsigned ba = __ballot_sync(0xFFFFFFFFu, fa), bb = __ballot_sync(0xFFFFFFFFu, fb);
+        if (!(ba | bb)) continue;
+        if (fa) cbuf[ccount + __popc(ba & below)] = aa;
+        ccount += __popc(ba);
+        if (fb) cbuf[ccount + __popc(bb & below)] = ab;
+        ccount += __popc(bb);
         __syncwarp();
         if (ccount >= 32) flush_cands(A, dir, cbuf, ccount, lane);
     }
@@ -269,6 +300,10 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
     const uint32_t lowbits = (k >= 16u) ? (2u * k - 32u) : 0u;
     const uint32_t lowmask = (1u << lowbits) - 1u;
     const uint32_t iters = A.jchunk / blockDim.x;  // jchunk is a multiple of blockDim
+    // the specialised loop: k >= 16 (no enumeration of t), the hot bitmap in
+    // shared memory, at most 8 rows, an even number of c1 steps
+    const bool fast = k >= 16u && A.smem_hot && G.r <= 8u && (iters & 1u) == 0;
+    const uint32_t hot2s = (uint32_t)__cvta_generic_to_shared(smem);
 
     for (uint64_t t = t_begin; t < t_stop; t += t_step) {
         const uint32_t t0 = (uint32_t)(t / nchunk);
@@ -284,23 +319,37 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
         for (uint32_t q = threadIdx.x; q < nc0; q += blockDim.x) s_c0[q] = he0[c0_base + q];
         __syncthreads();
         if (s_stop) break;
+        if (fast) {
+            // two c1 values per thread and step (iters is even: jchunk = 2 blockDim)
+            for (uint32_t m = 0; m < iters; m += 2) {
+                const uint64_t ja = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
+                const uint64_t jb = ja + blockDim.x;
+                const bool va = ja < J, vb = jb < J;
+                const uint32_t c1a = va ? he1[(uint32_t)ja] : 0u, c1b = vb ? he1[(uint32_t)jb] : 0u;
+                switch (G.r * 2u + (k == 16u ? 1u : 0u)) {
+#define SD_RESTORE_CASE(RR)                                                                                       \
+    case 2 * RR: restore_c1x2<RR, false>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,         \
+                                        ccount, lane); break;                                                     \
+    case 2 * RR + 1: restore_c1x2<RR, true>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,      \
+                                           ccount, lane); break;
+                    SD_RESTORE_CASE(3)
+                    SD_RESTORE_CASE(4)
+                    SD_RESTORE_CASE(5)
+                    SD_RESTORE_CASE(6)
+                    SD_RESTORE_CASE(7)
+                    SD_RESTORE_CASE(8)
+#undef SD_RESTORE_CASE
+                    default: break;
+                }
+            }
+            continue;
+        }
         for (uint32_t m = 0; m < iters; m++) {
             const uint64_t j = jc * A.jchunk + (uint64_t)m * blockDim.x + threadIdx.x;
             const bool jvalid = j < J;
             const uint32_t i1 = (uint32_t)(j >> A.ulog);
             const uint32_t tt = (uint32_t)(j & ((1ull << A.ulog) - 1ull));
             const uint32_t c1 = jvalid ? he1[i1] : 0u;
-            if (k >= 16u && G.r <= 8u) {
-                switch (G.r) {
-                    case 3: restore_c1_k16<3>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                    case 4: restore_c1_k16<4>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                    case 5: restore_c1_k16<5>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                    case 6: restore_c1_k16<6>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                    case 7: restore_c1_k16<7>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                    default: restore_c1_k16<8>(G, A, dir, s_c0, nc0, hot2, nw, c1, jvalid, A0, A0inv, cbuf, ccount, lane); break;
-                }
-                continue;
-            }
             for (uint32_t q = 0; q < nc0; q++) {
                 const uint32_t c0 = s_c0[q];  // same for the whole block
                 const uint32_t L = c0 ^ c1;                 // BL(1): the low k bits of a
@@ -334,7 +383,7 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
 
 // The tiles of direction 0 (tiles0 of them), then those of direction 1,
 // dealt round-robin to the blocks of a 1-D grid.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_restore(Geometry G, RestoreArgs A, uint64_t tiles0) {
     restore_body(G, A, 0, blockIdx.x, ~0ull, gridDim.x);
     if (G.dirs > 1) {
@@ -796,7 +845,7 @@ __device__ __forceinline__ uint32_t segment_of(const unsigned long long *base, u
 // Every block takes a contiguous run of the jobs' restore tiles (tile_base:
 // host-computed tile offsets per segment), so that blocks share the work of
 // the jobs in proportion to their tiles.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_restore_many(const CloseJob *__restrict__ J, const unsigned long long *__restrict__ tile_base, uint32_t count) {
     const uint64_t total = tile_base[2 * count];
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
@@ -935,7 +984,7 @@ cudaError_t launch_compact(const uint32_t *hotmap, const Geometry &G, uint32_t *
 void prepare_restore(const Geometry &G, RestoreArgs &A, int num_sms, uint32_t tiles_per_block) {
     const unsigned threads = 256;
     A.ulog = (G.k >= 16u) ? 0u : (32u - 2u * G.k);
-    A.jchunk = threads;
+    A.jchunk = 2 * threads;  // two c1 values per thread and step
     uint64_t tests = 0;
     for (uint32_t d = 0; d < G.dirs; d++)
         if (A.run[d]) tests += (uint64_t)A.n0[d] * ((uint64_t)A.n1[d] << A.ulog);

@@ -71,9 +71,10 @@ class Server:
     bytes; bin_chunk_log2 sets the most pairs a link gives one binned round.
     The update is the library's default for the shape (mode 6, binned by
     bit plane, where one plane fits; `mode=5` asks for the slice binning):
-    in mode 6 each link's rounds run in turn through the driver's bins of
-    one round; in mode 5 a round takes as many links as bin_bytes of bins
-    (default: half the budget) hold at their actual shares."""
+    in mode 6 the links' rounds run on up to four lanes, each with the bins
+    of one round (as many lanes as bin_bytes holds); in mode 5 a round
+    takes as many links as bin_bytes of bins (default: half the budget)
+    hold at their actual shares."""
 
     def __init__(self, workload, window_pairs: int, hbm_budget: int, device: int = 0,
                  bin_chunk_log2: int = 22, bin_bytes: int | None = None, cand_cap: int = 1 << 18,
@@ -126,7 +127,7 @@ class Server:
     # ---------------------------------------------------------- admission
     def _tune(self, h, **extra):
         if self.mode == 6:
-            sd.sd_set_tuning(h, mode=6, plane_round_log2=self.bin_chunk_log2)
+            sd.sd_set_tuning(h, mode=6, plane_round_log2=self.bin_chunk_log2, **extra)
         else:
             sd.sd_set_tuning(h, mode=5, bin_chunk_log2=self.bin_chunk_log2, **extra)
 

@@ -44,7 +44,8 @@ def _same_report(rep, ref, dirs):
 @pytest.mark.parametrize("tuning", [dict(mode=5), dict(mode=5, bin_chunk_log2=17), dict(mode=1),
                                     dict(mode=5, bin_batch_mib=1), dict(mode=5, bin_chunk_log2=14, bin_batch_mib=4),
                                     dict(mode=6), dict(mode=6, plane_round_log2=14),
-                                    dict(mode=6, plane_round_log2=16, plane_tile_pairs=1024)])
+                                    dict(mode=6, plane_round_log2=16, plane_tile_pairs=1024),
+                                    dict(mode=6, bin_batch_mib=1)])
 def test_batched_links_equal_each_link_alone(sd, O, tuning):
     """Seven links of uneven sizes (one of them much larger than a round's
     share), each with its own traffic and its own hash seed."""
