@@ -202,13 +202,13 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
 // (A0 L >> k)) mod 2^(32-k), computed as one multiply by A0^-1 2^k; unless
 // k = 16, the low 2k - 32 bits of c0 must also match the top bits of A0 L
 // mod 2^k.  Returns whether a is in K; a is set.
-template <int R, bool K16>
+template <int R, bool K16, int ALPHA>
 __device__ __forceinline__ bool restore_test(uint32_t c0, uint32_t c1, uint32_t k, uint32_t kmask, uint32_t lowbits,
                                              uint32_t lowmask, uint32_t A0, uint32_t A0inv_k, uint32_t hot2s,
                                              uint32_t nw4, const uint32_t (&sh)[R > 2 ? R - 2 : 1], uint32_t &a) {
     const uint32_t L = c0 ^ c1;
     const uint32_t Q = A0 * L;
-    bool found = true;
+    uint32_t found = 1u;
     if (K16) {
         a = A0inv_k * (c0 - (Q >> 16)) + L;
     } else {
@@ -217,17 +217,20 @@ __device__ __forceinline__ bool restore_test(uint32_t c0, uint32_t c1, uint32_t 
     }
 #pragma unroll
     for (int i = 2; i < R; i++) {
-        const uint32_t ci = (shr_clamp(a, sh[i - 2]) & kmask) ^ c0;
-        const uint32_t word = lds_u32(hot2s + (uint32_t)(i - 2) * nw4 + ((ci >> 5) << 2));
-        found = found & ((word >> (ci & 31u)) & 1u);
+        // with k = 16 and a compile-time alpha the shifts and masks are constants
+        const uint32_t s = ALPHA ? (uint32_t)((i - 1) * ALPHA) : sh[i - 2];
+        const uint32_t m = K16 ? 0xFFFFu : kmask;
+        const uint32_t ci = (ALPHA && s >= 32u ? 0u : (ALPHA ? (a >> (s & 31u)) : shr_clamp(a, s))) & m ^ c0;
+        const uint32_t word = lds_u32(hot2s + (uint32_t)(i - 2) * nw4 + ((ci >> 3) & ~3u));
+        found &= word >> (ci & 31u);
     }
-    return found;
+    return found & 1u;
 }
 
 // The tests of two c1 values per thread against the tile's c0 values, for
 // k >= 16 with the hot bitmap in shared memory; candidates go to the warp's
 // buffer.
-template <int R, bool K16>
+template <int R, bool K16, int ALPHA>
 __device__ __forceinline__ void restore_c1x2(const Geometry &G, const RestoreArgs &A, uint32_t dir,
                                              const uint32_t *s_c0, uint32_t nc0, uint32_t hot2s, uint32_t nw,
                                              uint32_t c1a, bool va, uint32_t c1b, bool vb, uint32_t A0,
@@ -242,8 +245,10 @@ __device__ __forceinline__ void restore_c1x2(const Geometry &G, const RestoreArg
     for (uint32_t q = 0; q < nc0; q++) {
         const uint32_t c0 = s_c0[q];  // same for the whole block
         uint32_t aa, ab;
-        const bool fa = va && restore_test<R, K16>(c0, c1a, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4, sh, aa);
-        const bool fb = vb && restore_test<R, K16>(c0, c1b, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4, sh, ab);
+        const bool fa = va && restore_test<R, K16, ALPHA>(c0, c1a, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4,
+                                                           sh, aa);
+        const bool fb = vb && restore_test<R, K16, ALPHA>(c0, c1b, k, kmask, lowbits, lowmask, A0, A0inv_k, hot2s, nw4,
+                                                           sh, ab);
         const unsigned ba = __ballot_sync(0xFFFFFFFFu, fa), bb = __ballot_sync(0xFFFFFFFFu, fb);
         if (!(ba | bb)) continue;
         if (fa) cbuf[ccount + __popc(ba & below)] = aa;
@@ -326,12 +331,17 @@ __device__ __forceinline__ void restore_body(const Geometry &G, const RestoreArg
                 const uint64_t jb = ja + blockDim.x;
                 const bool va = ja < J, vb = jb < J;
                 const uint32_t c1a = va ? he1[(uint32_t)ja] : 0u, c1b = vb ? he1[(uint32_t)jb] : 0u;
+                if (G.r == 4u && k == 16u && G.alpha == 8u) {  // the core-link sketch
+                    restore_c1x2<4, true, 8>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,
+                                             ccount, lane);
+                    continue;
+                }
                 switch (G.r * 2u + (k == 16u ? 1u : 0u)) {
 #define SD_RESTORE_CASE(RR)                                                                                       \
-    case 2 * RR: restore_c1x2<RR, false>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,         \
-                                        ccount, lane); break;                                                     \
-    case 2 * RR + 1: restore_c1x2<RR, true>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,      \
-                                           ccount, lane); break;
+    case 2 * RR: restore_c1x2<RR, false, 0>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,      \
+                                           ccount, lane); break;                                                  \
+    case 2 * RR + 1: restore_c1x2<RR, true, 0>(G, A, dir, s_c0, nc0, hot2s, nw, c1a, va, c1b, vb, A0, A0inv, cbuf,   \
+                                              ccount, lane); break;
                     SD_RESTORE_CASE(3)
                     SD_RESTORE_CASE(4)
                     SD_RESTORE_CASE(5)
