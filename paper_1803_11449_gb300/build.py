@@ -22,7 +22,7 @@ LIB = os.path.join(OUT_DIR, "libsd.so")
 # roofline lines); a library of its own, not part of the detection API
 CEILINGS_SRC = "sd_ceilings.cu"
 CEILINGS_LIB = os.path.join(OUT_DIR, "libsd_ceilings.so")
-SOURCES = ["sd_update.cu", "sd_binned.cu", "sd_plane.cu", "sd_close.cu", "sd_join.cu", "sd_shard.cu",
+SOURCES = ["sd_update.cu", "sd_binned.cu", "sd_plane.cu", "sd_fold.cu", "sd_close.cu", "sd_join.cu", "sd_shard.cu",
            "sd_api.cu", "sd_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "sd_common.cuh"), os.path.join(INCLUDE, "sd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

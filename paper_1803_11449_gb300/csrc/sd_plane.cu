@@ -31,10 +31,9 @@
 //                  (cp.reduce.async.bulk ... .or.b32, so units of one plane
 //                  may run on several SMs).  The last block lays out the
 //                  next round's bins from this round's counts.
-//   k_plane_fold   (window close, sd_get_grid, sd_merge) transposes the
-//                  plane-major copy into the estimator-major DHLA
-//                  (grid |= planes^T: tiles read with coalesced loads, 32 x
-//                  32 bit blocks transposed in registers) and clears it.
+//   k_plane_fold   (sd_fold.cu; window close, sd_get_grid, sd_merge) folds
+//                  the plane-major copy into the estimator-major DHLA
+//                  (grid |= planes^T) and clears it.
 //
 // Per pair this moves dirs keys (4 bytes each) through the bins instead of
 // r * dirs bit positions, and the plane copy is swept once per round by
@@ -501,162 +500,6 @@ k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf, uint32_t per_block) {
     write_layout(P, true, s_warp);
 }
 
-// ------------------------------------------------------------------- fold
-// One block per tile: TC groups of 32 planes (32 TC consecutive bits of
-// every estimator of a row) times W consecutive words of one row of those
-// planes (32 W estimators).  The tile is copied with coalesced 16-byte
-// asynchronous copies into shared memory (and its plane words cleared);
-// each thread (t, w)
-// transposes the 32 x 32 bit block of plane group t at word w in registers
-// (32 words of 32 planes -> word t of 32 estimators); the results are
-// staged by (t, estimator) and each estimator's TC words are written to the
-// DHLA with one or two vector stores.  A DHLA known to be all zero ("clean")
-// is written without being read.
-constexpr uint32_t kFoldThreads = 256;
-constexpr uint32_t kFoldTC = 8;   // estimator words (groups of 32 planes) per tile
-constexpr uint32_t kFoldW = 32;   // plane words per tile
-constexpr size_t kFoldSmem = (size_t)2 * 32 * kFoldTC * kFoldW * 4;  // two tile stages
-
-// 32 x 32 bit transpose in registers: afterwards bit j of x[b] is what was
-// bit b of x[j] (block swaps of 16, 8, 4, 2 and 1 bits).
-__device__ __forceinline__ void transpose32_regs(uint32_t (&x)[32]) {
-#pragma unroll
-    for (int s = 0; s < 5; s++) {
-        const uint32_t j = 16u >> s;
-        const uint32_t m = s == 0 ? 0x0000FFFFu : s == 1 ? 0x00FF00FFu : s == 2 ? 0x0F0F0F0Fu
-                         : s == 3 ? 0x33333333u : 0x55555555u;
-#pragma unroll
-        for (uint32_t r = 0; r < 32; r++) {
-            if (r & j) continue;
-            const uint32_t t = ((x[r] >> j) ^ x[r + j]) & m;
-            x[r] ^= t << j;
-            x[r + j] ^= t;
-        }
-    }
-}
-
-// Where tile `tile` of a fold lies: its job, direction, row, first plane
-// group and first plane word.
-struct FoldTile {
-    FoldJob job;
-    uint32_t d, i, tc0, w0;
-};
-__device__ __forceinline__ FoldTile fold_tile(uint64_t tile, uint64_t per_job, uint32_t tgroups, uint32_t wgroups,
-                                              uint32_t TC, uint32_t W, const Geometry &G, const FoldJob &one,
-                                              const FoldJob *jobs) {
-    FoldTile f;
-    const uint32_t jn = (uint32_t)(tile / per_job);
-    f.job = jobs ? jobs[jn] : one;
-    uint64_t rest = tile - (uint64_t)jn * per_job;
-    f.tc0 = (uint32_t)(rest % tgroups) * TC;
-    rest /= tgroups;
-    f.w0 = (uint32_t)(rest % wgroups) * W;
-    rest /= wgroups;
-    f.i = (uint32_t)(rest % G.r);
-    f.d = (uint32_t)(rest / G.r);
-    return f;
-}
-
-// Folds of several handles of one shape run as one launch (the batched
-// close): the tiles of job j follow those of job j - 1.  Two tile stages:
-// the next tile's plane words are copied in (cp.async) while the current
-// one is transposed; the transposed words are staged in place of the
-// current tile's input.
-__global__ void __launch_bounds__(kFoldThreads, 3)
-k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geometry G, uint32_t ps) {
-    extern __shared__ uint4 fold_smem[];
-    uint32_t *const stage0 = reinterpret_cast<uint32_t *>(fold_smem);
-    constexpr uint32_t kStageWords = 32 * kFoldTC * kFoldW;
-    const uint32_t wpc = G.wpc;
-    const uint32_t TC = wpc < kFoldTC ? wpc : kFoldTC;
-    const uint32_t rw = (1u << G.k) >> 5;  // plane words per row
-    const uint32_t W = rw < kFoldW ? rw : kFoldW;
-    const uint32_t wgroups = rw / W, tgroups = wpc / TC;
-    const uint64_t per_job = (uint64_t)G.dirs * G.r * wgroups * tgroups;
-    const uint64_t tiles = per_job * njobs;
-    const uint32_t W4 = W / 4, rows = 32u * TC;
-    const uint32_t tt = threadIdx.x >> 5, w = threadIdx.x & 31u;
-    // a tile's first plane word
-    auto plane_base = [&](const FoldTile &f) {
-        return f.job.planes + ((uint64_t)f.d * G.g + 32u * f.tc0) * ps + (uint64_t)f.i * rw + f.w0;
-    };
-    // start copying tile `tile` into stage s (one commit group per call)
-    auto issue = [&](uint64_t tile, uint32_t s) {
-        if (tile < tiles) {
-            const FoldTile f = fold_tile(tile, per_job, tgroups, wgroups, TC, W, G, one, jobs);
-            const uint32_t *pb = plane_base(f);
-            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(stage0 + s * kStageWords);
-            for (uint32_t q = threadIdx.x; q < rows * W4; q += blockDim.x) {
-                const uint32_t row = q / W4, c = q - row * W4;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             ::"r"(sa + 16u * q), "l"(pb + (uint64_t)row * ps + 4u * c)
-                             : "memory");
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    uint32_t cur = 0;
-    issue(blockIdx.x, 0);
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, cur ^= 1u) {
-        issue(tile + gridDim.x, cur ^ 1u);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are done
-        __syncthreads();
-        const FoldTile f = fold_tile(tile, per_job, tgroups, wgroups, TC, W, G, one, jobs);
-        uint32_t *in = stage0 + cur * kStageWords;
-        // clear the tile's plane words that hold bits
-        uint32_t *pb = plane_base(f);
-        for (uint32_t q = threadIdx.x; q < rows * W4; q += blockDim.x) {
-            const uint4 v = reinterpret_cast<const uint4 *>(in)[q];
-            if (v.x | v.y | v.z | v.w) {
-                const uint32_t row = q / W4, c = q - row * W4;
-                *reinterpret_cast<uint4 *>(pb + (uint64_t)row * ps + 4u * c) = make_uint4(0, 0, 0, 0);
-            }
-        }
-        uint32_t x[32];
-        const bool mine = tt < TC && w < W;
-        if (mine) {
-#pragma unroll
-            for (uint32_t j = 0; j < 32; j++) x[j] = in[(32u * tt + j) * W + w];
-            transpose32_regs(x);
-        }
-        __syncthreads();  // every read of the input stage is done
-        uint32_t *out = in;  // [TC][32 bits][W words]
-        if (mine) {
-#pragma unroll
-            for (uint32_t b = 0; b < 32; b++) out[(tt * 32u + b) * W + w] = x[b];
-        }
-        __syncthreads();
-        // estimator 32 (w0 + w) + b of row i gets words tc0 .. tc0 + TC - 1
-        uint32_t *row = f.job.grid + (uint64_t)f.d * G.dir_words + (uint64_t)f.i * G.row_words;
-        for (uint32_t e = threadIdx.x; e < 32u * W; e += blockDim.x) {
-            const uint32_t b = e / W, ww = e - b * W;
-            uint32_t v[kFoldTC];
-#pragma unroll
-            for (uint32_t t = 0; t < kFoldTC; t++) v[t] = t < TC ? out[(t * 32u + b) * W + ww] : 0u;
-            uint32_t *dst = row + (uint64_t)(32u * (f.w0 + ww) + b) * wpc + f.tc0;
-            if (TC == 8) {
-                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-#pragma unroll
-                for (uint32_t h = 0; h < 2; h++) {
-                    uint4 nv = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
-                    if (f.job.clean) {
-                        if (nv.x | nv.y | nv.z | nv.w) d4[h] = nv;
-                    } else if (nv.x | nv.y | nv.z | nv.w) {
-                        const uint4 c = d4[h];
-                        nv.x |= c.x; nv.y |= c.y; nv.z |= c.z; nv.w |= c.w;
-                        d4[h] = nv;
-                    }
-                }
-            } else {
-                for (uint32_t t = 0; t < TC; t++)
-                    if (v[t]) dst[t] = f.job.clean ? v[t] : (dst[t] | v[t]);
-            }
-        }
-        __syncthreads();  // the stage is refilled two tiles on
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 // --------------------------------------------------------------- launchers
 size_t plane_bin_smem_bytes(uint32_t tile_pairs, uint32_t dirs, uint32_t nbins) {
     return (size_t)dirs * tile_pairs * 8 + (size_t)nbins * 16;
@@ -749,20 +592,5 @@ cudaError_t launch_plane_round(const uint32_t *pairs, uint64_t n, const Geometry
     }
 }
 
-cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
-                              int num_sms, cudaStream_t s) {
-    if (njobs == 0) return cudaSuccess;
-    int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldThreads, kFoldSmem, &per_sm);
-    if (e != cudaSuccess) return e;
-    const uint64_t rw = ((uint64_t)1 << G.k) >> 5;
-    const uint64_t W = rw < kFoldW ? rw : kFoldW;
-    const uint64_t TC = G.wpc < kFoldTC ? G.wpc : kFoldTC;
-    const uint64_t tiles = (uint64_t)G.dirs * G.r * (rw / W) * (G.wpc / TC) * (jobs ? njobs : 1u);
-    uint64_t blocks = (uint64_t)num_sms * per_sm;
-    if (tiles < blocks) blocks = tiles;
-    k_plane_fold<<<(unsigned)blocks, kFoldThreads, kFoldSmem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps);
-    return cudaGetLastError();
-}
 
 }  // namespace sd
