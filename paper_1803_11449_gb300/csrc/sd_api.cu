@@ -520,6 +520,10 @@ static int create_impl(const sd_params *p, sd_handle *h) {
     // window, against 0.79 ms at 4096 / 2^24 and 1.2 ms at 2048 / 2^24);
     // 4096-pair tiles where 8192 would not fit shared memory
     if (plane_fits(G)) h->T.mode = 6;
+    // apply units of at least twice a plane's words in keys: every unit ORs
+    // its whole plane into the plane copy, which for planes beyond 32 KiB
+    // (k >= 18: a copy larger than L2) goes to DRAM
+    h->T.plane_unit_log2 = std::max<uint32_t>(14u, ilog2(plane_words(G)) + 1u);
     if (plane_bin_smem_bytes(h->T.plane_tile_pairs, G.dirs, G.dirs * G.g) > 200 * 1024) h->T.plane_tile_pairs = 4096;
     h->zhot = zhot_of(p->g, p->theta);
     resolve_caps(p, &h->pair_cap, &h->cand_cap, &h->hits_cap, &h->report_cap, &h->stage_pairs);
