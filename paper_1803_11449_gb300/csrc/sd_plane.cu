@@ -51,7 +51,7 @@ namespace sd {
 namespace {
 
 constexpr uint32_t kPlaneThreads = 512;   // k_plane_bin / k_plane_count block
-constexpr uint32_t kApplyThreads = 512;   // k_plane_apply block
+constexpr uint32_t kApplyThreads = 512;   // k_plane_apply block (1024 where one plane fills the block's shared memory)
 constexpr uint32_t kHeldReservations = 2;  // reservation results a thread holds across the scatter
 constexpr uint32_t kBinTilesPerBlock = 8;   // k_plane_bin tiles per block (blocks retire as a round runs)
 constexpr uint32_t kApplyUnitsPerBlock = 4; // k_plane_apply units per block
@@ -425,9 +425,10 @@ __device__ __forceinline__ void apply_key(uint32_t *pl, const Geometry &G, uint3
 // memory) a unit is applied in one buffer while the bulk reduction of the
 // previous unit still reads the other; before a buffer is reused, its
 // reduction must have finished reading it (wait_group.read allows one
-// reduction, the other buffer's, to stay in flight).
-template <int R>
-__global__ void __launch_bounds__(kApplyThreads)
+// reduction, the other buffer's, to stay in flight).  Planes too large for
+// two buffers leave one block per SM, which then runs 1024 threads.
+template <int R, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 k_plane_apply(Geometry G, PlaneArgs P, uint32_t nbuf, uint32_t per_block) {
     extern __shared__ uint4 pl4_all[];  // nbuf planes of ps words
     __shared__ uint32_t s_unit;
@@ -541,11 +542,12 @@ static cudaError_t launch_plane_bin_d(const uint32_t *pairs, uint64_t n, const G
 template <int R>
 static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, uint64_t n, int num_sms,
                                      cudaStream_t s) {
-    auto kern = k_plane_apply<R>;
     const uint32_t nbuf = (size_t)P.ps * 8 <= (size_t)100 * 1024 ? 2u : 1u;
+    auto kern = nbuf == 2 ? k_plane_apply<R, kApplyThreads> : k_plane_apply<R, 2 * kApplyThreads>;
+    const uint32_t threads = nbuf == 2 ? kApplyThreads : 2 * kApplyThreads;
     const size_t smem = (size_t)P.ps * 4 * nbuf;
     int per_sm = 0;
-    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)kApplyThreads, smem, &per_sm);
+    cudaError_t e = prepare_launch(reinterpret_cast<const void *>(kern), (int)threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     // units of the round: at most (keys + slack) / unit + one partial unit per plane
     const uint64_t keys = (uint64_t)(P.nbins / G.g) * n;
@@ -554,7 +556,7 @@ static cudaError_t launch_plane_apply(const Geometry &G, const PlaneArgs &P, uin
     uint64_t blocks = (most + per_block - 1) / per_block;
     if (blocks < (uint64_t)num_sms * per_sm) blocks = (uint64_t)num_sms * per_sm;
     if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    kern<<<(unsigned)blocks, kApplyThreads, smem, s>>>(G, P, nbuf, per_block);
+    kern<<<(unsigned)blocks, threads, smem, s>>>(G, P, nbuf, per_block);
     return cudaGetLastError();
 }
 
