@@ -742,7 +742,7 @@ static int plane_rounds(sd_handle *h, const uint32_t *pairs, uint64_t n, int dir
 // plane-binned mode are pending.
 static int fold_planes(sd_handle *h) {
     if (!h->planes_dirty) return SD_OK;
-    const FoldJob job{h->grid, h->planes, h->grid_clean ? 1u : 0u, 0u};
+    const FoldJob job{h->grid, h->planes, h->grid_clean ? 1u : 0u, h->zhot, nullptr, nullptr};
     SD_CK(h, launch_plane_fold(job, nullptr, 1, h->G, h->pa.ps, h->num_sms, h->stream));
     launched(1);
     h->planes_dirty = false;
@@ -1222,11 +1222,21 @@ static int close_phase_a(sd_handle *h, sd_report *out) {
     std::memset(&h->cs, 0, sizeof h->cs);
     h->report.clear();
     h->last_ncand[0] = h->last_ncand[1] = 0;
-    const int frc = fold_planes(h);
-    if (frc != SD_OK) return frc;
-    SD_CK(h, launch_row_stats(h->grid, h->G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
+    if (h->planes_dirty && fold_stats_fit(h->G)) {
+        // the fold writes the row statistics as it goes
+        const FoldJob job{h->grid, h->planes, h->grid_clean ? 1u : 0u, h->zhot, h->st_d, h->hotmap};
+        SD_CK(h, launch_plane_fold(job, nullptr, 1, h->G, h->pa.ps, h->num_sms, h->stream));
+        launched(1);
+        h->planes_dirty = false;
+        h->grid_clean = false;
+    } else {
+        const int frc = fold_planes(h);
+        if (frc != SD_OK) return frc;
+        SD_CK(h, launch_row_stats(h->grid, h->G, h->zhot, h->hotmap, h->st_d, h->num_sms, h->stream));
+        launched(1);
+    }
     SD_CK(h, launch_compact(h->hotmap, h->G, h->he, 2, h->stream));
-    launched(2);
+    launched(1);
     SD_CK(h, cudaMemcpyAsync(h->st_h, h->st_d, sizeof(StatBlock), cudaMemcpyDeviceToHost, h->stream));
     return SD_OK;
 }
@@ -1554,11 +1564,17 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
     // phase A: row statistics and HE(0), HE(1) of every window (pending
     // plane-binned updates folded into each DHLA first, all in one launch
     // on the driver's stream, which is ordered after every member's work)
+    // (with the row statistics where the shape allows: those members skip
+    // k_row_stats_many)
     uint32_t nfold = 0;
+    const bool fold_stats = fold_stats_fit(G);
+    std::vector<char> folded(count, 0);
     for (uint32_t i = 0; i < count; i++) {
         sd_handle *h = hs[i];
         if (!h->planes_dirty) continue;
-        d->fj_h[nfold++] = FoldJob{h->grid, h->planes, h->grid_clean ? 1u : 0u, 0u};
+        d->fj_h[nfold++] = FoldJob{h->grid, h->planes, h->grid_clean ? 1u : 0u, h->zhot,
+                                   fold_stats ? h->st_d : nullptr, fold_stats ? h->hotmap : nullptr};
+        folded[i] = fold_stats;
         h->planes_dirty = false;
         h->grid_clean = false;
     }
@@ -1581,6 +1597,7 @@ static int close_many_batched(sd_handle *const *hs, uint32_t count, sd_report *o
         j.A.hotmap = h->hotmap;
         j.A.stats = h->st_d;
         j.zhot = h->zhot;
+        j.stats_done = folded[i];
         rcs[i] = SD_OK;
     }
     SD_CK(d, cudaMemcpyAsync(d->cj_d, d->cj_h, count * sizeof(CloseJob), cudaMemcpyHostToDevice, s));

@@ -831,6 +831,7 @@ __global__ void k_merge_or(uint4 *dst, const uint4 *__restrict__ src, uint64_t n
 // The same kernels over an array of jobs, one grid dimension per job.
 __global__ void __launch_bounds__(256) k_row_stats_many(const CloseJob *__restrict__ J) {
     const CloseJob &j = J[blockIdx.y];
+    if (j.stats_done) return;  // the job's fold wrote its statistics
     row_stats_body(j.A.grid, j.G, j.zhot, const_cast<uint32_t *>(j.A.hotmap), j.A.stats, blockIdx.x, gridDim.x);
 }
 

@@ -144,7 +144,7 @@ struct CloseJob {
     Geometry G;
     RestoreArgs A;
     int zhot;
-    int pad;
+    int stats_done;  // the fold already wrote the row statistics
 };
 
 // The staged join of sd_join.cu (the paper's Algorithms 3 and 4).
@@ -278,13 +278,20 @@ cudaError_t launch_partition(const uint32_t *pairs, uint64_t n, uint32_t dir, ui
                              unsigned long long *counts, unsigned long long *cursor, uint32_t *out, int num_sms,
                              cudaStream_t s, bool scatter);
 // One handle's fold: grid |= planes^T (grid = planes^T where `clean`: the
-// DHLA is all zero), planes = 0.
+// DHLA is all zero), planes = 0; with `st` (the window close, where
+// fold_stats_fit), also the row statistics of k_row_stats: ZR and |HE(i)|
+// added to st, every hot bitmap word written.
 struct FoldJob {
     uint32_t *grid;
     uint32_t *planes;
     uint32_t clean;
-    uint32_t pad;
+    int zhot;
+    StatBlock *st;       // nullptr: no statistics
+    uint32_t *hotmap;    // [dirs][r][2^k/32]
 };
+// Whether a fold can compute the row statistics: tiles then hold every bit
+// of their estimators (g/32 words of 8, 16 or 32).
+inline bool fold_stats_fit(const Geometry &G) { return G.wpc >= 8 && G.wpc <= 32; }
 // `one`'s fold, or (jobs != nullptr) the folds of njobs device-resident jobs
 cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
                               int num_sms, cudaStream_t s);

@@ -17,17 +17,23 @@ namespace sd {
 // ------------------------------------------------------------------- fold
 // One block per tile: TC groups of 32 planes (32 TC consecutive bits of
 // every estimator of a row) times W consecutive words of one row of those
-// planes (32 W estimators).  The tile is copied with coalesced 16-byte
-// asynchronous copies into shared memory (and its plane words cleared);
-// each thread (t, w) transposes the 32 x 32 bit block of plane group t at
-// word w in registers (32 words of 32 planes -> word t of 32 estimators);
-// the results are staged by (t, estimator) and each estimator's TC words
-// are written to the DHLA with one or two vector stores.  A DHLA known to be all zero ("clean")
-// is written without being read.
+// planes (32 W estimators), 32 TC W = 8192 words at most.  The tile is
+// copied with coalesced 16-byte asynchronous copies into shared memory (and
+// its plane words cleared); each thread (t, w) transposes the 32 x 32 bit
+// block of plane group t at word w in registers (32 words of 32 planes ->
+// word t of 32 estimators); the results are staged by (t, estimator) and
+// each estimator's TC words are written to the DHLA with vector stores.  A
+// DHLA known to be all zero ("clean") is written without being read.
+//
+// Shapes: TC = min(8, g/32), W = min(32, 2^k/32); or, when the fold also
+// computes the row statistics, TC = g/32 (8, 16 or 32: the tile holds every
+// bit of its estimators) and W = 256 / TC.  With statistics each estimator's
+// z_0 = g - popcount is tested against zhot, its hot bit goes to the tile's
+// W hot bitmap words (written whole), and the tile adds its sum of z_0 and
+// its hot count to ZR(i) and |HE(i)| -- what k_row_stats computes.
 constexpr uint32_t kFoldThreads = 256;
-constexpr uint32_t kFoldTC = 8;   // estimator words (groups of 32 planes) per tile
-constexpr uint32_t kFoldW = 32;   // plane words per tile
-constexpr size_t kFoldSmem = (size_t)2 * 32 * kFoldTC * kFoldW * 4;  // two tile stages
+constexpr uint32_t kFoldTile = 8192;  // words per tile stage (32 TC W)
+constexpr size_t kFoldSmem = (size_t)2 * kFoldTile * 4;  // two tile stages
 
 // 32 x 32 bit transpose in registers: afterwards bit j of x[b] is what was
 // bit b of x[j] (block swaps of 16, 8, 4, 2 and 1 bits).
@@ -69,25 +75,37 @@ __device__ __forceinline__ FoldTile fold_tile(uint64_t tile, uint64_t per_job, u
     return f;
 }
 
+// The tile shape of a fold (see above).
+__host__ __device__ __forceinline__ void fold_shape(const Geometry &G, bool stats, uint32_t &TC, uint32_t &W) {
+    const uint32_t rw = (1u << G.k) >> 5;
+    TC = stats ? G.wpc : (G.wpc < 8u ? G.wpc : 8u);
+    const uint32_t wmax = stats ? 256u / G.wpc : 32u;
+    W = rw < wmax ? rw : wmax;
+}
+
 // Folds of several handles of one shape run as one launch (the batched
 // close): the tiles of job j follow those of job j - 1.  Two tile stages:
 // the next tile's plane words are copied in (cp.async) while the current
 // one is transposed; the transposed words are staged in place of the
 // current tile's input.
 __global__ void __launch_bounds__(kFoldThreads, 3)
-k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geometry G, uint32_t ps) {
+k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geometry G, uint32_t ps,
+             uint32_t stats) {
     extern __shared__ uint4 fold_smem[];
+    __shared__ uint32_t s_hot[32];
+    __shared__ unsigned long long s_zr;
+    __shared__ uint32_t s_nhot;
     uint32_t *const stage0 = reinterpret_cast<uint32_t *>(fold_smem);
-    constexpr uint32_t kStageWords = 32 * kFoldTC * kFoldW;
     const uint32_t wpc = G.wpc;
-    const uint32_t TC = wpc < kFoldTC ? wpc : kFoldTC;
+    uint32_t TC, W;
+    fold_shape(G, stats != 0, TC, W);
     const uint32_t rw = (1u << G.k) >> 5;  // plane words per row
-    const uint32_t W = rw < kFoldW ? rw : kFoldW;
     const uint32_t wgroups = rw / W, tgroups = wpc / TC;
     const uint64_t per_job = (uint64_t)G.dirs * G.r * wgroups * tgroups;
     const uint64_t tiles = per_job * njobs;
     const uint32_t W4 = W / 4, rows = 32u * TC;
-    const uint32_t tt = threadIdx.x >> 5, w = threadIdx.x & 31u;
+    const uint32_t tt = threadIdx.x / W, w = threadIdx.x % W;
+    const uint32_t lane = threadIdx.x & 31u;
     // a tile's first plane word
     auto plane_base = [&](const FoldTile &f) {
         return f.job.planes + ((uint64_t)f.d * G.g + 32u * f.tc0) * ps + (uint64_t)f.i * rw + f.w0;
@@ -97,7 +115,7 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
         if (tile < tiles) {
             const FoldTile f = fold_tile(tile, per_job, tgroups, wgroups, TC, W, G, one, jobs);
             const uint32_t *pb = plane_base(f);
-            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(stage0 + s * kStageWords);
+            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(stage0 + s * kFoldTile);
             for (uint32_t q = threadIdx.x; q < rows * W4; q += blockDim.x) {
                 const uint32_t row = q / W4, c = q - row * W4;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
@@ -107,6 +125,11 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
+    if (threadIdx.x < 32) s_hot[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        s_zr = 0;
+        s_nhot = 0;
+    }
     uint32_t cur = 0;
     issue(blockIdx.x, 0);
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, cur ^= 1u) {
@@ -114,7 +137,7 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are done
         __syncthreads();
         const FoldTile f = fold_tile(tile, per_job, tgroups, wgroups, TC, W, G, one, jobs);
-        uint32_t *in = stage0 + cur * kStageWords;
+        uint32_t *in = stage0 + cur * kFoldTile;
         // clear the tile's plane words that hold bits
         uint32_t *pb = plane_base(f);
         for (uint32_t q = threadIdx.x; q < rows * W4; q += blockDim.x) {
@@ -125,7 +148,7 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
             }
         }
         uint32_t x[32];
-        const bool mine = tt < TC && w < W;
+        const bool mine = tt < TC;
         if (mine) {
 #pragma unroll
             for (uint32_t j = 0; j < 32; j++) x[j] = in[(32u * tt + j) * W + w];
@@ -140,31 +163,74 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
         __syncthreads();
         // estimator 32 (w0 + w) + b of row i gets words tc0 .. tc0 + TC - 1
         uint32_t *row = f.job.grid + (uint64_t)f.d * G.dir_words + (uint64_t)f.i * G.row_words;
-        for (uint32_t e = threadIdx.x; e < 32u * W; e += blockDim.x) {
+        for (uint32_t e0 = 0; e0 < 32u * W; e0 += blockDim.x) {  // the same trip count for every thread
+            const uint32_t e = e0 + threadIdx.x;
+            const bool live = e < 32u * W;
             const uint32_t b = e / W, ww = e - b * W;
-            uint32_t v[kFoldTC];
-#pragma unroll
-            for (uint32_t t = 0; t < kFoldTC; t++) v[t] = t < TC ? out[(t * 32u + b) * W + ww] : 0u;
-            uint32_t *dst = row + (uint64_t)(32u * (f.w0 + ww) + b) * wpc + f.tc0;
-            if (TC == 8) {
-                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-#pragma unroll
-                for (uint32_t h = 0; h < 2; h++) {
-                    uint4 nv = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
-                    if (f.job.clean) {
-                        if (nv.x | nv.y | nv.z | nv.w) d4[h] = nv;
-                    } else if (nv.x | nv.y | nv.z | nv.w) {
-                        const uint4 c = d4[h];
-                        nv.x |= c.x; nv.y |= c.y; nv.z |= c.z; nv.w |= c.w;
-                        d4[h] = nv;
+            uint32_t pop = 0;
+            if (live) {
+                uint32_t *dst = row + (uint64_t)(32u * (f.w0 + ww) + b) * wpc + f.tc0;
+                if ((TC & 3u) == 0) {
+                    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                    for (uint32_t h = 0; h < TC / 4; h++) {
+                        uint4 nv = make_uint4(out[((4 * h) * 32u + b) * W + ww], out[((4 * h + 1) * 32u + b) * W + ww],
+                                              out[((4 * h + 2) * 32u + b) * W + ww],
+                                              out[((4 * h + 3) * 32u + b) * W + ww]);
+                        const bool any = (nv.x | nv.y | nv.z | nv.w) != 0;
+                        if (!f.job.clean && (any || stats)) {
+                            const uint4 c = d4[h];
+                            nv.x |= c.x; nv.y |= c.y; nv.z |= c.z; nv.w |= c.w;
+                            if (nv.x != c.x || nv.y != c.y || nv.z != c.z || nv.w != c.w) d4[h] = nv;
+                        } else if (any) {
+                            d4[h] = nv;
+                        }
+                        pop += __popc(nv.x) + __popc(nv.y) + __popc(nv.z) + __popc(nv.w);
+                    }
+                } else {
+                    for (uint32_t t = 0; t < TC; t++) {
+                        uint32_t v = out[(t * 32u + b) * W + ww];
+                        if (!f.job.clean && (v || stats)) v |= dst[t];
+                        if (out[(t * 32u + b) * W + ww]) dst[t] = v;
+                        pop += __popc(v);
                     }
                 }
-            } else {
-                for (uint32_t t = 0; t < TC; t++)
-                    if (v[t]) dst[t] = f.job.clean ? v[t] : (dst[t] | v[t]);
+            }
+            if (stats) {
+                // z_0 of this estimator; hot bits gathered per hot bitmap word
+                const uint32_t z0 = G.g - pop;
+                const bool hot = live && (int)z0 <= f.job.zhot;
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, hot);
+                unsigned long long zs = live ? z0 : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xFFFFFFFFu, zs, o);
+                if (lane == 0) {
+                    atomicAdd(&s_zr, zs);
+                    atomicAdd(&s_nhot, (uint32_t)__popc(mask));
+                }
+                // the warp's estimators: 32 / W values of b (W < 32) or one
+                if (lane < W && live) {
+                    const uint32_t b0 = (e - lane) / W;
+                    uint32_t c = 0;
+                    for (uint32_t qq = 0; qq * W < 32u; qq++) c |= ((mask >> (qq * W + lane)) & 1u) << (b0 + qq);
+                    atomicOr(&s_hot[lane], c);
+                }
             }
         }
-        __syncthreads();  // the stage is refilled two tiles on
+        __syncthreads();  // the stage is refilled two tiles on; the tile's statistics are complete
+        if (stats) {
+            uint32_t *hm = f.job.hotmap + ((uint64_t)f.d * G.r + f.i) * (rw) + f.w0;
+            if (threadIdx.x < W) {
+                hm[threadIdx.x] = s_hot[threadIdx.x];
+                s_hot[threadIdx.x] = 0;
+            }
+            if (threadIdx.x == 0) {
+                atomicAdd(&f.job.st->zr[f.d][f.i], s_zr);
+                atomicAdd(&f.job.st->nhot[f.d][f.i], s_nhot);
+                s_zr = 0;
+                s_nhot = 0;
+            }
+            __syncthreads();
+        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
@@ -172,16 +238,19 @@ k_plane_fold(FoldJob one, const FoldJob *__restrict__ jobs, uint32_t njobs, Geom
 cudaError_t launch_plane_fold(const FoldJob &one, const FoldJob *jobs, uint32_t njobs, const Geometry &G, uint32_t ps,
                               int num_sms, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
+    const bool stats = one.st != nullptr;
+    if (stats && !fold_stats_fit(G)) return cudaErrorInvalidValue;
     int per_sm = 0;
     cudaError_t e = prepare_launch(reinterpret_cast<const void *>(k_plane_fold), kFoldThreads, kFoldSmem, &per_sm);
     if (e != cudaSuccess) return e;
+    uint32_t TC, W;
+    fold_shape(G, stats, TC, W);
     const uint64_t rw = ((uint64_t)1 << G.k) >> 5;
-    const uint64_t W = rw < kFoldW ? rw : kFoldW;
-    const uint64_t TC = G.wpc < kFoldTC ? G.wpc : kFoldTC;
     const uint64_t tiles = (uint64_t)G.dirs * G.r * (rw / W) * (G.wpc / TC) * (jobs ? njobs : 1u);
     uint64_t blocks = (uint64_t)num_sms * per_sm;
     if (tiles < blocks) blocks = tiles;
-    k_plane_fold<<<(unsigned)blocks, kFoldThreads, kFoldSmem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps);
+    k_plane_fold<<<(unsigned)blocks, kFoldThreads, kFoldSmem, s>>>(one, jobs, jobs ? njobs : 1u, G, ps,
+                                                                   stats ? 1u : 0u);
     return cudaGetLastError();
 }
 

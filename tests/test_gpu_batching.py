@@ -123,6 +123,34 @@ def test_plane_batches_across_round_sizes(sd, O):
         assert rep.n_pairs == len(win.pairs)
 
 
+def test_plane_batch_lanes_with_handles_on_one_stream(sd, O):
+    """Members that share the driver's CUDA stream, dealt to the batch's
+    side lanes: each lane waits for the stream's earlier work and the
+    stream for every lane, so a second batch and the closes see every bit."""
+    import torch
+    w = T.WORKLOADS["tiny"].with_(dirs=2)
+    stream = torch.cuda.Stream()
+    sizes = [300_000, 250_000, 200_000, 150_000, 100_000, 5000]
+    seeds = [4000 + i for i in range(len(sizes))]
+    wins = [T.make_window(w.with_(n=n, planted=4), s, n=n) for n, s in zip(sizes, seeds)]
+    hs = [sd.sd_create(sd.params_for(w, s, cuda_stream=stream.cuda_stream)) for s in seeds]
+    try:
+        devs = [_dev(win.pairs) for win in wins]
+        half = [d[: 2 * (len(d) // 4)] for d in devs]
+        rest = [d[2 * (len(d) // 4):] for d in devs]
+        sd.sd_update_many(hs, half)
+        sd.sd_update_many(hs, rest)
+        grids = [np.concatenate([sd.sd_get_grid(h, d) for d in range(2)]) for h in hs]
+        reps = sd.sd_close_many(hs)
+    finally:
+        for h in hs:
+            sd.sd_destroy(h)
+    for win, s, g, rep in zip(wins, seeds, grids, reps):
+        og, ref = _oracle(O, w, win.pairs, s)
+        assert np.array_equal(g, og)
+        _same_report(rep, ref, 2)
+
+
 def test_close_many_equals_close_window_on_core_links(sd, O):
     """Core-link sketches (both directions, 2^16 estimators of 512 bits):
     three links closed together report what each reports alone."""
