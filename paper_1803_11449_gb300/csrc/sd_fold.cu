@@ -7,9 +7,9 @@
 // Plane (d, b) holds bit b of every estimator of direction d: its row i
 // starts at word i * 2^k/32 and holds estimator c's bit at word c >> 5, bit
 // c & 31 (planes are ps words apart).  The DHLA holds estimator c's g bits
-// as g/32 consecutive words.  Bit j of word (c >> 5) of plane 32 t + j is
-// bit j of word t of the 32 estimators of that word: each 32 x 32 bit block
-// is transposed.
+// as g/32 consecutive words.  Bit c & 31 of word c >> 5 of row i of plane
+// 32 t + j is bit j of word t of estimator c of row i: each 32 x 32 bit block
+// (32 planes x 32 estimators) is transposed.
 #include "sd_common.cuh"
 
 namespace sd {
@@ -27,7 +27,7 @@ namespace sd {
 //
 // Shapes: TC = min(8, g/32), W = min(32, 2^k/32); or, when the fold also
 // computes the row statistics, TC = g/32 (8, 16 or 32: the tile holds every
-// bit of its estimators) and W = 256 / TC.  With statistics each estimator's
+// bit of its estimators) and W = min(2^k/32, 256 / TC).  With statistics each estimator's
 // z_0 = g - popcount is tested against zhot, its hot bit goes to the tile's
 // W hot bitmap words (written whole), and the tile adds its sum of z_0 and
 // its hot count to ZR(i) and |HE(i)| -- what k_row_stats computes.
