@@ -1,8 +1,11 @@
 """Autotuner for the update kernel's launch knobs (sd_tuning).
 
-Each candidate setting is timed with CUDA events on the handle's stream over
-the caller's own pair buffer, starting from an empty DHLA every time (a
-window close clears it), and the fastest setting is applied to the handle.
+Each candidate setting is timed over the caller's own pair buffer as one
+whole window -- the update, then the close -- starting from an empty DHLA
+every time, and the fastest setting is applied to the handle.  The close is
+in the timed region because the plane-binned mode (6) folds its plane-major
+copy into the DHLA there; the rest of the close is the same for every
+setting.
 """
 from __future__ import annotations
 
@@ -20,7 +23,7 @@ BINNED = [dict(bin_slice_log2=sl, bin_tile_pairs=tp, bin_chunk_log2=ch, bin_slac
           for sl in (13, 14, 15) for tp in (512, 1024, 2048) for ch in (21, 22, 23, 24)]
 
 PLANES = [dict(plane_tile_pairs=tp, plane_round_log2=rd, plane_unit_log2=un)
-          for tp in (1024, 2048, 4096) for rd in (21, 22, 23, 24) for un in (13, 14, 15, 16)]
+          for tp in (4096, 8192) for rd in (22, 24, 26) for un in (13, 14, 15, 16)]
 
 
 def _space(modes, unrolls, threads, filters):
@@ -40,8 +43,11 @@ def _space(modes, unrolls, threads, filters):
 
 def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, threads=THREADS,
              filters=FILTERS, verbose: bool = False) -> dict:
-    """Time every setting of the search space on `pairs_dev`; apply and
-    return the best as a dict with its knobs, "ms" and "table"."""
+    """Time every setting of the search space on `pairs_dev` (one window:
+    sd_update, then sd_close_window, wall time after the stream is idle);
+    apply and return the best as a dict with its knobs, "ms" and "table"."""
+    import time
+
     import torch
 
     table = []
@@ -51,15 +57,13 @@ def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, 
         except sd.SdError:
             continue  # a setting this DHLA cannot take (e.g. a binning tile too large)
         times = []
+        sd.sd_close_window(h)  # clears the DHLA: every trial starts from zero
         for _ in range(reps):
-            sd.sd_close_window(h)  # clears the DHLA: every trial starts from zero
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             sd.sd_update(h, pairs_dev)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
+            sd.sd_close_window(h)
+            times.append(1e3 * (time.perf_counter() - t0))
         ms = sorted(times)[len(times) // 2]
         table.append(dict(knobs, ms=ms))
         if verbose:
@@ -70,39 +74,42 @@ def autotune(h, pairs_dev, stream, reps: int = 3, modes=MODES, unrolls=UNROLLS, 
     return dict(best, table=table)
 
 
-BATCHED = [dict(bin_chunk_log2=ch, bin_batch_mib=mib, bin_tile_pairs=tp)
-           for ch in (20, 21, 22, 23, 24) for mib in (1024, 4096, 8192) for tp in (1024, 2048)]
+BATCHED = ([dict(mode=5, bin_chunk_log2=ch, bin_batch_mib=mib, bin_tile_pairs=tp)
+            for ch in (21, 22, 23, 24) for mib in (1024, 8192) for tp in (1024, 2048)] +
+           [dict(mode=6, plane_round_log2=rd, bin_batch_mib=mib)
+            for rd in (22, 24, 26) for mib in (1, 8192)])
 
 
 def autotune_many(hs, pairs_list, stream, reps: int = 2, space=None, verbose: bool = False) -> dict:
-    """Time sd_update_many over the caller's links for every batched-update
-    setting (the driver hs[0]'s chunk, bins per round and tile), each trial
-    from empty DHLAs (sd_close_many clears them); apply the best to every
-    handle and return it as a dict with "ms" and "table"."""
+    """Time sd_update_many then sd_close_many over the caller's links for
+    every batched setting (mode 5: the driver hs[0]'s chunk, bins per round
+    and tile; mode 6: its round and the bins of its lanes -- 1 MiB allows one
+    lane), each trial from empty DHLAs; apply the best to every handle (the
+    mode to all, the knobs to each) and return it as a dict with "ms" and
+    "table"."""
+    import time
+
     import torch
 
     table = []
     for knobs in (space or BATCHED):
         try:
             for h in hs:
-                sd.sd_set_tuning(h, mode=5, **knobs)
+                sd.sd_set_tuning(h, **knobs)
         except sd.SdError:
             continue
         times = []
+        sd.sd_close_many(hs)
         for _ in range(reps):
-            sd.sd_close_many(hs)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             sd.sd_update_many(hs, pairs_list)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
+            sd.sd_close_many(hs)
+            times.append(1e3 * (time.perf_counter() - t0))
         table.append(dict(knobs, ms=min(times)))
         if verbose:
             print(table[-1], flush=True)
-    sd.sd_close_many(hs)
     best = min(table, key=lambda r: r["ms"])
     for h in hs:
-        sd.sd_set_tuning(h, mode=5, **{k: v for k, v in best.items() if k != "ms"})
+        sd.sd_set_tuning(h, **{k: v for k, v in best.items() if k != "ms"})
     return dict(best, table=table)
